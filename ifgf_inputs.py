@@ -1,0 +1,273 @@
+"""Seeded synthetic inputs for the IFGF operator: point sets, densities, targets.
+
+This module is shared by the CPU oracle's tests and by the CUDA path's tests and
+benchmark.  It holds only random-number and surface-sampling code, none of the
+method's arithmetic (no Green function, no tree, no interpolation).
+
+Random numbers come from the counter-based SplitMix64 generator (Steele, Lea &
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+output i of stream `seed` is mix64(seed + (i + 1) * 0x9E3779B97F4A7C15), with the
+published mix64 finaliser.  Uniform doubles take the top 53 bits; normal variates
+use the Box-Muller transform.
+
+Workloads (surfaces in the units of the paper's Section 4 examples):
+  * Fibonacci lattice on the unit sphere (the paper's sphere of radius a = 1),
+  * area-uniform points on the prolate spheroid of Eq. (defspheroid) with
+    alpha = beta = 0.1, gamma = 1,
+  * area-uniform points on the surface of a union of three overlapping cubes
+    (not in the paper; a closed non-convex surface with sharp edges).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, start: int, count: int) -> np.ndarray:
+    """Outputs start .. start+count-1 of the SplitMix64 stream `seed` (uint64)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, start: int, count: int) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, start, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, count: int) -> np.ndarray:
+    """count standard normal variates (Box-Muller on consecutive uniform pairs)."""
+    npair = (count + 1) // 2
+    u = uniform(seed, 0, 2 * npair)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    rad = np.sqrt(-2.0 * np.log(u1))
+    out = np.empty(2 * npair)
+    out[0::2] = rad * np.cos(2.0 * np.pi * u2)
+    out[1::2] = rad * np.sin(2.0 * np.pi * u2)
+    return out[:count]
+
+
+def complex_normal(seed: int, shape) -> np.ndarray:
+    """complex128 array whose real and imaginary parts are i.i.d. N(0,1)."""
+    n = int(np.prod(shape))
+    z = normal(seed, 2 * n)
+    return (z[0::2] + 1j * z[1::2]).reshape(shape)
+
+
+# --------------------------------------------------------------------------------------
+# Surfaces
+# --------------------------------------------------------------------------------------
+
+def fibonacci_sphere(n: int, radius: float = 1.0) -> np.ndarray:
+    """Fibonacci lattice: z_i = 1-(2i+1)/n, phi_i = i*pi*(3-sqrt 5) mod 2pi.  [n,3] f64."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    ga = math.pi * (3.0 - math.sqrt(5.0))
+    phi = np.mod(i * ga, 2.0 * math.pi)
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return radius * np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+
+
+def _unit_directions(seed: int, start: int, count: int) -> np.ndarray:
+    u = uniform(seed, 2 * start, 2 * count)
+    z = 2.0 * u[0::2] - 1.0
+    phi = 2.0 * math.pi * u[1::2]
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+
+
+def spheroid_points(n: int, axes=(0.1, 0.1, 1.0), seed: int = 3) -> np.ndarray:
+    """Area-uniform points on the ellipsoid x^2/a^2 + y^2/b^2 + z^2/c^2 = 1.
+
+    A uniform sphere direction u maps to (a u_x, b u_y, c u_z); the ellipsoid's
+    area element relative to the sphere's is a b c sqrt(sum u_i^2 / a_i^2), so the
+    candidate is accepted with probability sqrt(sum u_i^2/a_i^2) / max_i(1/a_i).
+    """
+    a = np.asarray(axes, dtype=np.float64)
+    inv_max = 1.0 / np.max(1.0 / a)
+    out = []
+    have = 0
+    start = 0
+    batch = max(1024, 2 * n)
+    while have < n:
+        d = _unit_directions(seed, start, batch)
+        acc = uniform(seed + 0x5151, start, batch)
+        p = np.sqrt(np.sum(d * d / (a * a), axis=1)) * inv_max
+        keep = acc < p
+        pts = d[keep] * a
+        out.append(pts)
+        have += pts.shape[0]
+        start += batch
+    return np.concatenate(out, axis=0)[:n]
+
+
+CUBES = (((0.0, 0.0, 0.0), 20.0), ((10.0, 10.0, 10.0), 20.0), ((20.0, 20.0, 20.0), 20.0))
+
+
+def cube_union_points(n: int, cubes=CUBES, seed: int = 4) -> np.ndarray:
+    """Area-uniform points on the boundary of a union of axis-aligned cubes.
+
+    Every cube face has the same area, so a candidate picks a cube and a face
+    uniformly, a point uniformly on that face, and is rejected when it lies
+    strictly inside another cube.
+    """
+    lo = np.array([c[0] for c in cubes], dtype=np.float64)
+    side = np.array([c[1] for c in cubes], dtype=np.float64)
+    nc = len(cubes)
+    out = []
+    have = 0
+    start = 0
+    batch = max(1024, 2 * n)
+    while have < n:
+        u = uniform(seed, 4 * start, 4 * batch).reshape(batch, 4)
+        ci = np.minimum((u[:, 0] * nc).astype(np.int64), nc - 1)
+        face = np.minimum((u[:, 1] * 6).astype(np.int64), 5)
+        axis = face // 2
+        high = face % 2
+        s = side[ci]
+        p = np.empty((batch, 3))
+        # the two in-face coordinates
+        a1 = (axis + 1) % 3
+        a2 = (axis + 2) % 3
+        rows = np.arange(batch)
+        p[rows, axis] = lo[ci, axis] + high * s
+        p[rows, a1] = lo[ci, a1] + u[:, 2] * s
+        p[rows, a2] = lo[ci, a2] + u[:, 3] * s
+        inside_other = np.zeros(batch, dtype=bool)
+        for j in range(nc):
+            strict = np.all((p > lo[j]) & (p < lo[j] + side[j]), axis=1)
+            inside_other |= strict & (ci != j)
+        pts = p[~inside_other]
+        out.append(pts)
+        have += pts.shape[0]
+        start += batch
+    return np.concatenate(out, axis=0)[:n]
+
+
+def plane_wave_densities(points: np.ndarray, kappa: float, nrhs: int, seed: int) -> np.ndarray:
+    """sigma_r(x) = A_r exp(i kappa d_r . x), d_r seeded unit vectors, A_r complex N(0,1).
+
+    Returns complex128 [nrhs, N].
+    """
+    d = _unit_directions(seed, 0, nrhs)
+    amp = complex_normal(seed + 0x77, (nrhs,))
+    phase = kappa * (points @ d.T)  # [N, nrhs]
+    return (amp[None, :] * np.exp(1j * phase)).T.copy()
+
+
+def sample_targets(n: int, m: int, seed: int) -> np.ndarray:
+    """First m entries of a seeded Fisher-Yates permutation of [0, n) (int64).
+
+    Only the first m swaps are carried out, so the cost is O(m) for any n.
+    """
+    m = min(m, n)
+    u = uniform(seed, 0, m)
+    swaps: dict[int, int] = {}
+    out = np.empty(m, dtype=np.int64)
+    for i in range(m):
+        j = min(i + int(u[i] * (n - i)), n - 1)
+        vi = swaps.get(i, i)
+        vj = swaps.get(j, j)
+        swaps[i] = vj
+        swaps[j] = vi
+        out[i] = vj
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    """One synthetic problem: points, wavenumber, tree/cone parameters, densities."""
+    name: str
+    n: int
+    kappa: float
+    levels: int
+    p_radial: int = 3
+    p_angular: int = 5
+    leaf_ns: int = 1
+    leaf_nc: int = 2
+    nrhs: int = 1
+    precision: str = "fp64"
+    targets: int = 1000
+    seed: int = 0
+    surface: str = "sphere"
+    description: str = ""
+    _points: np.ndarray | None = field(default=None, repr=False)
+
+    def points(self) -> np.ndarray:
+        if self._points is None:
+            if self.surface == "sphere":
+                self._points = fibonacci_sphere(self.n)
+            elif self.surface == "prolate":
+                self._points = spheroid_points(self.n, (0.1, 0.1, 1.0), seed=self.seed)
+            elif self.surface == "cubes":
+                self._points = cube_union_points(self.n, seed=self.seed)
+            elif self.surface == "random_sphere":
+                d = _unit_directions(self.seed, 0, self.n)
+                self._points = d
+            else:
+                raise ValueError(self.surface)
+        return self._points
+
+    def densities(self) -> np.ndarray:
+        """complex128 [nrhs, N]."""
+        if self.surface == "cubes" and self.nrhs > 1:
+            return plane_wave_densities(self.points(), self.kappa, self.nrhs, self.seed + 100)
+        return complex_normal(self.seed + 100, (self.nrhs, self.n))
+
+    def target_indices(self) -> np.ndarray:
+        return sample_targets(self.n, self.targets, self.seed + 200)
+
+
+def wavelengths_to_kappa(size: float, n_lambda: float) -> float:
+    """kappa = 2 pi / lambda for a body of extent `size` spanning n_lambda wavelengths."""
+    return 2.0 * math.pi * n_lambda / size
+
+
+WORKLOADS = {
+    # unit sphere, diameter 4 wavelengths, D = 4
+    "sphere_4lambda": Workload("sphere_4lambda", 24_576, wavelengths_to_kappa(2.0, 4), 4,
+                               leaf_ns=2, leaf_nc=4, targets=24_576, seed=1, surface="sphere",
+                               description="Fibonacci sphere N=24576, 4 lambda, D=4, FP64"),
+    # unit sphere, diameter 32 wavelengths, D = 8
+    "sphere_32lambda": Workload("sphere_32lambda", 393_216, wavelengths_to_kappa(2.0, 32), 8,
+                                leaf_ns=1, leaf_nc=2, targets=2_000, seed=2, surface="sphere",
+                                description="Fibonacci sphere N=393216, 32 lambda, D=8, FP64 + adjoint"),
+    # prolate spheroid 10:1:1, long axis 128 wavelengths, D = 10
+    "prolate_128lambda": Workload("prolate_128lambda", 3_145_728, wavelengths_to_kappa(2.0, 128), 10,
+                                  leaf_ns=1, leaf_nc=2, targets=4_096, seed=3, surface="prolate",
+                                  precision="mixed",
+                                  description="prolate spheroid N=3145728, 128 lambda, D=10, mixed"),
+    # union of three cubes of side 20 wavelengths, 64 plane-wave RHS, D = 8
+    "cubes_64rhs": Workload("cubes_64rhs", 1_572_864, 2.0 * math.pi, 8,
+                            leaf_ns=1, leaf_nc=2, nrhs=64, targets=2_048, seed=4, surface="cubes",
+                            precision="batched",
+                            description="three-cube union N=1572864, lambda=1, 64 RHS"),
+    # unit sphere, diameter 256 wavelengths, D = 9, 8 RHS
+    "sphere_256lambda": Workload("sphere_256lambda", 25_165_824, wavelengths_to_kappa(2.0, 256), 9,
+                                 leaf_ns=4, leaf_nc=8, nrhs=8, targets=1_024, seed=5, surface="sphere",
+                                 precision="mixed",
+                                 description="Fibonacci sphere N=25165824, 256 lambda, D=9, 8 RHS"),
+}
+
+
+def small_sphere(n: int, n_lambda: float, levels: int, leaf_ns=1, leaf_nc=2, seed=11,
+                 nrhs=1) -> Workload:
+    """A small Fibonacci-sphere case sized for the oracle (test use)."""
+    return Workload(f"sphere_n{n}", n, wavelengths_to_kappa(2.0, n_lambda), levels,
+                    leaf_ns=leaf_ns, leaf_nc=leaf_nc, nrhs=nrhs, targets=n, seed=seed,
+                    surface="sphere")
