@@ -1,0 +1,314 @@
+"""Benchmark of the IFGF apply (u = A sigma, Eq. field1) on GB300.
+
+Metric: IFGF apply time t and equivalent interactions per second N^2 * nrhs / t
+(the exact sum of Eq. field1 would touch N^2 pairs per right-hand side).
+
+A step is one full apply (density permutation, leaf analytic factors, upward
+interpolation of every level, target evaluation = near field + cousin
+interpolation of every level, output permutation) on densities already resident
+in HBM.  The plan (octree and relevant cones) is built once before timing, as the
+paper's T_acc excludes T_pre; its build time is reported as t_plan_ms.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ifgf|reference]
+
+--impl reference times the CPU oracle (the direct sum of Eq. field1 on a bounded
+sample of targets, all host cores) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ifgf_inputs as wi  # noqa: E402
+
+DEFAULT_WORKLOAD = "sphere_32lambda"
+METRIC = "IFGF apply time and equivalent interactions/s (N^2/t) at rel.err<=1e-3 vs FP64 direct"
+UNIT = "interactions/s"
+
+# Algorithmic FP64 work of one upward evaluation (one parent interpolation point
+# interpolated from one child cone), counted as floating-point operations of the
+# method's arithmetic: 75-term sum-factorised contraction 2*(75+15+3)*2 = 372,
+# Lagrange weights 3*(2+1)+2*5*(4+1) = 59, three local coordinates 12, the
+# re-centring factor 14, complex multiply-accumulate 8; transcendental and
+# correctly-rounded calls (2 sqrt, 3 div, 2 atan2, 1 sincos, 1 rint) counted as 1 each.
+UPWARD_FLOPS_PER_EVAL = 372 + 59 + 12 + 14 + 8 + 9
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def fp64_peak_tflops() -> tuple[float, str]:
+    """FP64 FMA-pipe peak of this GPU (measured by the committed probe summary)."""
+    path = os.path.join(ROOT, "profiles", "fp64_peak.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["fp64_tflops"]), "measured (profiles/fp64_peak.json)"
+    return 1.25, "nominal GB300 FP64 (no measurement committed)"
+
+
+def run_reference(args, wl: wi.Workload):
+    """The oracle's direct sum on a bounded sample of targets, on the host cores."""
+    import oracle
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    pts = wl.points()
+    sig = wl.densities()
+    tg = wl.target_indices()
+    m = min(len(tg), max(8, int(args.ref_targets)))
+    tg = tg[:m]
+    oracle.direct(pts, wl.kappa, sig, tg[:4])  # warm the library
+    times = []
+    for _ in range(args.warmup):
+        oracle.direct(pts, wl.kappa, sig, tg)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.direct(pts, wl.kappa, sig, tg)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = m * wl.n * wl.nrhs / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "nrhs": wl.nrhs, "kappa": wl.kappa},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"FP64 direct sum of Eq. (field1) at {m} sampled targets x {wl.n} sources"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(wl: wi.Workload, seconds: float = 12.0) -> dict:
+    import oracle
+    oracle.build()
+    pts = wl.points()
+    sig = wl.densities()
+    tg = wl.target_indices()
+    m = 8
+    t = 0.0
+    while True:
+        t0 = time.perf_counter()
+        oracle.direct(pts, wl.kappa, sig, tg[:m])
+        t = time.perf_counter() - t0
+        if t > seconds / 4 or m >= len(tg):
+            break
+        m = min(len(tg), int(m * max(2.0, seconds / 4 / max(t, 1e-3))))
+    value = m * wl.n * wl.nrhs / t
+    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 direct sum of Eq. (field1) at {m} sampled targets x {wl.n} sources, {t:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(wi.WORKLOADS))
+    ap.add_argument("--impl", default="ifgf", choices=["ifgf", "reference"])
+    ap.add_argument("--ref-targets", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
+    args = ap.parse_args()
+    wl = wi.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    import paper_2010_02857_gb300 as pkg
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precision = {"fp64": "fp64", "mixed": "mixed", "batched": "mixed"}[wl.precision]
+    pts = torch.from_numpy(wl.points()).to(dev)
+    t0 = time.perf_counter()
+    plan = pkg.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc,
+                    max_nrhs=wl.nrhs, precision=precision)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    stats = plan.stats()
+    sig_np = wl.densities().astype(plan.numpy_dtype)
+    sig = torch.from_numpy(sig_np).to(dev)
+    u = torch.empty_like(sig)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(max(3, args.warmup)):
+        plan.apply(sig, out=u)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between steps (256 MB > 129 MB L2)
+        ev[k][0].record(stream)
+        plan.apply(sig, out=u)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    timings = plan.timings()
+    plan.set_profiling(False)
+
+    # end to end through the C ABI with pinned host buffers
+    sig_h = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
+    sig_h.copy_(torch.from_numpy(sig_np))
+    u_h = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
+    e2e_times = []
+    for _ in range(max(2, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        plan.apply(sig_h, out=u_h)  # host pointers: H2D, apply, D2H, synchronise
+        e2e_times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    n, nrhs = wl.n, wl.nrhs
+    value = world * n * n * nrhs / (ms * 1e-3)
+    e2e_s = float(np.median(e2e_times))
+    eb = 16 if precision == "fp64" else 8
+
+    # roofline of the dominant stage (upward interpolation, FP64-pipe bound)
+    st = timings["stages"]
+    calls = max(1, timings["calls"])
+    up_ms = st["upward"]["ms"] / calls
+    up_launches = st["upward"]["launches"] / calls
+    up_evals = sum(lv["upward_evals"] for lv in stats["level"])
+    peak, peak_src = fp64_peak_tflops()
+    achieved = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
+    roofline = {"bound": "alu", "kernel": "k_upward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": peak_src,
+                "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
+                        f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+
+    check = None
+    if args.check:
+        import oracle
+        tg = wl.target_indices()[:512]
+        ex = oracle.direct(wl.points(), wl.kappa, wl.densities(), tg)
+        got = u.cpu().numpy()[:, tg]
+        check = float(np.linalg.norm(got - ex) / np.linalg.norm(ex))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
+                           "p_radial": wl.p_radial, "p_angular": wl.p_angular,
+                           "leaf_cones": [wl.leaf_ns, wl.leaf_nc], "precision": precision,
+                           "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "t_plan_ms": t_plan * 1e3,
+                "stage_ms": {k: v["ms"] / calls for k, v in st.items() if v["launches"]},
+                "e2e": {"value": world * n * n * nrhs / e2e_s, "unit": UNIT,
+                        "h2d_bytes_per_step": n * nrhs * eb, "d2h_bytes_per_step": n * nrhs * eb,
+                        "ms_per_step": e2e_s * 1e3},
+                "gpu_launches": int(sum(v["launches"] for v in st.values()) / calls * args.steps),
+                "roofline": roofline, "clocks": clk,
+                "device_bytes": stats["device_bytes"]}
+        if check is not None:
+            line["rel_err_sampled"] = check
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * ifgf.h - C ABI of the GB300 (sm_103a) IFGF library.
+ *
+ * The library evaluates the discrete Helmholtz single-layer operator of
+ * Bauinger & Bruno, "Interpolated Factored Green Function method for accelerated
+ * solution of scattering problems" (arXiv 2010.02857), Eq. (field1) with the
+ * kernel of Eq. (greensfunction):
+ *
+ *     u_r(x_l) = sum_{m != l} sigma_r(x_m) exp(i kappa |x_l - x_m|) / (4 pi |x_l - x_m|),
+ *
+ * for l = 1..N and right-hand sides r = 0..nrhs-1, by the IFGF method of
+ * Algorithm 1 (Sec. 3.3.3): a box octree of D levels (Sec. 3.3.1), per-box cone
+ * segments in the (s, theta, phi) variables of Eq. (defparametrizationins), and
+ * Chebyshev interpolation of the analytic factor of Eq. (factored_f) with
+ * P = P_s * P_ang^2 points per cone (Eq. interp_pts).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an ifgf_status; none aborts, traps or exits.
+ *   - Complex data are interleaved (re, im) pairs.  FP64 plans take complex128
+ *     (double pairs); all other precisions take complex64 (float pairs).
+ *   - Densities and fields are row-major [nrhs][N] in the caller's point order.
+ *   - Array arguments may be host or device pointers unless stated otherwise;
+ *     the library detects which with cudaPointerGetAttributes.  With device
+ *     pointers the call is asynchronous on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream).  With host pointers the call copies through
+ *     plan-owned device buffers and returns after the result is on the host.
+ *   - The caller owns every array it passes; the plan copies what it needs
+ *     (the points) and keeps no caller pointer after a call returns.
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the
+ *     caller (the plan owns the intermediate cone-value buffers).
+ */
+#ifndef IFGF_H
+#define IFGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ifgf_plan ifgf_plan;
+
+typedef enum {
+    IFGF_OK = 0,
+    IFGF_EINVAL = 1,    /* invalid argument (sizes, levels, non-finite points, nrhs) */
+    IFGF_ENOMEM = 2,    /* device or host allocation failed */
+    IFGF_ECUDA = 3,     /* a CUDA runtime call failed; see ifgf_last_error */
+    IFGF_ETIMEOUT = 4,  /* a host-side wait exceeded its limit */
+    IFGF_EINTERNAL = 5  /* an internal invariant failed (e.g. a cone lookup missed) */
+} ifgf_status;
+
+typedef enum {
+    /* all arithmetic in FP64; complex128 data */
+    IFGF_FP64 = 0,
+    /* FP64 for point differences, distances, spherical coordinates and phase
+     * arguments; FP32 interpolation, accumulation and reduced-phase sincos;
+     * complex64 data */
+    IFGF_MIXED = 1,
+    /* IFGF_MIXED with the per-cone interpolation contraction on tensor cores
+     * (BF16 operands, FP32 accumulate); meant for many right-hand sides */
+    IFGF_BATCHED_BF16 = 2
+} ifgf_precision;
+
+typedef struct {
+    int leaf_ns;    /* n_{s,D}: radial cone intervals at the leaf level; 0 = default */
+    int leaf_nc;    /* n_{C,D}: polar intervals at the leaf level (2 n_C azimuthal); 0 = default */
+    int max_nrhs;   /* largest nrhs a later apply may use; 0 = 1 */
+    int precision;  /* an ifgf_precision */
+    int flags;      /* bit 0: build the adjoint's transpose lists at plan time */
+} ifgf_options;
+
+/*
+ * Build a plan: the octree, cousin lists and relevant cone segments of every level
+ * (Sec. 3.3.1, Eq. defcousinboxes and defallrelevantconesegments; the
+ * pre-computation stage of Algorithm 1), on the GPU.
+ *   points    [N][3] double, x y z per point, host or device; pairwise distinct.
+ *   n         N >= 2 (and < 2^31).
+ *   kappa     wavenumber >= 0 (kappa = 0 gives the Laplace kernel 1/(4 pi r)).
+ *   levels    D >= 3, <= 20: the number of octree levels, root = level 1 (Sec. 3.3.1).
+ *   p_radial  P_s  >= 1, <= 8: Chebyshev points per cone along s.
+ *   p_angular P_ang >= 1, <= 8: Chebyshev points per cone along theta and along phi.
+ *   opt       NULL for defaults.  Default leaf cones: (n_s, n_C) = (1, 2) for leaf boxes
+ *             up to a quarter wavelength, doubled per doubling of the leaf size
+ *             (Sec. 4 uses (1, 2) at H_D ~ lambda / 4).
+ *   stream    cudaStream_t used for the build; the call synchronises it before return.
+ *   out       receives the plan (NULL on failure).
+ * Errors: IFGF_EINVAL for bad arguments, IFGF_ENOMEM, IFGF_ECUDA.
+ */
+ifgf_status ifgf_plan_create(const double *points, int64_t n, double kappa, int levels,
+                             int p_radial, int p_angular, const ifgf_options *opt,
+                             void *stream, ifgf_plan **out);
+
+/*
+ * u = A sigma: the IFGF evaluation stage of Algorithm 1 (level-D direct sums over
+ * neighbouring boxes, analytic factors at the leaf cones' interpolation points,
+ * and for d = D..3 interpolation to cousin targets and, for d > 3, to the parent
+ * cones' interpolation points with re-centring).
+ *   sigma  [nrhs][N] complex (complex128 for IFGF_FP64 plans, complex64 otherwise).
+ *   u      [nrhs][N] complex output, same type; overwritten.
+ *   nrhs   1 <= nrhs <= max_nrhs of the plan.
+ * Errors: IFGF_EINVAL (nrhs, NULL), IFGF_ECUDA.
+ */
+ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma, void *u, int nrhs, void *stream);
+
+/*
+ * w = A^H v: the exact conjugate transpose of the operator that ifgf_apply
+ * computes (every linear step of Algorithm 1 transposed and conjugated, run from
+ * targets to cone nodes to sources).  The paper has no adjoint; this is the
+ * linear algebra of the same steps.  Arguments as for ifgf_apply.
+ */
+ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *v, void *w, int nrhs, void *stream);
+
+/*
+ * Partial evaluation for stage-wise checks: mode bit 0 = level-D direct
+ * neighbour sums only, bit 1 = interpolated (far) contributions only, 3 = both
+ * (= ifgf_apply).  `adjoint` != 0 selects the adjoint.
+ */
+ifgf_status ifgf_apply_partial(ifgf_plan *plan, const void *in, void *out, int nrhs, int mode,
+                               int adjoint, void *stream);
+
+/* Release every device and host resource of the plan.  NULL is accepted. */
+ifgf_status ifgf_plan_destroy(ifgf_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * Introspection (host outputs; the call synchronises the plan's work first).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Per-level counts of level d (1..D), written to info[0..7]:
+ * nbox, neighbour entries, cousin entries, relevant cones, n_s, n_C,
+ * cousin evaluations per apply, upward evaluations per apply.
+ */
+ifgf_status ifgf_plan_level_info(const ifgf_plan *plan, int level, int64_t *info);
+
+/* perm[i] = caller index of the i-th point in Morton order ([N] int64, host). */
+ifgf_status ifgf_plan_get_perm(const ifgf_plan *plan, int64_t *perm);
+
+/* Relevant boxes of level d: keys[nbox] (Morton key of the integer box
+ * coordinate) and start[nbox+1] (ranges into the Morton-ordered points). */
+ifgf_status ifgf_plan_get_boxes(const ifgf_plan *plan, int level, uint64_t *keys, int64_t *start);
+
+/* Cousin lists of level d >= 3 (Eq. defcousinboxes) in CSR form. */
+ifgf_status ifgf_plan_get_cousins(const ifgf_plan *plan, int level, int64_t *start, int64_t *list);
+
+/* Relevant cones of level d >= 3 (Eq. defallrelevantconesegments) in CSR form:
+ * start[nbox+1], cones[nact] = linear cone id (g1 n_C + g2) 2 n_C + g3. */
+ifgf_status ifgf_plan_get_active(const ifgf_plan *plan, int level, int64_t *start, int64_t *cones);
+
+/* Cone values F_k^d at the interpolation points of level d after the last apply:
+ * [nact][P][nrhs] complex of the plan's data type (host). */
+ifgf_status ifgf_plan_get_values(const ifgf_plan *plan, int level, void *out);
+
+/* Root cube: geom[0] = H_1, geom[1..3] = lower corner. */
+ifgf_status ifgf_plan_geometry(const ifgf_plan *plan, double *geom);
+
+/* JSON statistics (counts per level, device bytes, build time) into buf[cap]. */
+ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t cap);
+
+/* Status of the device-side invariant checks of all calls since the last query
+ * (0 = none failed); synchronises the plan's stream and clears the flag. */
+ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors);
+
+/*
+ * Per-stage timing.  With profiling on, every apply records CUDA events on its
+ * stream between stages and waits for them before returning, adding the elapsed
+ * times per stage.  Turning it on or off clears the totals.
+ */
+ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on);
+
+/*
+ * Totals since profiling was turned on: ms[s] milliseconds and launches[s] kernel
+ * launches of stage s, calls = profiled calls; count >= 7.  Stages: 0 density
+ * permutation, 1 leaf analytic factors, 2 upward interpolation (all levels),
+ * 3 target evaluation (near + cousin interpolation), 4 output permutation,
+ * 5 adjoint cone levels, 6 adjoint source evaluation.
+ */
+ifgf_status ifgf_plan_timings(const ifgf_plan *plan, double *ms, int64_t *launches, int64_t *calls,
+                              int count);
+
+/* Message of the last failed call on this plan (or of the last failed
+ * ifgf_plan_create when plan is NULL).  Never NULL. */
+const char *ifgf_last_error(const ifgf_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFGF_H */

@@ -1,0 +1,412 @@
+// C ABI of the IFGF library: argument checks, plan lifetime, host/device pointer
+// handling and introspection.  All numerical work is in ifgf_plan.cu and the
+// ifgf_apply_*.cu kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ifgf_internal.h"
+
+cudaError_t ifgf_run_typed_f64(const PlanDev &pd, int nrhs, const void *in_user, void *out_user,
+                               void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
+                               StageTimer &tm);
+cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user, void *out_user,
+                               void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
+                               StageTimer &tm);
+
+static thread_local std::string g_create_error;
+
+static bool is_device_pointer(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void free_plan(ifgf_plan *p)
+{
+    for (int i = 0; i < 64; ++i)
+        if (p->timer.ev[i]) cudaEventDestroy(p->timer.ev[i]);
+    for (void *ptr : p->allocs) cudaFree(ptr);
+    p->allocs.clear();
+    delete p;
+}
+
+// Default leaf cones: (1, 2) for leaves up to a quarter wavelength (the setting of
+// the paper's Sec. 4 experiments), doubled per doubling of H_D / (lambda / 4).
+static void default_leaf_cones(double kappa, double HD, int *ns, int *nc)
+{
+    int m = 0;
+    if (kappa > 0) {
+        double lambda = 2.0 * M_PI / kappa;
+        double ratio = HD / (0.25 * lambda);
+        if (ratio > 1.0) m = (int)std::lround(std::log2(ratio));
+    }
+    if (m > 10) m = 10;
+    *ns = 1 << m;
+    *nc = 2 << m;
+}
+
+extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double kappa, int levels,
+                                        int p_radial, int p_angular, const ifgf_options *opt,
+                                        void *stream, ifgf_plan **out)
+{
+    if (out) *out = nullptr;
+    g_create_error.clear();
+    if (!points || !out) { g_create_error = "NULL argument"; return IFGF_EINVAL; }
+    if (n < 2 || n >= ((int64_t)1 << 31) - 1) { g_create_error = "N must be in [2, 2^31)"; return IFGF_EINVAL; }
+    if (!(kappa >= 0.0) || !std::isfinite(kappa)) { g_create_error = "kappa must be finite and >= 0"; return IFGF_EINVAL; }
+    if (levels < 3 || levels > IFGF_MAX_LEVELS) { g_create_error = "levels must be in [3, 20]"; return IFGF_EINVAL; }
+    if (!((p_radial == 3 && p_angular == 5) || (p_radial == 4 && p_angular == 7))) {
+        g_create_error = "supported (P_s, P_ang): (3, 5) and (4, 7)";
+        return IFGF_EINVAL;
+    }
+    ifgf_options o = {0, 0, 1, IFGF_FP64, 0};
+    if (opt) o = *opt;
+    if (o.max_nrhs <= 0) o.max_nrhs = 1;
+    if (o.max_nrhs > 1024) { g_create_error = "max_nrhs must be <= 1024"; return IFGF_EINVAL; }
+    if (o.precision != IFGF_FP64 && o.precision != IFGF_MIXED && o.precision != IFGF_BATCHED_BF16) {
+        g_create_error = "unknown precision";
+        return IFGF_EINVAL;
+    }
+    if (o.leaf_ns < 0 || o.leaf_nc < 0 || o.leaf_ns > 1024 || o.leaf_nc > 1024) {
+        g_create_error = "leaf cone counts out of range";
+        return IFGF_EINVAL;
+    }
+    ifgf_plan *p = new (std::nothrow) ifgf_plan();
+    if (!p) { g_create_error = "host allocation failed"; return IFGF_ENOMEM; }
+    p->n = n;
+    p->D = levels;
+    p->Ps = p_radial;
+    p->Pang = p_angular;
+    p->P = p_radial * p_angular * p_angular;
+    p->kappa = kappa;
+    p->precision = o.precision;
+    p->max_nrhs = o.max_nrhs;
+    p->flags = o.flags;
+    cudaStream_t st = (cudaStream_t)stream;
+    p->build_stream = st;
+    // leaf cones need H_D, known only after the root cube: the builder reads lh[D]
+    // and a non-positive entry means "default"
+    p->lh[levels].ns = o.leaf_ns;
+    p->lh[levels].nc = o.leaf_nc;
+    if (o.leaf_ns == 0 || o.leaf_nc == 0) {
+        // the root cube is the bounding cube of the points; compute its side on the
+        // host only for this default (the builder recomputes it on the GPU)
+        std::vector<double> h;
+        const double *hp = points;
+        if (is_device_pointer(points)) {
+            h.resize((size_t)n * 3);
+            if (cudaMemcpy(h.data(), points, h.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                g_create_error = "copy of points failed";
+                delete p;
+                return IFGF_ECUDA;
+            }
+            hp = h.data();
+        }
+        double lo[3] = {hp[0], hp[1], hp[2]}, hi[3] = {hp[0], hp[1], hp[2]};
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = std::min(lo[c], hp[3 * i + c]);
+                hi[c] = std::max(hi[c], hp[3 * i + c]);
+            }
+        double H1 = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        int ns, nc;
+        default_leaf_cones(kappa, std::ldexp(H1, -(levels - 1)), &ns, &nc);
+        if (o.leaf_ns == 0) p->lh[levels].ns = ns;
+        if (o.leaf_nc == 0) p->lh[levels].nc = nc;
+    }
+    ifgf_status s = ifgf_build_plan(p, points, st);
+    if (s == IFGF_OK && (o.flags & 1)) s = ifgf_build_adjoint_lists(p, st);
+    if (s != IFGF_OK) {
+        g_create_error = p->last_error;
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        free_plan(p);
+        return s;
+    }
+    *out = p;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, int mode, int adjoint,
+                           cudaStream_t st)
+{
+    if (!p || !in || !out) return IFGF_EINVAL;
+    if (nrhs < 1 || nrhs > p->max_nrhs) {
+        p->last_error = "nrhs must be in [1, max_nrhs]";
+        return IFGF_EINVAL;
+    }
+    if (mode < 1 || mode > 3) {
+        p->last_error = "mode must be 1, 2 or 3";
+        return IFGF_EINVAL;
+    }
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    const size_t bytes = (size_t)p->n * nrhs * eb;
+    const bool in_dev = is_device_pointer(in), out_dev = is_device_pointer(out);
+    if ((!in_dev || !out_dev) && !p->stage_in) {
+        p->stage_in = ifgf_dalloc(p, (size_t)p->n * p->max_nrhs * eb);
+        p->stage_out = ifgf_dalloc(p, (size_t)p->n * p->max_nrhs * eb);
+        if (!p->stage_in || !p->stage_out) {
+            p->last_error = "staging buffers";
+            return IFGF_ENOMEM;
+        }
+    }
+    const void *din = in;
+    void *dout = out;
+    if (!in_dev) {
+        if (cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            p->last_error = "host-to-device copy failed";
+            return IFGF_ECUDA;
+        }
+        din = p->stage_in;
+    }
+    if (!out_dev) dout = p->stage_out;
+    if (adjoint && !p->adjoint_ready) {
+        // first adjoint call: build the transpose lists (synchronises the stream)
+        ifgf_status s = ifgf_build_adjoint_lists(p, st);
+        if (s != IFGF_OK) return s;
+    }
+    p->timer.n = 0;
+    cudaError_t e = p->precision == IFGF_FP64
+                        ? ifgf_run_typed_f64(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st,
+                                             p->timer)
+                        : ifgf_run_typed_f32(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st,
+                                             p->timer);
+    if (e != cudaSuccess) {
+        p->last_error = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+        return IFGF_ECUDA;
+    }
+    if (p->timer.on && p->timer.n > 1) {
+        // profiling mode: wait for this call and attribute the time between marks
+        if (cudaEventSynchronize(p->timer.ev[p->timer.n - 1]) != cudaSuccess) {
+            p->last_error = "event synchronisation failed";
+            return IFGF_ECUDA;
+        }
+        for (int i = 1; i < p->timer.n; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->timer.ev[i - 1], p->timer.ev[i]);
+            int s = p->timer.stage[i];
+            if (s >= 0 && s < STAGE_COUNT) {
+                p->stage_ms[s] += ms;
+                p->stage_launches[s] += p->timer.launches[i];
+            }
+        }
+        p->stage_calls += 1;
+    }
+    p->last_nrhs = nrhs;
+    if (!out_dev) {
+        if (cudaMemcpyAsync(out, p->stage_out, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            p->last_error = "device-to-host copy failed";
+            return IFGF_ECUDA;
+        }
+    }
+    if (!in_dev || !out_dev) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            p->last_error = std::string("stream synchronisation failed: ") + cudaGetErrorString(e);
+            return IFGF_ECUDA;
+        }
+    }
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma, void *u, int nrhs, void *stream)
+{
+    return ifgf_run_apply(plan, sigma, u, nrhs, 3, 0, (cudaStream_t)stream);
+}
+
+extern "C" ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *v, void *w, int nrhs, void *stream)
+{
+    return ifgf_run_apply(plan, v, w, nrhs, 3, 1, (cudaStream_t)stream);
+}
+
+extern "C" ifgf_status ifgf_apply_partial(ifgf_plan *plan, const void *in, void *out, int nrhs, int mode,
+                                          int adjoint, void *stream)
+{
+    return ifgf_run_apply(plan, in, out, nrhs, mode, adjoint ? 1 : 0, (cudaStream_t)stream);
+}
+
+extern "C" ifgf_status ifgf_plan_destroy(ifgf_plan *plan)
+{
+    if (!plan) return IFGF_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return IFGF_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Introspection
+// ---------------------------------------------------------------------------------
+static ifgf_status copy_i32_as_i64(ifgf_plan *p, const int *src, int64_t count, int64_t *dst)
+{
+    if (count <= 0) return IFGF_OK;
+    std::vector<int> h((size_t)count);
+    if (cudaMemcpy(h.data(), src, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        p->last_error = "device-to-host copy failed";
+        return IFGF_ECUDA;
+    }
+    for (int64_t i = 0; i < count; ++i) dst[i] = h[(size_t)i];
+    return IFGF_OK;
+}
+
+static bool level_ok(const ifgf_plan *p, int level, int min_level)
+{
+    return p && level >= min_level && level <= p->D;
+}
+
+extern "C" ifgf_status ifgf_plan_level_info(const ifgf_plan *plan, int level, int64_t *info)
+{
+    if (!level_ok(plan, level, 1) || !info) return IFGF_EINVAL;
+    const LevelHost &h = plan->lh[level];
+    const LevelDev &L = plan->dev.lev[level];
+    info[0] = L.nbox;
+    info[1] = 0;
+    info[2] = level >= 3 ? h.ncous : 0;
+    info[3] = level >= 3 ? L.nact : 0;
+    info[4] = level >= 3 ? L.ns : 0;
+    info[5] = level >= 3 ? L.nc : 0;
+    info[6] = level >= 3 ? h.cousin_evals : 0;
+    info[7] = level >= 4 ? h.upward_evals : 0;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_get_perm(const ifgf_plan *plan, int64_t *perm)
+{
+    if (!plan || !perm) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    return copy_i32_as_i64((ifgf_plan *)plan, plan->dev.perm, plan->n, perm);
+}
+
+extern "C" ifgf_status ifgf_plan_get_boxes(const ifgf_plan *plan, int level, uint64_t *keys, int64_t *start)
+{
+    if (!level_ok(plan, level, 1) || !keys || !start) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    if (cudaMemcpy(keys, L.key, (size_t)L.nbox * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IFGF_ECUDA;
+    return copy_i32_as_i64((ifgf_plan *)plan, L.start, L.nbox + 1, start);
+}
+
+extern "C" ifgf_status ifgf_plan_get_cousins(const ifgf_plan *plan, int level, int64_t *start, int64_t *list)
+{
+    if (!level_ok(plan, level, 3) || !start || !list) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    ifgf_status s = copy_i32_as_i64((ifgf_plan *)plan, L.cous_start, L.nbox + 1, start);
+    if (s != IFGF_OK) return s;
+    return copy_i32_as_i64((ifgf_plan *)plan, L.cous, plan->lh[level].ncous, list);
+}
+
+extern "C" ifgf_status ifgf_plan_get_active(const ifgf_plan *plan, int level, int64_t *start, int64_t *cones)
+{
+    if (!level_ok(plan, level, 3) || !start || !cones) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    ifgf_status s = copy_i32_as_i64((ifgf_plan *)plan, L.act_start, L.nbox + 1, start);
+    if (s != IFGF_OK) return s;
+    return copy_i32_as_i64((ifgf_plan *)plan, L.act_cone, L.nact, cones);
+}
+
+extern "C" ifgf_status ifgf_plan_get_values(const ifgf_plan *plan, int level, void *out)
+{
+    if (!level_ok(plan, level, 3) || !out) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    size_t bytes = (size_t)L.nact * plan->P * plan->last_nrhs * ifgf_elem_bytes(plan->precision);
+    if (bytes && cudaMemcpy(out, L.F, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return IFGF_ECUDA;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_geometry(const ifgf_plan *plan, double *geom)
+{
+    if (!plan || !geom) return IFGF_EINVAL;
+    geom[0] = plan->H1;
+    geom[1] = plan->corner[0];
+    geom[2] = plan->corner[1];
+    geom[3] = plan->corner[2];
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t cap)
+{
+    if (!plan || !buf || cap == 0) return IFGF_EINVAL;
+    std::string s = "{";
+    char tmp[512];
+    snprintf(tmp, sizeof tmp,
+             "\"n\": %lld, \"levels\": %d, \"P\": %d, \"kappa\": %.17g, \"precision\": %d, \"max_nrhs\": %d, "
+             "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, \"level\": [",
+             (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
+             (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes);
+    s += tmp;
+    for (int d = 1; d <= plan->D; ++d) {
+        const LevelHost &h = plan->lh[d];
+        const LevelDev &L = plan->dev.lev[d];
+        snprintf(tmp, sizeof tmp,
+                 "%s{\"d\": %d, \"nbox\": %d, \"ncous\": %lld, \"nact\": %d, \"ns\": %d, \"nc\": %d, "
+                 "\"cousin_evals\": %lld, \"upward_evals\": %lld}",
+                 d > 1 ? ", " : "", d, L.nbox, (long long)h.ncous, d >= 3 ? L.nact : 0, d >= 3 ? L.ns : 0,
+                 d >= 3 ? L.nc : 0, (long long)h.cousin_evals, (long long)h.upward_evals);
+        s += tmp;
+    }
+    s += "]}";
+    if (s.size() + 1 > cap) return IFGF_EINVAL;
+    memcpy(buf, s.c_str(), s.size() + 1);
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors)
+{
+    if (!plan || !device_errors) return IFGF_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        plan->last_error = "device synchronisation failed";
+        return IFGF_ECUDA;
+    }
+    int h = 0;
+    if (cudaMemcpy(&h, plan->dev.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return IFGF_ECUDA;
+    if (cudaMemset(plan->dev.err, 0, sizeof(int)) != cudaSuccess) return IFGF_ECUDA;
+    *device_errors = h;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on)
+{
+    if (!plan) return IFGF_EINVAL;
+    if (on && !plan->timer.ev[0]) {
+        for (int i = 0; i < 64; ++i)
+            if (cudaEventCreate(&plan->timer.ev[i]) != cudaSuccess) {
+                plan->last_error = "event creation failed";
+                return IFGF_ECUDA;
+            }
+    }
+    plan->timer.on = on != 0;
+    for (int s = 0; s < STAGE_COUNT; ++s) {
+        plan->stage_ms[s] = 0;
+        plan->stage_launches[s] = 0;
+    }
+    plan->stage_calls = 0;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_timings(const ifgf_plan *plan, double *ms, int64_t *launches, int64_t *calls,
+                                         int count)
+{
+    if (!plan || !ms || !launches || !calls || count < STAGE_COUNT) return IFGF_EINVAL;
+    for (int s = 0; s < STAGE_COUNT; ++s) {
+        ms[s] = plan->stage_ms[s];
+        launches[s] = plan->stage_launches[s];
+    }
+    *calls = plan->stage_calls;
+    return IFGF_OK;
+}
+
+extern "C" const char *ifgf_last_error(const ifgf_plan *plan)
+{
+    if (!plan) return g_create_error.c_str();
+    return plan->last_error.c_str();
+}

@@ -1,0 +1,10 @@
+// Mixed-precision instantiation of the evaluation kernels (IFGF_MIXED plans): FP64
+// geometry and phase arguments, FP32 values, interpolation and accumulation.
+#include "ifgf_apply_impl.cuh"
+
+cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user, void *out_user,
+                               void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
+                               StageTimer &tm)
+{
+    return ifgf::run_typed<float>(pd, nrhs, in_user, out_user, in_sorted, out_sorted, mode, adjoint, st, tm);
+}

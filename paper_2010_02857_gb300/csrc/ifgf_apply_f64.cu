@@ -1,0 +1,9 @@
+// FP64 instantiation of the evaluation kernels (IFGF_FP64 plans).
+#include "ifgf_apply_impl.cuh"
+
+cudaError_t ifgf_run_typed_f64(const PlanDev &pd, int nrhs, const void *in_user, void *out_user,
+                               void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
+                               StageTimer &tm)
+{
+    return ifgf::run_typed<double>(pd, nrhs, in_user, out_user, in_sorted, out_sorted, mode, adjoint, st, tm);
+}

@@ -1,0 +1,551 @@
+// Evaluation kernels of the IFGF method (Algorithm 1, evaluation stage) and of its
+// exact adjoint, templated on the value type T (double: all-FP64; float: FP64
+// geometry and phase arguments, FP32 interpolation and accumulation), on the
+// number R of right-hand sides a thread carries, and on the interpolation orders
+// (PS, PA) = (P_s, P_ang).
+//
+// Forward (u = A sigma), all in pull form so every output has one writer and a
+// fixed summation order (bitwise reproducible, no atomics):
+//   k_leaf    F_k^D at the interpolation points of every relevant leaf cone
+//             (Eq. I_k with d = D): one thread per (cone, point).
+//   k_upward  F_j^{d-1} at the parent cones' interpolation points from the children's
+//             interpolants, re-centred by G(x, x_k^d) / G(x, x_j^{d-1}): one thread
+//             per (parent cone, point), looping over the children.
+//   k_eval    per target: level-D direct sums over neighbouring boxes (skipping the
+//             self term) plus, for d = D..3, interpolation from every cousin box's
+//             cone times G(x, x_k^d).
+// Adjoint (w = A^H v), same data, transposed:
+//   k_adj_level  per relevant cone slot of level d (one warp per slot): conjugated
+//             contributions of the cousin targets that read the slot and of the
+//             parent interpolation points that read it (lists built at plan time).
+//   k_adj_eval   per source: conjugated direct sums plus conj(g) of its leaf's cone
+//             values.
+#pragma once
+
+#include "ifgf_device.cuh"
+
+namespace ifgf {
+
+constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
+
+template <typename T> struct Vec { using type = double2; };
+template <> struct Vec<float> { using type = float2; };
+
+template <typename T> __device__ __forceinline__ cpx<T> ld(const void *base, size_t i)
+{
+    if constexpr (sizeof(T) == 8) {
+        double2 v = __ldg((const double2 *)base + i);
+        return {v.x, v.y};
+    } else {
+        float2 v = __ldg((const float2 *)base + i);
+        return {v.x, v.y};
+    }
+}
+template <typename T> __device__ __forceinline__ void st(void *base, size_t i, cpx<T> v)
+{
+    if constexpr (sizeof(T) == 8) ((double2 *)base)[i] = make_double2(v.x, v.y);
+    else ((float2 *)base)[i] = make_float2(v.x, v.y);
+}
+
+// Lagrange weights of the three local coordinates
+template <typename T, int PS, int PA>
+__device__ __forceinline__ void weights3(const PlanDev &pd, const double *loc, T *ws, T *wt, T *wp)
+{
+    lagrange<T>(PS, pd.ts, pd.its, (T)loc[0], ws);
+    lagrange<T>(PA, pd.ta, pd.ita, (T)loc[1], wt);
+    lagrange<T>(PA, pd.ta, pd.ita, (T)loc[2], wp);
+}
+
+// sum_{a,b,c} ws[a] wt[b] wp[c] F[(a PA + b) PA + c][r], sum-factorised (phi, theta, s)
+template <typename T, int R, int PS, int PA>
+__device__ __forceinline__ void contract(const void *F, size_t base, int nrhs, int r0, const T *ws,
+                                         const T *wt, const T *wp, cpx<T> *out)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = {T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < PS; ++a) {
+        cpx<T> mid[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) mid[r] = {T(0), T(0)};
+#pragma unroll
+        for (int b = 0; b < PA; ++b) {
+            cpx<T> in[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) in[r] = {T(0), T(0)};
+#pragma unroll
+            for (int c = 0; c < PA; ++c) {
+                size_t idx = (base + (size_t)((a * PA + b) * PA + c)) * nrhs + r0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (R == 1 || r0 + r < nrhs) {
+                        cpx<T> f = ld<T>(F, idx + r);
+                        in[r].x += wp[c] * f.x;
+                        in[r].y += wp[c] * f.y;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) { mid[r].x += wt[b] * in[r].x; mid[r].y += wt[b] * in[r].y; }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) { out[r].x += ws[a] * mid[r].x; out[r].y += ws[a] * mid[r].y; }
+    }
+}
+
+// e^{i kappa r} / (4 pi r)
+template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, double r)
+{
+    T c, s;
+    expi(kappa * r, c, s);
+    T a = (T)(kInv4Pi / r);
+    return {a * c, a * s};
+}
+
+// Re-centring factor G(q, x_k) / G(q, x_j) = (r_j / r_k) e^{i kappa (r_k - r_j)} for the
+// interpolation point q = x_j + Rj dir, child centre x_k = x_j + delta, r_k = |q - x_k|.
+// r_k - r_j = (|delta|^2 - 2 Rj dir.delta) / (r_k + r_j) avoids the cancellation of
+// the plain difference.
+template <typename T>
+__device__ __forceinline__ cpx<T> recentre(double kappa, double Rj, const double *dir, double rk,
+                                           double dx, double dy, double dz)
+{
+    double dd = dx * dx + dy * dy + dz * dz;
+    double yd = dir[0] * dx + dir[1] * dy + dir[2] * dz;
+    double diff = (dd - 2.0 * Rj * yd) / (rk + Rj);
+    T c, s;
+    expi(kappa * diff, c, s);
+    T a = (T)(Rj / rk);
+    return {a * c, a * s};
+}
+
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_permute_in(const void *in, void *out, const int *perm, int n, int nrhs)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    int i = (int)(t / nrhs), r = (int)(t % nrhs);
+    st<T>(out, t, ld<T>(in, (size_t)r * n + perm[i]));
+}
+
+template <typename T>
+__global__ void k_permute_out(const void *in, void *out, const int *perm, int n, int nrhs)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    int i = (int)(t / nrhs), r = (int)(t % nrhs);
+    st<T>(out, (size_t)r * n + perm[i], ld<T>(in, t));
+}
+
+// ---------------------------------------------------------------------------------
+// Leaf level: F_k^D(q) = sum_{x' in B_k} sigma(x') |q - x_k| / |q - x'| e^{i kappa (|q - x'| - |q - x_k|)}
+// ---------------------------------------------------------------------------------
+template <typename T, int R, int PS, int PA>
+__global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int nrhs, const void *sig)
+{
+    constexpr int P = PS * PA * PA;
+    const LevelDev &L = pd.lev[pd.D];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)L.nact * P) return;
+    int slot = (int)(t / P), node = (int)(t % P);
+    int b = L.act_box[slot];
+    const double *c = L.center + 3 * (size_t)b;
+    double q[3];
+    double R0 = node_pos(L, PS, PA, L.act_cone[slot], node, c[0], c[1], c[2], q, nullptr);
+    const int j0 = L.start[b], j1 = L.start[b + 1];
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        cpx<T> acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
+        for (int j = j0; j < j1; ++j) {
+            double dx = q[0] - pd.xs[j], dy = q[1] - pd.ys[j], dz = q[2] - pd.zs[j];
+            double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+            T cc, ss;
+            expi(pd.kappa * (r1 - R0), cc, ss);
+            T a = (T)(R0 / r1);
+            cpx<T> g = {a * cc, a * ss};
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (R == 1 || r0 + r < nrhs) {
+                    cpx<T> s = ld<T>(sig, (size_t)j * nrhs + r0 + r);
+                    cpx<T> m = cmul(s, g);
+                    acc[r].x += m.x;
+                    acc[r].y += m.y;
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r0 + r < nrhs) st<T>(L.F, ((size_t)slot * P + node) * nrhs + r0 + r, acc[r]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Upward step d -> d-1 (d > 3)
+// ---------------------------------------------------------------------------------
+template <typename T, int R, int PS, int PA>
+__global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
+{
+    constexpr int P = PS * PA * PA;
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Lp.nact * P) return;
+    int slot = (int)(t / P), node = (int)(t % P);
+    int j = Lp.act_box[slot];
+    const double *cj = Lp.center + 3 * (size_t)j;
+    double q[3], dir[3];
+    double Rj = node_pos(Lp, PS, PA, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, dir);
+    const int k0 = Lp.child_start[j], k1 = Lp.child_start[j + 1];
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        cpx<T> acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
+        for (int k = k0; k < k1; ++k) {
+            const double *ck = L.center + 3 * (size_t)k;
+            double vx = __dsub_rn(q[0], ck[0]), vy = __dsub_rn(q[1], ck[1]), vz = __dsub_rn(q[2], ck[2]);
+            ConeGeom g = cone_of(L, vx, vy, vz);
+            int sl = cone_slot(L, k, g.cone);
+            if (sl < 0) { atomicAdd(pd.err, 1); continue; }
+            double loc[3];
+            local_coords(L, g, vx, vy, vz, loc);
+            T ws[PS], wt[PA], wp[PA];
+            weights3<T, PS, PA>(pd, loc, ws, wt, wp);
+            cpx<T> val[R];
+            contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, ws, wt, wp, val);
+            cpx<T> f = recentre<T>(pd.kappa, Rj, dir, g.r, ck[0] - cj[0], ck[1] - cj[1], ck[2] - cj[2]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cpx<T> m = cmul(f, val[r]);
+                acc[r].x += m.x;
+                acc[r].y += m.y;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r0 + r < nrhs) st<T>(Lp.F, ((size_t)slot * P + node) * nrhs + r0 + r, acc[r]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Targets: near field + interpolation from every cousin box of every level
+// ---------------------------------------------------------------------------------
+template <typename T, int R, int PS, int PA>
+__global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *sig, void *us, int mode)
+{
+    constexpr int P = PS * PA * PA;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+    const LevelDev &LD = pd.lev[pd.D];
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        cpx<T> acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
+        if (mode & 1) {
+            int b = LD.pt_box[i];
+            for (int e = 0; e < 27; ++e) {
+                int k = LD.nbr[27 * (size_t)b + e];
+                if (k < 0) break;
+                for (int j = LD.start[k]; j < LD.start[k + 1]; ++j) {
+                    if (j == i) continue;
+                    double dx = x - pd.xs[j], dy = y - pd.ys[j], dz = z - pd.zs[j];
+                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    cpx<T> G = green_r<T>(pd.kappa, r1);
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r0 + r < nrhs) {
+                            cpx<T> m = cmul(G, ld<T>(sig, (size_t)j * nrhs + r0 + r));
+                            acc[r].x += m.x;
+                            acc[r].y += m.y;
+                        }
+                }
+            }
+        }
+        if (mode & 2) {
+            for (int d = pd.D; d >= 3; --d) {
+                const LevelDev &L = pd.lev[d];
+                int b = L.pt_box[i];
+                for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
+                    int k = L.cous[e];
+                    const double *ck = L.center + 3 * (size_t)k;
+                    double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
+                    ConeGeom g = cone_of(L, vx, vy, vz);
+                    int sl = cone_slot(L, k, g.cone);
+                    if (sl < 0) { atomicAdd(pd.err, 1); continue; }
+                    double loc[3];
+                    local_coords(L, g, vx, vy, vz, loc);
+                    T ws[PS], wt[PA], wp[PA];
+                    weights3<T, PS, PA>(pd, loc, ws, wt, wp);
+                    cpx<T> val[R];
+                    contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, ws, wt, wp, val);
+                    cpx<T> G = green_r<T>(pd.kappa, g.r);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        cpx<T> m = cmul(G, val[r]);
+                        acc[r].x += m.x;
+                        acc[r].y += m.y;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r0 + r < nrhs) st<T>(us, (size_t)i * nrhs + r0 + r, acc[r]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint: cone slots of level d gather from their readers (one warp per slot).
+// ---------------------------------------------------------------------------------
+constexpr int kAdjWarps = 4;
+
+template <typename T, int R, int PS, int PA>
+__global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d, int nrhs, const void *vs, int mode)
+{
+    constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
+    constexpr int NPL = (P + 31) / 32;  // nodes per lane
+    __shared__ T sw[kAdjWarps][32][NW];
+    __shared__ cpx<T> sc[kAdjWarps][32][R];
+    const LevelDev &L = pd.lev[d];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kAdjWarps + warp;
+    const int nwarps = gridDim.x * kAdjWarps;
+    for (int slot = gw; slot < L.nact; slot += nwarps) {
+        const int k = L.act_box[slot];
+        const double *ck = L.center + 3 * (size_t)k;
+        for (int r0 = 0; r0 < nrhs; r0 += R) {
+            cpx<T> acc[NPL][R];
+#pragma unroll
+            for (int h = 0; h < NPL; ++h)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[h][r] = {T(0), T(0)};
+            for (int pass = 0; pass < 2; ++pass) {
+                const int *lst;
+                int e_begin, e_end;
+                if (pass == 0) {
+                    lst = L.tl;
+                    e_begin = L.tl_start[slot];
+                    e_end = L.tl_start[slot + 1];
+                } else {
+                    if (d <= 3 || !(mode & 2)) break;
+                    lst = L.ul;
+                    e_begin = L.ul_start[slot];
+                    e_end = L.ul_start[slot + 1];
+                }
+                for (int e0 = e_begin; e0 < e_end; e0 += 32) {
+                    int e = e0 + lane;
+                    if (e < e_end) {
+                        int item = lst[e];
+                        double px, py, pz;
+                        double Rj = 0, dir[3] = {0, 0, 0};
+                        const double *cj = nullptr;
+                        int psl = 0, pnode = 0;
+                        if (pass == 0) {
+                            px = pd.xs[item]; py = pd.ys[item]; pz = pd.zs[item];
+                        } else {
+                            const LevelDev &Lp = pd.lev[d - 1];
+                            psl = item / P;
+                            pnode = item % P;
+                            int j = Lp.act_box[psl];
+                            cj = Lp.center + 3 * (size_t)j;
+                            double q[3];
+                            Rj = node_pos(Lp, PS, PA, Lp.act_cone[psl], pnode, cj[0], cj[1], cj[2], q, dir);
+                            px = q[0]; py = q[1]; pz = q[2];
+                        }
+                        double vx = __dsub_rn(px, ck[0]), vy = __dsub_rn(py, ck[1]), vz = __dsub_rn(pz, ck[2]);
+                        ConeGeom g = cone_of(L, vx, vy, vz);
+                        double loc[3];
+                        local_coords(L, g, vx, vy, vz, loc);
+                        T w[NW];
+                        weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+#pragma unroll
+                        for (int m = 0; m < NW; ++m) sw[warp][lane][m] = w[m];
+                        cpx<T> f;
+                        if (pass == 0) f = cconj(green_r<T>(pd.kappa, g.r));
+                        else f = cconj(recentre<T>(pd.kappa, Rj, dir, g.r, ck[0] - cj[0], ck[1] - cj[1], ck[2] - cj[2]));
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            cpx<T> src = {T(0), T(0)};
+                            if (R == 1 || r0 + r < nrhs) {
+                                if (pass == 0) src = ld<T>(vs, (size_t)item * nrhs + r0 + r);
+                                else src = ld<T>(pd.lev[d - 1].Fadj, ((size_t)psl * P + pnode) * nrhs + r0 + r);
+                            }
+                            sc[warp][lane][r] = cmul(f, src);
+                        }
+                    }
+                    __syncwarp();
+                    int cnt = min(32, e_end - e0);
+                    for (int m = 0; m < cnt; ++m) {
+#pragma unroll
+                        for (int h = 0; h < NPL; ++h) {
+                            int p = lane + 32 * h;
+                            if (p < P) {
+                                int a = p / (PA * PA), b = (p / PA) % PA, c = p % PA;
+                                T w = sw[warp][m][a] * sw[warp][m][PS + b] * sw[warp][m][PS + PA + c];
+#pragma unroll
+                                for (int r = 0; r < R; ++r) {
+                                    acc[h][r].x += w * sc[warp][m][r].x;
+                                    acc[h][r].y += w * sc[warp][m][r].y;
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < NPL; ++h) {
+                int p = lane + 32 * h;
+                if (p < P)
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r0 + r < nrhs) st<T>(L.Fadj, ((size_t)slot * P + p) * nrhs + r0 + r, acc[h][r]);
+            }
+        }
+    }
+}
+
+// Adjoint per source: conjugated neighbour sums + conj(g(q, x')) times the leaf cones' adjoint values.
+template <typename T, int R, int PS, int PA>
+__global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const void *vs, void *ws, int mode)
+{
+    constexpr int P = PS * PA * PA;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= pd.n) return;
+    const double x = pd.xs[j], y = pd.ys[j], z = pd.zs[j];
+    const LevelDev &LD = pd.lev[pd.D];
+    const int b = LD.pt_box[j];
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        cpx<T> acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
+        if (mode & 1) {
+            for (int e = 0; e < 27; ++e) {
+                int k = LD.nbr[27 * (size_t)b + e];
+                if (k < 0) break;
+                for (int i = LD.start[k]; i < LD.start[k + 1]; ++i) {
+                    if (i == j) continue;
+                    double dx = pd.xs[i] - x, dy = pd.ys[i] - y, dz = pd.zs[i] - z;
+                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    cpx<T> G = cconj(green_r<T>(pd.kappa, r1));
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r0 + r < nrhs) {
+                            cpx<T> m = cmul(G, ld<T>(vs, (size_t)i * nrhs + r0 + r));
+                            acc[r].x += m.x;
+                            acc[r].y += m.y;
+                        }
+                }
+            }
+        }
+        if (mode & 2) {
+            const double *c = LD.center + 3 * (size_t)b;
+            for (int slot = LD.act_start[b]; slot < LD.act_start[b + 1]; ++slot) {
+                int cone = LD.act_cone[slot];
+                for (int node = 0; node < P; ++node) {
+                    double q[3];
+                    double R0 = node_pos(LD, PS, PA, cone, node, c[0], c[1], c[2], q, nullptr);
+                    double dx = q[0] - x, dy = q[1] - y, dz = q[2] - z;
+                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    T cc, ss;
+                    expi(pd.kappa * (r1 - R0), cc, ss);
+                    T a = (T)(R0 / r1);
+                    cpx<T> g = {a * cc, -a * ss};
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r0 + r < nrhs) {
+                            cpx<T> m = cmul(g, ld<T>(LD.Fadj, ((size_t)slot * P + node) * nrhs + r0 + r));
+                            acc[r].x += m.x;
+                            acc[r].y += m.y;
+                        }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r0 + r < nrhs) st<T>(ws, (size_t)j * nrhs + r0 + r, acc[r]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Host launcher
+// ---------------------------------------------------------------------------------
+inline int grid_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T, int R, int PS, int PA>
+cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *us, int mode, cudaStream_t st,
+                           StageTimer &tm)
+{
+    constexpr int P = PS * PA * PA;
+    if (mode & 2) {
+        const LevelDev &L = pd.lev[pd.D];
+        int64_t nt = (int64_t)L.nact * P;
+        if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
+        tm.mark(STAGE_LEAF, nt > 0, st);
+        int nl = 0;
+        for (int d = pd.D; d >= 4; --d) {
+            int64_t np = (int64_t)pd.lev[d - 1].nact * P;
+            if (np > 0) { k_upward<T, R, PS, PA><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs); ++nl; }
+        }
+        tm.mark(STAGE_UPWARD, nl, st);
+    }
+    k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
+    tm.mark(STAGE_EVAL, 1, st);
+    return cudaGetLastError();
+}
+
+template <typename T, int R, int PS, int PA>
+cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws, int mode, cudaStream_t st,
+                           StageTimer &tm)
+{
+    if (mode & 2) {
+        int nl = 0;
+        for (int d = 3; d <= pd.D; ++d) {
+            int nact = pd.lev[d].nact;
+            if (nact == 0) continue;
+            int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+            k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode);
+            ++nl;
+        }
+        tm.mark(STAGE_ADJ_LEVEL, nl, st);
+    }
+    k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, mode);
+    tm.mark(STAGE_ADJ_EVAL, 1, st);
+    return cudaGetLastError();
+}
+
+template <typename T, int PS, int PA>
+cudaError_t launch_orders(const PlanDev &pd, int nrhs, const void *in, void *out, int mode, int adjoint,
+                          cudaStream_t st, StageTimer &tm)
+{
+    if (nrhs == 1) {
+        return adjoint ? launch_adjoint<T, 1, PS, PA>(pd, nrhs, in, out, mode, st, tm)
+                       : launch_forward<T, 1, PS, PA>(pd, nrhs, in, out, mode, st, tm);
+    }
+    constexpr int RB = sizeof(T) == 8 ? 4 : 8;
+    return adjoint ? launch_adjoint<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm)
+                   : launch_forward<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm);
+}
+
+// entry used by the per-type translation units
+template <typename T>
+cudaError_t run_typed(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
+                      void *out_sorted, int mode, int adjoint, cudaStream_t st, StageTimer &tm)
+{
+    int64_t tot = (int64_t)pd.n * nrhs;
+    tm.mark(-1, 0, st);
+    k_permute_in<T><<<grid_for(tot, 256), 256, 0, st>>>(in_user, in_sorted, pd.perm, pd.n, nrhs);
+    tm.mark(STAGE_PERMUTE_IN, 1, st);
+    cudaError_t e;
+    if (pd.Ps == 3 && pd.Pang == 5) e = launch_orders<T, 3, 5>(pd, nrhs, in_sorted, out_sorted, mode, adjoint, st, tm);
+    else if (pd.Ps == 4 && pd.Pang == 7) e = launch_orders<T, 4, 7>(pd, nrhs, in_sorted, out_sorted, mode, adjoint, st, tm);
+    else return cudaErrorInvalidValue;
+    if (e != cudaSuccess) return e;
+    k_permute_out<T><<<grid_for(tot, 256), 256, 0, st>>>(out_sorted, out_user, pd.perm, pd.n, nrhs);
+    tm.mark(STAGE_PERMUTE_OUT, 1, st);
+    return cudaGetLastError();
+}
+
+}  // namespace ifgf

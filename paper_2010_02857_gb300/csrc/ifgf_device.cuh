@@ -1,0 +1,176 @@
+// Device helpers shared by the plan and apply kernels.
+//
+// Index path (box coordinates, cone cells, interpolation-point positions): only
+// correctly rounded double operations (__dadd_rn, __dsub_rn, __dmul_rn,
+// __ddiv_rn, __dsqrt_rn) in a fixed order, never contracted into FMAs, and
+// trigonometric values only from host-computed tables.  This makes every box
+// and cone index a deterministic function of the input bits.
+#pragma once
+
+#include <cstdint>
+
+#include "ifgf_internal.h"
+
+namespace ifgf {
+
+template <typename T> struct cpx { T x, y; };
+
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
+
+// ----------------------------------------------------------------------------------
+// Cone cell of the vector v = y - c at level L (cells of Eq. defconedomain and
+// defconedomainproduct).  Cells are half-open; the theta cell is the number of
+// k in 1..n_C-1 with v_z/r <= cos(k pi/n_C); the phi cell is found the same way
+// from v_x/rho on [0, pi] (v_y >= 0) and on (pi, 2 pi) (v_y < 0, where the cell
+// boundaries are -cos(k pi/n_C)).  On the axis (rho == 0) the pole rule of
+// Eq. (defconedomain) applies: theta = 0 lies in the first phi cell, theta = pi
+// in the last.  Returns the linear id (g1 n_C + g2) 2 n_C + g3 and the
+// quantities that the local coordinates need.
+// ----------------------------------------------------------------------------------
+struct ConeGeom {
+    double r, rho, s_over_ds;   // distance, distance to the axis, s / Delta_s
+    int g1, g2, g3;
+    int cone;
+};
+
+__device__ __forceinline__ ConeGeom cone_of(const LevelDev &L, double vx, double vy, double vz)
+{
+    ConeGeom o;
+    double rho2 = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
+    double r = __dsqrt_rn(__dadd_rn(rho2, __dmul_rn(vz, vz)));
+    double rho = __dsqrt_rn(rho2);
+    o.r = r;
+    o.rho = rho;
+    const int nc = L.nc, ns = L.ns;
+    if (r == 0.0) {
+        o.g1 = o.g2 = o.g3 = 0;
+        o.s_over_ds = 0.0;
+    } else {
+        double s = __ddiv_rn(L.h, r);
+        double q = __ddiv_rn(s, L.ds);
+        o.s_over_ds = q;
+        double fq = floor(q);
+        o.g1 = fq < 0.0 ? 0 : (fq > (double)(ns - 1) ? ns - 1 : (int)fq);
+        double ct = __ddiv_rn(vz, r);
+        // cosk is strictly decreasing: count k in [1, nc-1] with ct <= cosk[k]
+        int lo = 1, hi = nc;  // answer m in [0, nc-1]: cosk[1..m] >= ct
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (ct <= L.cosk[mid]) lo = mid + 1; else hi = mid;
+        }
+        o.g2 = lo - 1;
+        if (rho == 0.0) {
+            o.g3 = vz > 0.0 ? 0 : 2 * nc - 1;
+        } else {
+            double cp = __ddiv_rn(vx, rho);
+            if (vy >= 0.0) {
+                // count j in [1, nc] with cp <= cosk[j]
+                int a = 1, b = nc + 1;
+                while (a < b) {
+                    int mid = (a + b) >> 1;
+                    if (cp <= L.cosk[mid]) a = mid + 1; else b = mid;
+                }
+                o.g3 = a - 1;
+            } else {
+                // nc + count j in [1, nc-1] with cp >= -cosk[j]  (-cosk increasing)
+                int a = 1, b = nc;
+                while (a < b) {
+                    int mid = (a + b) >> 1;
+                    if (cp >= -L.cosk[mid]) a = mid + 1; else b = mid;
+                }
+                o.g3 = nc + a - 1;
+            }
+        }
+    }
+    o.cone = (o.g1 * nc + o.g2) * (2 * nc) + o.g3;
+    return o;
+}
+
+// Local coordinates in [-1, 1] of (s, theta, phi) inside the cell (value path).
+__device__ __forceinline__ void local_coords(const LevelDev &L, const ConeGeom &g, double vx,
+                                             double vy, double vz, double *t)
+{
+    t[0] = 2.0 * (g.s_over_ds - (double)g.g1) - 1.0;
+    double th = atan2(g.rho, vz);
+    t[1] = 2.0 * (th / L.dth - (double)g.g2) - 1.0;
+    if (g.rho == 0.0) {
+        t[2] = 0.0;
+    } else {
+        double ph = atan2(vy, vx);
+        if (ph < 0.0) ph += 6.283185307179586476925286766559;
+        t[2] = 2.0 * (ph / L.dth - (double)g.g3) - 1.0;
+    }
+}
+
+// Interpolation point `node` = (a, b, c) of cone `cone` around centre (cx, cy, cz),
+// Eq. (interp_pts): centre + (h/s_a) (sin th_b cos ph_c, sin th_b sin ph_c, cos th_b).
+// Exact-rounding order; returns the radius h/s_a and the unit direction.
+__device__ __forceinline__ double node_pos(const LevelDev &L, int Ps, int Pang, int cone, int node,
+                                           double cx, double cy, double cz, double *q, double *dir)
+{
+    const int nc = L.nc;
+    int g3 = cone % (2 * nc);
+    int g2 = (cone / (2 * nc)) % nc;
+    int g1 = cone / (2 * nc) / nc;
+    int a = node / (Pang * Pang), b = (node / Pang) % Pang, c = node % Pang;
+    double R = L.nodeR[g1 * Ps + a];
+    double st = L.sth[g2 * Pang + b], ct = L.cth[g2 * Pang + b];
+    double sp = L.sph[g3 * Pang + c], cp = L.cph[g3 * Pang + c];
+    double dx = __dmul_rn(st, cp), dy = __dmul_rn(st, sp);
+    q[0] = __dadd_rn(cx, __dmul_rn(R, dx));
+    q[1] = __dadd_rn(cy, __dmul_rn(R, dy));
+    q[2] = __dadd_rn(cz, __dmul_rn(R, ct));
+    if (dir) { dir[0] = dx; dir[1] = dy; dir[2] = ct; }
+    return R;
+}
+
+// Slot of cone id `cone` of box b via the bitmap rank directory; -1 if not relevant.
+__device__ __forceinline__ int cone_slot(const LevelDev &L, int b, int cone)
+{
+    size_t w = (size_t)b * L.words + (cone >> 6);
+    uint64_t word = L.bits[w];
+    uint64_t bit = 1ull << (cone & 63);
+    if (!(word & bit)) return -1;
+    return L.rank[w] + __popcll(word & (bit - 1));
+}
+
+// Lagrange basis at the first-kind Chebyshev nodes: w_a = inv_a prod_{e != a}(t - t_e).
+template <typename W>
+__device__ __forceinline__ void lagrange(int n, const double *nodes, const double *inv, W t, W *w)
+{
+    W d[IFGF_MAX_P];
+#pragma unroll
+    for (int e = 0; e < IFGF_MAX_P; ++e)
+        if (e < n) d[e] = t - (W)nodes[e];
+#pragma unroll
+    for (int a = 0; a < IFGF_MAX_P; ++a) {
+        if (a < n) {
+            W v = (W)inv[a];
+#pragma unroll
+            for (int e = 0; e < IFGF_MAX_P; ++e)
+                if (e < n && e != a) v *= d[e];
+            w[a] = v;
+        }
+    }
+}
+
+// exp(i arg) with the argument in FP64: full FP64 sincos for double results; for
+// float results the argument is reduced modulo 2 pi in FP64 (Cody-Waite, two-part
+// 2 pi) and the reduced angle goes to FP32 sincos.
+__device__ __forceinline__ void expi(double arg, double &c, double &s) { sincos(arg, &s, &c); }
+__device__ __forceinline__ void expi(double arg, float &c, float &s)
+{
+    const double inv2pi = 0.15915494309189533577;
+    const double twopi_hi = 6.283185307179586232;      // nearest double to 2 pi
+    const double twopi_lo = 2.4492935982947064e-16;    // 2 pi - twopi_hi
+    double k = rint(arg * inv2pi);
+    double red = fma(-k, twopi_hi, arg);
+    red = fma(-k, twopi_lo, red);
+    sincosf((float)red, &s, &c);
+}
+
+}  // namespace ifgf

@@ -1,0 +1,147 @@
+// Internal data structures of the IFGF library (host and device views).
+//
+// Layout in device memory (one plan):
+//   points, Morton order:  xs, ys, zs            double [N]
+//   perm                   int32 [N]             sorted position -> caller index
+//   per level d = 1..D:
+//     key[nbox]            uint64  Morton key of the box's integer coordinate
+//     start[nbox+1]        int32   point range of the box (Morton order)
+//     pt_box[N]            int32   box of every sorted point
+//     parent[nbox]         int32   box at level d-1
+//     child_start[nbox+1]  int32   children at level d+1 form a contiguous range
+//     nbr[nbox][27]        int32   neighbours (Sec. 3.3.1), ascending, -1 padded
+//     center[nbox][3]      double  x_k^d (Eq. defboxsizesandcenters)
+//   per level d = 3..D (cone levels):
+//     cous_start/cous      int32   CSR cousin lists (Eq. defcousinboxes)
+//     tables               double  cos(k pi/n_C), node radii h/s_a, sin/cos of the
+//                                  theta and phi interpolation nodes
+//     bits[nbox][words]    uint64  relevant-cone bitmap (Eq. defallrelevantconesegments)
+//     rank[nbox][words]    int32   slot of the first cone of each bitmap word
+//     act_start/act_cone/act_box   relevant cones in (box, cone id) order
+//     F[nact][P][nrhs]     complex values of F_k^d at the interpolation points
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ifgf.h"
+
+#define IFGF_MAX_LEVELS 20
+#define IFGF_MAX_P 8
+
+struct LevelDev {
+    int nbox = 0;
+    int ns = 0, nc = 0;     // cone grid n_{s,d}, n_{C,d}
+    int ncone = 0;          // n_s * n_C * 2 n_C
+    int words = 0;          // bitmap words per box
+    int nact = 0;           // relevant cones at this level
+    double H = 0, h = 0, ds = 0, dth = 0;
+    const uint64_t *key = nullptr;
+    const int *start = nullptr;
+    const int *pt_box = nullptr;
+    const int *parent = nullptr;
+    const int *child_start = nullptr;
+    const int *nbr = nullptr;          // [nbox][27]
+    const int *cous_start = nullptr;
+    const int *cous = nullptr;
+    const double *center = nullptr;    // [nbox][3]
+    const double *cosk = nullptr;      // [nc+1]
+    const double *nodeR = nullptr;     // [ns*Ps]
+    const double *sth = nullptr, *cth = nullptr;  // [nc*Pang]
+    const double *sph = nullptr, *cph = nullptr;  // [2nc*Pang]
+    const uint64_t *bits = nullptr;    // [nbox*words]
+    const int *rank = nullptr;         // [nbox*words]
+    const int *act_start = nullptr;    // [nbox+1]
+    const int *act_cone = nullptr;     // [nact]
+    const int *act_box = nullptr;      // [nact]
+    void *F = nullptr;                 // forward values
+    void *Fadj = nullptr;              // adjoint values
+    const int *tl_start = nullptr;     // adjoint: per slot, cousin targets landing in it
+    const int *tl = nullptr;
+    const int *ul_start = nullptr;     // adjoint: per slot, parent (slot*P + node) landing in it
+    const int *ul = nullptr;
+};
+
+struct PlanDev {
+    int n = 0, D = 0, Ps = 0, Pang = 0, P = 0;
+    double kappa = 0;
+    double ts[IFGF_MAX_P] = {}, ta[IFGF_MAX_P] = {};    // Chebyshev nodes
+    double its[IFGF_MAX_P] = {}, ita[IFGF_MAX_P] = {};  // 1 / prod_{e != a} (t_a - t_e)
+    const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
+    const int *perm = nullptr;
+    int *err = nullptr;                                  // device invariant-failure counter
+    LevelDev lev[IFGF_MAX_LEVELS + 1];
+};
+
+// Per-stage CUDA-event timing of one call (enabled by ifgf_plan_set_profiling).
+enum IfgfStage {
+    STAGE_PERMUTE_IN = 0, STAGE_LEAF, STAGE_UPWARD, STAGE_EVAL, STAGE_PERMUTE_OUT,
+    STAGE_ADJ_LEVEL, STAGE_ADJ_EVAL, STAGE_COUNT
+};
+
+struct StageTimer {
+    bool on = false;
+    int n = 0;
+    cudaEvent_t ev[64] = {};
+    int stage[64] = {};
+    int launches[64] = {};
+    void mark(int s, int nlaunch, cudaStream_t st)
+    {
+        if (!on || n >= 64) return;
+        cudaEventRecord(ev[n], st);
+        stage[n] = s;
+        launches[n] = nlaunch;
+        ++n;
+    }
+};
+
+struct LevelHost {
+    int64_t nbox = 0, nnbr = 0, ncous = 0, nact = 0;
+    int ns = 0, nc = 0;
+    int64_t cousin_evals = 0, upward_evals = 0;
+    int64_t words = 0;
+};
+
+struct ifgf_plan {
+    int64_t n = 0;
+    int D = 0, Ps = 0, Pang = 0, P = 0;
+    double kappa = 0;
+    int precision = IFGF_FP64;
+    int max_nrhs = 1;
+    int flags = 0;
+    double H1 = 0, corner[3] = {0, 0, 0};
+    PlanDev dev;
+    LevelHost lh[IFGF_MAX_LEVELS + 1];
+    int64_t near_pairs = 0;
+    int64_t leaf_evals = 0;
+    double build_ms = 0;
+    size_t device_bytes = 0;
+    std::vector<void *> allocs;
+    void *sig_sorted = nullptr;   // [N][max_nrhs] complex
+    void *u_sorted = nullptr;     // [N][max_nrhs] complex
+    void *stage_in = nullptr;     // staging for host-pointer calls
+    void *stage_out = nullptr;
+    bool adjoint_ready = false;
+    int last_nrhs = 1;
+    cudaStream_t build_stream = nullptr;
+    std::string last_error;
+    StageTimer timer;
+    double stage_ms[STAGE_COUNT] = {};
+    int64_t stage_launches[STAGE_COUNT] = {};
+    int64_t stage_calls = 0;
+};
+
+// complex element size of the plan's data type
+inline size_t ifgf_elem_bytes(int precision) { return precision == IFGF_FP64 ? 16 : 8; }
+
+// plan.cu
+ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
+ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
+void *ifgf_dalloc(ifgf_plan *p, size_t bytes);
+// apply.cu
+ifgf_status ifgf_run_apply(ifgf_plan *p, const void *sigma, void *u, int nrhs, int mode,
+                           int adjoint, cudaStream_t st);

@@ -1,0 +1,908 @@
+// Plan construction on the GPU: the pre-computation stage of Algorithm 1.
+//
+//   root cube -> leaf integer coordinates -> Morton keys -> stable radix sort
+//   -> per-level relevant boxes (unique keys), parents, children, centres
+//   -> neighbours (Sec. 3.3.1) and cousins (Eq. defcousinboxes)
+//   -> relevant cone segments, top-down d = 3..D (Sec. 3.3.2): rule (i) cousin
+//      surface points, rule (ii) interpolation points of the parent's relevant
+//      cones; deduplicated in a per-box bitmap, numbered by a rank directory.
+//
+// Radix sort and prefix sums use CUB (the CUDA toolkit's header library); every
+// other step is a kernel in this file.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <chrono>
+
+#include <cub/cub.cuh>
+
+#include "ifgf_device.cuh"
+
+using namespace ifgf;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(int64_t n, int t = kThreads)
+{
+    int64_t b = (n + t - 1) / t;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 30));
+}
+
+// ---------------------------------------------------------------------------------
+// Root cube: componentwise min/max and finiteness.
+// ---------------------------------------------------------------------------------
+__global__ void k_bbox_partial(const double *pts, int n, double *part, int *bad)
+{
+    __shared__ double smin[3][kThreads], smax[3][kThreads];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int c = 0; c < 3; ++c) {
+            double v = pts[3 * (size_t)i + c];
+            if (!isfinite(v)) atomicAdd(bad, 1);
+            lo[c] = fmin(lo[c], v);
+            hi[c] = fmax(hi[c], v);
+        }
+    }
+    for (int c = 0; c < 3; ++c) { smin[c][threadIdx.x] = lo[c]; smax[c][threadIdx.x] = hi[c]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) {
+                smin[c][threadIdx.x] = fmin(smin[c][threadIdx.x], smin[c][threadIdx.x + s]);
+                smax[c][threadIdx.x] = fmax(smax[c][threadIdx.x], smax[c][threadIdx.x + s]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            part[6 * blockIdx.x + c] = smin[c][0];
+            part[6 * blockIdx.x + 3 + c] = smax[c][0];
+        }
+}
+
+__global__ void k_bbox_final(const double *part, int nb, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], part[6 * b + c]);
+            hi[c] = fmax(hi[c], part[6 * b + 3 + c]);
+        }
+    for (int c = 0; c < 3; ++c) { out[c] = lo[c]; out[3 + c] = hi[c]; }
+}
+
+// ---------------------------------------------------------------------------------
+// Leaf integer coordinate k = clamp(floor((x - corner) / H_D), 0, 2^{D-1}-1), Morton key.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+__device__ __forceinline__ uint64_t compact3(uint64_t v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return v;
+}
+
+__global__ void k_morton(const double *pts, int n, double c0, double c1, double c2, double HD,
+                         int nside, uint64_t *key, int *idx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double cr[3] = {c0, c1, c2};
+    uint64_t k[3];
+    for (int c = 0; c < 3; ++c) {
+        double q = floor(__ddiv_rn(__dsub_rn(pts[3 * (size_t)i + c], cr[c]), HD));
+        k[c] = q < 0.0 ? 0 : (q > (double)(nside - 1) ? (uint64_t)(nside - 1) : (uint64_t)q);
+    }
+    key[i] = spread3(k[0]) | (spread3(k[1]) << 1) | (spread3(k[2]) << 2);
+    idx[i] = i;
+}
+
+__global__ void k_gather_points(const double *pts, const int *idx, int n, double *xs, double *ys,
+                                double *zs, int *perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j = idx[i];
+    xs[i] = pts[3 * (size_t)j];
+    ys[i] = pts[3 * (size_t)j + 1];
+    zs[i] = pts[3 * (size_t)j + 2];
+    perm[i] = j;
+}
+
+// box boundaries of level d: flag[i] = 1 where the level key changes
+__global__ void k_level_flags(const uint64_t *leafkey, int n, int shift, int *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (i == 0 || (leafkey[i] >> shift) != (leafkey[i - 1] >> shift)) ? 1 : 0;
+}
+
+// pt_box = inclusive scan - 1; scatter box starts and keys
+__global__ void k_level_boxes(const uint64_t *leafkey, const int *incl, int n, int shift, int *pt_box,
+                              int *start, uint64_t *key)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = incl[i] - 1;
+    pt_box[i] = b;
+    if (i == 0 || incl[i - 1] != incl[i]) {
+        start[b] = i;
+        key[b] = leafkey[i] >> shift;
+    }
+    if (i == n - 1) start[b + 1] = n;
+}
+
+__global__ void k_parents(const int *start, int nbox, const int *pt_box_parent, int *parent)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    parent[b] = pt_box_parent[start[b]];
+}
+
+// children of parent box p (level d-1) are the contiguous level-d boxes with parent p
+__global__ void k_child_start(const int *parent, int nbox, int nparent, int *child_start)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    if (b == 0 || parent[b] != parent[b - 1]) child_start[parent[b]] = b;
+    if (b == nbox - 1) child_start[nparent] = nbox;
+}
+
+// x_k^d = corner + (k + 1/2) H_d   (Eq. defboxsizesandcenters, 0-based k)
+__global__ void k_centers(const uint64_t *key, int nbox, double c0, double c1, double c2, double H,
+                          double *center)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    uint64_t kk = key[b];
+    double cr[3] = {c0, c1, c2};
+    for (int c = 0; c < 3; ++c) {
+        double k = (double)compact3(kk >> c);
+        center[3 * (size_t)b + c] = __dadd_rn(cr[c], __dmul_rn(k + 0.5, H));
+    }
+}
+
+__device__ __forceinline__ int find_key(const uint64_t *keys, int n, uint64_t key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == key) ? lo : -1;
+}
+
+// neighbours N B: relevant boxes a with |a - k|_inf <= 1 (including k), ascending
+__global__ void k_neighbours(const uint64_t *key, int nbox, int side, int *nbr)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    uint64_t kk = key[b];
+    int k[3] = {(int)compact3(kk), (int)compact3(kk >> 1), (int)compact3(kk >> 2)};
+    int list[27];
+    int m = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int a0 = k[0] + dx, a1 = k[1] + dy, a2 = k[2] + dz;
+                if (a0 < 0 || a1 < 0 || a2 < 0 || a0 >= side || a1 >= side || a2 >= side) continue;
+                uint64_t ck = spread3(a0) | (spread3(a1) << 1) | (spread3(a2) << 2);
+                int f = find_key(key, nbox, ck);
+                if (f >= 0) {
+                    int j = m++;
+                    while (j > 0 && list[j - 1] > f) { list[j] = list[j - 1]; --j; }
+                    list[j] = f;
+                }
+            }
+    for (int j = 0; j < 27; ++j) nbr[27 * (size_t)b + j] = j < m ? list[j] : -1;
+}
+
+// cousins M B (Eq. defcousinboxes): children of the parent's neighbours that are
+// not neighbours of B.  Parents' neighbours are ascending and children ranges are
+// ordered by parent, so the list comes out ascending.
+template <bool FILL>
+__global__ void k_cousins(const uint64_t *key, int nbox, const int *parent, const int *pnbr,
+                          const int *pchild_start, int *count, const int *cstart, int *cous)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    uint64_t kk = key[b];
+    int k[3] = {(int)compact3(kk), (int)compact3(kk >> 1), (int)compact3(kk >> 2)};
+    int p = parent[b];
+    int m = 0;
+    int out = FILL ? cstart[b] : 0;
+    for (int e = 0; e < 27; ++e) {
+        int q = pnbr[27 * (size_t)p + e];
+        if (q < 0) break;
+        for (int c = pchild_start[q]; c < pchild_start[q + 1]; ++c) {
+            uint64_t ck = key[c];
+            int a0 = (int)compact3(ck), a1 = (int)compact3(ck >> 1), a2 = (int)compact3(ck >> 2);
+            int dd = max(abs(a0 - k[0]), max(abs(a1 - k[1]), abs(a2 - k[2])));
+            if (dd > 1) {
+                if (FILL) cous[out + m] = c;
+                ++m;
+            }
+        }
+    }
+    if (!FILL) count[b] = m;
+}
+
+// ---------------------------------------------------------------------------------
+// Relevant cones (Sec. 3.3.2).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void set_bit(uint64_t *bits, int words, int box, int cone)
+{
+    atomicOr((unsigned long long *)&bits[(size_t)box * words + (cone >> 6)], 1ull << (cone & 63));
+}
+
+// rule (i): every cousin surface point of box k marks its cone around x_k.
+// Written per point over the boxes that have it as a cousin point (the cousin
+// relation is symmetric).
+__global__ void k_activate_cousins(PlanDev pd, int d, uint64_t *bits)
+{
+    const LevelDev &L = pd.lev[d];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+    int b = L.pt_box[i];
+    for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
+        int k = L.cous[e];
+        const double *c = L.center + 3 * (size_t)k;
+        ConeGeom g = cone_of(L, __dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2]));
+        set_bit(bits, L.words, k, g.cone);
+    }
+}
+
+// rule (ii): every interpolation point of a relevant parent cone marks its cone
+// around each child centre.
+__global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
+{
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Lp.nact * pd.P) return;
+    int slot = (int)(t / pd.P), node = (int)(t % pd.P);
+    int j = Lp.act_box[slot];
+    const double *cj = Lp.center + 3 * (size_t)j;
+    double q[3];
+    node_pos(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, nullptr);
+    for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k) {
+        const double *c = L.center + 3 * (size_t)k;
+        ConeGeom g = cone_of(L, __dsub_rn(q[0], c[0]), __dsub_rn(q[1], c[1]), __dsub_rn(q[2], c[2]));
+        set_bit(bits, L.words, k, g.cone);
+    }
+}
+
+__global__ void k_popc(const uint64_t *bits, int64_t nw, int *cnt)
+{
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) cnt[w] = __popcll(bits[w]);
+}
+
+__global__ void k_expand(const uint64_t *bits, const int *rank, int64_t nw, int words, int *act_cone,
+                         int *act_box)
+{
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    uint64_t v = bits[w];
+    int s = rank[w];
+    int box = (int)(w / words);
+    int base = (int)(w % words) * 64;
+    while (v) {
+        int j = __ffsll((long long)v) - 1;
+        act_cone[s] = base + j;
+        act_box[s] = box;
+        ++s;
+        v &= v - 1;
+    }
+}
+
+__global__ void k_act_start(const int *rank, int nbox, int words, int nact, int *act_start)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbox) return;
+    act_start[b] = b < nbox ? rank[(size_t)b * words] : nact;
+}
+
+// statistics: cousin evaluations = sum over points of the cousin count of their box
+__global__ void k_count_cousin_evals(PlanDev pd, int d, unsigned long long *acc)
+{
+    const LevelDev &L = pd.lev[d];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < pd.n) {
+        int b = L.pt_box[i];
+        v = (unsigned long long)(L.cous_start[b + 1] - L.cous_start[b]);
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+__global__ void k_count_near(PlanDev pd, unsigned long long *acc)
+{
+    const LevelDev &L = pd.lev[pd.D];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < pd.n) {
+        int b = L.pt_box[i];
+        for (int e = 0; e < 27; ++e) {
+            int k = L.nbr[27 * (size_t)b + e];
+            if (k < 0) break;
+            v += (unsigned long long)(L.start[k + 1] - L.start[k]);
+        }
+        v -= 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+__global__ void k_count_upward(PlanDev pd, int d, unsigned long long *acc)
+{
+    const LevelDev &Lp = pd.lev[d - 1];
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (s < Lp.nact) {
+        int j = Lp.act_box[s];
+        v = (unsigned long long)(Lp.child_start[j + 1] - Lp.child_start[j]) * pd.P;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+__global__ void k_count_leaf(PlanDev pd, unsigned long long *acc)
+{
+    const LevelDev &L = pd.lev[pd.D];
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (s < L.nact) {
+        int b = L.act_box[s];
+        v = (unsigned long long)(L.start[b + 1] - L.start[b]) * pd.P;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
+}
+
+// ---------------------------------------------------------------------------------
+// Transpose lists for the adjoint.
+// ---------------------------------------------------------------------------------
+
+// (slot, target) pairs of all cousin evaluations of level d; offsets from a scan
+// of the per-point cousin counts.
+__global__ void k_emit_tlist(PlanDev pd, int d, const int *off, int *keys, int *vals)
+{
+    const LevelDev &L = pd.lev[d];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+    int b = L.pt_box[i];
+    int o = off[i];
+    for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e, ++o) {
+        int k = L.cous[e];
+        const double *c = L.center + 3 * (size_t)k;
+        ConeGeom g = cone_of(L, __dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2]));
+        int sl = cone_slot(L, k, g.cone);
+        if (sl < 0) { atomicAdd(pd.err, 1); sl = 0; }
+        keys[o] = sl;
+        vals[o] = i;
+    }
+}
+
+__global__ void k_point_cousin_count(PlanDev pd, int d, int *cnt)
+{
+    const LevelDev &L = pd.lev[d];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    int b = L.pt_box[i];
+    cnt[i] = L.cous_start[b + 1] - L.cous_start[b];
+}
+
+__global__ void k_parent_slot_count(PlanDev pd, int d, int *cnt)
+{
+    const LevelDev &Lp = pd.lev[d - 1];
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= Lp.nact) return;
+    int j = Lp.act_box[s];
+    cnt[s] = (Lp.child_start[j + 1] - Lp.child_start[j]) * pd.P;
+}
+
+// (child slot, parent slot * P + node) pairs of all upward evaluations of level d
+__global__ void k_emit_ulist(PlanDev pd, int d, const int *off, int *keys, int *vals)
+{
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Lp.nact * pd.P) return;
+    int slot = (int)(t / pd.P), node = (int)(t % pd.P);
+    int j = Lp.act_box[slot];
+    int nch = Lp.child_start[j + 1] - Lp.child_start[j];
+    const double *cj = Lp.center + 3 * (size_t)j;
+    double q[3];
+    node_pos(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, nullptr);
+    int o = off[slot] + node * nch;
+    for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k, ++o) {
+        const double *c = L.center + 3 * (size_t)k;
+        ConeGeom g = cone_of(L, __dsub_rn(q[0], c[0]), __dsub_rn(q[1], c[1]), __dsub_rn(q[2], c[2]));
+        int sl = cone_slot(L, k, g.cone);
+        if (sl < 0) { atomicAdd(pd.err, 1); sl = 0; }
+        keys[o] = sl;
+        vals[o] = (int)t;
+    }
+}
+
+// CSR starts from sorted keys: start[s] = first position with key >= s
+__global__ void k_csr_from_sorted(const int *keys, int64_t m, int nslot, int *start)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > nslot) return;
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < s) lo = mid + 1; else hi = mid;
+    }
+    start[s] = (int)lo;
+}
+
+}  // namespace
+
+// ===================================================================================
+// Host orchestration
+// ===================================================================================
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            p->last_error = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;          \
+        }                                                                                 \
+    } while (0)
+
+void *ifgf_dalloc(ifgf_plan *p, size_t bytes)
+{
+    void *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    p->allocs.push_back(ptr);
+    p->device_bytes += bytes;
+    return ptr;
+}
+
+template <typename T> static T *dalloc(ifgf_plan *p, size_t count)
+{
+    return (T *)ifgf_dalloc(p, count * sizeof(T));
+}
+
+#define DALLOC(var, T, count)                                                        \
+    T *var = dalloc<T>(p, (size_t)(count));                                          \
+    if (!var) {                                                                      \
+        p->last_error = "device allocation failed (" #var ")";                      \
+        return IFGF_ENOMEM;                                                          \
+    }
+
+// temporary device buffer freed at scope exit
+struct Scratch {
+    void *ptr = nullptr;
+    ~Scratch() { if (ptr) cudaFree(ptr); }
+    bool alloc(size_t bytes)
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        return cudaMalloc(&ptr, bytes ? bytes : 16) == cudaSuccess;
+    }
+};
+
+static ifgf_status cub_inclusive_sum(ifgf_plan *p, const int *in, int *out, int64_t n, cudaStream_t st)
+{
+    size_t bytes = 0;
+    CK(cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, n, st));
+    Scratch tmp;
+    if (!tmp.alloc(bytes)) { p->last_error = "scan scratch"; return IFGF_ENOMEM; }
+    CK(cub::DeviceScan::InclusiveSum(tmp.ptr, bytes, in, out, n, st));
+    CK(cudaStreamSynchronize(st));
+    return IFGF_OK;
+}
+
+static ifgf_status cub_exclusive_sum(ifgf_plan *p, const int *in, int *out, int64_t n, cudaStream_t st)
+{
+    size_t bytes = 0;
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, st));
+    Scratch tmp;
+    if (!tmp.alloc(bytes)) { p->last_error = "scan scratch"; return IFGF_ENOMEM; }
+    CK(cub::DeviceScan::ExclusiveSum(tmp.ptr, bytes, in, out, n, st));
+    CK(cudaStreamSynchronize(st));
+    return IFGF_OK;
+}
+
+static inline double cheb_node(int k, int n)
+{
+    return cos(((double)(2 * k + 1) * M_PI) / (double)(2 * n));
+}
+
+ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = (int)p->n, D = p->D, Ps = p->Ps, Pang = p->Pang, P = p->P;
+    PlanDev &pd = p->dev;
+    pd.n = n; pd.D = D; pd.Ps = Ps; pd.Pang = Pang; pd.P = P; pd.kappa = p->kappa;
+    for (int a = 0; a < Ps; ++a) pd.ts[a] = cheb_node(a, Ps);
+    for (int a = 0; a < Pang; ++a) pd.ta[a] = cheb_node(a, Pang);
+    for (int a = 0; a < Ps; ++a) {
+        double v = 1.0;
+        for (int e = 0; e < Ps; ++e) if (e != a) v *= pd.ts[a] - pd.ts[e];
+        pd.its[a] = 1.0 / v;
+    }
+    for (int a = 0; a < Pang; ++a) {
+        double v = 1.0;
+        for (int e = 0; e < Pang; ++e) if (e != a) v *= pd.ta[a] - pd.ta[e];
+        pd.ita[a] = 1.0 / v;
+    }
+    DALLOC(d_err, int, 1);
+    CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    pd.err = d_err;
+
+    // points to the device (AoS, caller order)
+    Scratch pts;
+    if (!pts.alloc((size_t)n * 3 * sizeof(double))) { p->last_error = "points scratch"; return IFGF_ENOMEM; }
+    CK(cudaMemcpyAsync(pts.ptr, points, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault, st));
+    const double *dpts = (const double *)pts.ptr;
+
+    // root cube (reading: bounding cube of the points, centred at the bbox midpoint)
+    {
+        int nb = std::min(nblocks(n), 1024);
+        Scratch part, out;
+        if (!part.alloc((size_t)nb * 6 * sizeof(double)) || !out.alloc(6 * sizeof(double) + sizeof(int)))
+            return IFGF_ENOMEM;
+        int *bad = (int *)((double *)out.ptr + 6);
+        CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        k_bbox_partial<<<nb, kThreads, 0, st>>>(dpts, n, (double *)part.ptr, bad);
+        k_bbox_final<<<1, 32, 0, st>>>((double *)part.ptr, nb, (double *)out.ptr);
+        CK(cudaGetLastError());
+        double h[6];
+        int hbad = 0;
+        CK(cudaMemcpyAsync(h, out.ptr, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hbad) { p->last_error = "non-finite point coordinates"; return IFGF_EINVAL; }
+        double H1 = 0.0;
+        for (int c = 0; c < 3; ++c)
+            if (h[3 + c] - h[c] > H1) H1 = h[3 + c] - h[c];
+        if (!(H1 > 0.0)) { p->last_error = "all points coincide"; return IFGF_EINVAL; }
+        p->H1 = H1;
+        for (int c = 0; c < 3; ++c) p->corner[c] = (h[c] + h[3 + c]) * 0.5 - H1 * 0.5;
+    }
+    double Hd[IFGF_MAX_LEVELS + 1];
+    for (int d = 1; d <= D; ++d) Hd[d] = ldexp(p->H1, -(d - 1));
+
+    // Morton keys and stable sort (ties keep the caller order)
+    DALLOC(xs, double, n);
+    DALLOC(ys, double, n);
+    DALLOC(zs, double, n);
+    DALLOC(perm, int, n);
+    pd.xs = xs; pd.ys = ys; pd.zs = zs; pd.perm = perm;
+    Scratch keyA, keyB, idxA, idxB;
+    if (!keyA.alloc((size_t)n * 8) || !keyB.alloc((size_t)n * 8) || !idxA.alloc((size_t)n * 4) ||
+        !idxB.alloc((size_t)n * 4)) {
+        p->last_error = "sort scratch";
+        return IFGF_ENOMEM;
+    }
+    k_morton<<<nblocks(n), kThreads, 0, st>>>(dpts, n, p->corner[0], p->corner[1], p->corner[2], Hd[D],
+                                              1 << (D - 1), (uint64_t *)keyA.ptr, (int *)idxA.ptr);
+    CK(cudaGetLastError());
+    {
+        size_t bytes = 0;
+        CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, (uint64_t *)keyA.ptr, (uint64_t *)keyB.ptr,
+                                           (int *)idxA.ptr, (int *)idxB.ptr, n, 0, 3 * (D - 1), st));
+        Scratch tmp;
+        if (!tmp.alloc(bytes)) { p->last_error = "sort temp"; return IFGF_ENOMEM; }
+        CK(cub::DeviceRadixSort::SortPairs(tmp.ptr, bytes, (uint64_t *)keyA.ptr, (uint64_t *)keyB.ptr,
+                                           (int *)idxA.ptr, (int *)idxB.ptr, n, 0, 3 * (D - 1), st));
+    }
+    const uint64_t *leafkey = (const uint64_t *)keyB.ptr;
+    k_gather_points<<<nblocks(n), kThreads, 0, st>>>(dpts, (int *)idxB.ptr, n, xs, ys, zs, perm);
+    CK(cudaGetLastError());
+
+    // relevant boxes of every level
+    Scratch flag, incl;
+    if (!flag.alloc((size_t)n * 4) || !incl.alloc((size_t)n * 4)) return IFGF_ENOMEM;
+    for (int d = 1; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        int shift = 3 * (D - d);
+        k_level_flags<<<nblocks(n), kThreads, 0, st>>>(leafkey, n, shift, (int *)flag.ptr);
+        CK(cudaGetLastError());
+        ifgf_status s = cub_inclusive_sum(p, (int *)flag.ptr, (int *)incl.ptr, n, st);
+        if (s != IFGF_OK) return s;
+        int nbox = 0;
+        CK(cudaMemcpy(&nbox, (int *)incl.ptr + (n - 1), sizeof(int), cudaMemcpyDeviceToHost));
+        L.nbox = nbox;
+        p->lh[d].nbox = nbox;
+        DALLOC(pt_box, int, n);
+        DALLOC(start, int, nbox + 1);
+        DALLOC(key, uint64_t, nbox);
+        k_level_boxes<<<nblocks(n), kThreads, 0, st>>>(leafkey, (int *)incl.ptr, n, shift, pt_box, start, key);
+        CK(cudaGetLastError());
+        L.pt_box = pt_box; L.start = start; L.key = key;
+        L.H = Hd[d];
+        DALLOC(center, double, 3 * (size_t)nbox);
+        k_centers<<<nblocks(nbox), kThreads, 0, st>>>(key, nbox, p->corner[0], p->corner[1], p->corner[2],
+                                                      Hd[d], center);
+        CK(cudaGetLastError());
+        L.center = center;
+        DALLOC(nbr, int, 27 * (size_t)nbox);
+        k_neighbours<<<nblocks(nbox), kThreads, 0, st>>>(key, nbox, 1 << (d - 1), nbr);
+        CK(cudaGetLastError());
+        L.nbr = nbr;
+    }
+    for (int d = 2; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        LevelDev &Lp = pd.lev[d - 1];
+        DALLOC(parent, int, L.nbox);
+        k_parents<<<nblocks(L.nbox), kThreads, 0, st>>>(L.start, L.nbox, Lp.pt_box, parent);
+        DALLOC(cstart, int, Lp.nbox + 1);
+        k_child_start<<<nblocks(L.nbox), kThreads, 0, st>>>(parent, L.nbox, Lp.nbox, cstart);
+        CK(cudaGetLastError());
+        L.parent = parent;
+        Lp.child_start = cstart;
+    }
+    // cousins of levels 3..D
+    for (int d = 3; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        LevelDev &Lp = pd.lev[d - 1];
+        Scratch cnt;
+        if (!cnt.alloc((size_t)(L.nbox + 1) * 4)) return IFGF_ENOMEM;
+        CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(L.nbox + 1) * 4, st));
+        k_cousins<false><<<nblocks(L.nbox), kThreads, 0, st>>>(L.key, L.nbox, L.parent, Lp.nbr,
+                                                               Lp.child_start, (int *)cnt.ptr, nullptr, nullptr);
+        CK(cudaGetLastError());
+        DALLOC(cstart, int, L.nbox + 1);
+        ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, cstart, L.nbox + 1, st);
+        if (s != IFGF_OK) return s;
+        int total = 0;
+        CK(cudaMemcpy(&total, cstart + L.nbox, sizeof(int), cudaMemcpyDeviceToHost));
+        DALLOC(cous, int, total);
+        k_cousins<true><<<nblocks(L.nbox), kThreads, 0, st>>>(L.key, L.nbox, L.parent, Lp.nbr,
+                                                              Lp.child_start, nullptr, cstart, cous);
+        CK(cudaGetLastError());
+        L.cous_start = cstart;
+        L.cous = cous;
+        p->lh[d].ncous = total;
+    }
+
+    // cone levels: n_{.,d-1} = a_d n_{.,d}, a_d = 2 iff 2 kappa H_d > 1
+    int ns[IFGF_MAX_LEVELS + 1], nc[IFGF_MAX_LEVELS + 1];
+    ns[D] = p->lh[D].ns;
+    nc[D] = p->lh[D].nc;
+    for (int d = D; d >= 4; --d) {
+        int a = (2.0 * p->kappa * Hd[d] > 1.0) ? 2 : 1;
+        ns[d - 1] = a * ns[d];
+        nc[d - 1] = a * nc[d];
+    }
+    const double eta = sqrt(3.0) / 3.0;
+    for (int d = 3; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        int64_t ncone64 = (int64_t)ns[d] * nc[d] * 2 * nc[d];
+        if (ncone64 >= (int64_t)1 << 30) {
+            p->last_error = "too many cone cells per box at level " + std::to_string(d);
+            return IFGF_EINVAL;
+        }
+        L.ns = ns[d]; L.nc = nc[d]; L.ncone = (int)ncone64;
+        L.words = (L.ncone + 63) / 64;
+        L.h = sqrt(3.0) * 0.5 * Hd[d];
+        L.ds = eta / (double)ns[d];
+        L.dth = M_PI / (double)nc[d];
+        p->lh[d].ns = ns[d];
+        p->lh[d].nc = nc[d];
+        p->lh[d].words = L.words;
+        std::vector<double> tab;
+        size_t o_cosk = tab.size();
+        for (int k = 0; k <= nc[d]; ++k) tab.push_back(cos(((double)k * M_PI) / (double)nc[d]));
+        size_t o_R = tab.size();
+        for (int g = 0; g < ns[d]; ++g)
+            for (int a = 0; a < Ps; ++a) {
+                double s = L.ds * ((double)g + (1.0 + pd.ts[a]) * 0.5);
+                tab.push_back(L.h / s);
+            }
+        size_t o_sth = tab.size();
+        for (int g = 0; g < nc[d]; ++g)
+            for (int b = 0; b < Pang; ++b) tab.push_back(sin(L.dth * ((double)g + (1.0 + pd.ta[b]) * 0.5)));
+        size_t o_cth = tab.size();
+        for (int g = 0; g < nc[d]; ++g)
+            for (int b = 0; b < Pang; ++b) tab.push_back(cos(L.dth * ((double)g + (1.0 + pd.ta[b]) * 0.5)));
+        size_t o_sph = tab.size();
+        for (int g = 0; g < 2 * nc[d]; ++g)
+            for (int c = 0; c < Pang; ++c) tab.push_back(sin(L.dth * ((double)g + (1.0 + pd.ta[c]) * 0.5)));
+        size_t o_cph = tab.size();
+        for (int g = 0; g < 2 * nc[d]; ++g)
+            for (int c = 0; c < Pang; ++c) tab.push_back(cos(L.dth * ((double)g + (1.0 + pd.ta[c]) * 0.5)));
+        DALLOC(dtab, double, tab.size());
+        CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        L.cosk = dtab + o_cosk; L.nodeR = dtab + o_R;
+        L.sth = dtab + o_sth; L.cth = dtab + o_cth; L.sph = dtab + o_sph; L.cph = dtab + o_cph;
+    }
+
+    // relevant cones, top-down
+    for (int d = 3; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        int64_t nw = (int64_t)L.nbox * L.words;
+        DALLOC(bits, uint64_t, nw);
+        DALLOC(rank, int, nw + 1);
+        CK(cudaMemsetAsync(bits, 0, nw * sizeof(uint64_t), st));
+        L.bits = bits;
+        L.rank = rank;
+        k_activate_cousins<<<nblocks(n), kThreads, 0, st>>>(pd, d, bits);
+        CK(cudaGetLastError());
+        if (d >= 4) {
+            int64_t nt = (int64_t)pd.lev[d - 1].nact * P;
+            k_activate_parent<<<nblocks(nt), kThreads, 0, st>>>(pd, d, bits);
+            CK(cudaGetLastError());
+        }
+        Scratch cnt;
+        if (!cnt.alloc((size_t)(nw + 1) * 4)) return IFGF_ENOMEM;
+        CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nw + 1) * 4, st));
+        k_popc<<<nblocks(nw), kThreads, 0, st>>>(bits, nw, (int *)cnt.ptr);
+        CK(cudaGetLastError());
+        ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, rank, nw + 1, st);
+        if (s != IFGF_OK) return s;
+        int nact = 0;
+        CK(cudaMemcpy(&nact, rank + nw, sizeof(int), cudaMemcpyDeviceToHost));
+        L.nact = nact;
+        p->lh[d].nact = nact;
+        DALLOC(act_cone, int, nact);
+        DALLOC(act_box, int, nact);
+        DALLOC(act_start, int, L.nbox + 1);
+        k_expand<<<nblocks(nw), kThreads, 0, st>>>(bits, rank, nw, L.words, act_cone, act_box);
+        k_act_start<<<nblocks(L.nbox + 1), kThreads, 0, st>>>(rank, L.nbox, L.words, nact, act_start);
+        CK(cudaGetLastError());
+        L.act_cone = act_cone; L.act_box = act_box; L.act_start = act_start;
+    }
+
+    // statistics of one apply
+    {
+        Scratch acc;
+        if (!acc.alloc(sizeof(unsigned long long) * (IFGF_MAX_LEVELS + 4))) return IFGF_ENOMEM;
+        unsigned long long *a = (unsigned long long *)acc.ptr;
+        CK(cudaMemsetAsync(a, 0, sizeof(unsigned long long) * (IFGF_MAX_LEVELS + 4), st));
+        for (int d = 3; d <= D; ++d) k_count_cousin_evals<<<nblocks(n), kThreads, 0, st>>>(pd, d, a + d);
+        k_count_near<<<nblocks(n), kThreads, 0, st>>>(pd, a + 0);
+        k_count_leaf<<<nblocks(pd.lev[D].nact), kThreads, 0, st>>>(pd, a + 1);
+        CK(cudaGetLastError());
+        unsigned long long h[IFGF_MAX_LEVELS + 4];
+        CK(cudaMemcpyAsync(h, a, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        p->near_pairs = (int64_t)h[0];
+        p->leaf_evals = (int64_t)h[1];
+        for (int d = 3; d <= D; ++d) p->lh[d].cousin_evals = (int64_t)h[d];
+        CK(cudaMemsetAsync(a, 0, sizeof(unsigned long long) * (IFGF_MAX_LEVELS + 4), st));
+        for (int d = 4; d <= D; ++d)
+            k_count_upward<<<nblocks(pd.lev[d - 1].nact), kThreads, 0, st>>>(pd, d, a + d);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h, a, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int d = 4; d <= D; ++d) p->lh[d].upward_evals = (int64_t)h[d];
+    }
+
+    // value buffers
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    for (int d = 3; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        size_t bytes = (size_t)L.nact * P * p->max_nrhs * eb;
+        L.F = ifgf_dalloc(p, bytes);
+        if (!L.F) { p->last_error = "cone value buffer"; return IFGF_ENOMEM; }
+    }
+    p->sig_sorted = ifgf_dalloc(p, (size_t)n * p->max_nrhs * eb);
+    p->u_sorted = ifgf_dalloc(p, (size_t)n * p->max_nrhs * eb);
+    if (!p->sig_sorted || !p->u_sorted) { p->last_error = "sorted density buffers"; return IFGF_ENOMEM; }
+    CK(cudaStreamSynchronize(st));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, pd.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { p->last_error = "plan build: internal invariant failed"; return IFGF_EINTERNAL; }
+    p->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return IFGF_OK;
+}
+
+// Transpose lists for the adjoint: for every relevant cone slot of level d, the
+// cousin targets whose interpolation reads it, and the parent interpolation points
+// (parent slot * P + node) whose upward interpolation reads it; both in ascending
+// order within a slot (stable radix sort by slot).
+static ifgf_status sort_to_csr(ifgf_plan *p, int *keys, int *vals, int64_t m, int nslot, int **start_out,
+                               int **list_out, cudaStream_t st)
+{
+    DALLOC(list, int, m);
+    DALLOC(start, int, nslot + 1);
+    Scratch kb;
+    if (!kb.alloc((size_t)m * 4)) { p->last_error = "adjoint list sort"; return IFGF_ENOMEM; }
+    int end_bit = 1;
+    while (end_bit < 31 && (1 << end_bit) <= nslot) ++end_bit;
+    size_t bytes = 0;
+    CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
+    Scratch tmp;
+    if (!tmp.alloc(bytes)) { p->last_error = "adjoint list sort temp"; return IFGF_ENOMEM; }
+    CK(cub::DeviceRadixSort::SortPairs(tmp.ptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
+    k_csr_from_sorted<<<nblocks(nslot + 1), kThreads, 0, st>>>((int *)kb.ptr, m, nslot, start);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    *start_out = start;
+    *list_out = list;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
+{
+    if (p->adjoint_ready) return IFGF_OK;
+    PlanDev &pd = p->dev;
+    const int n = (int)p->n, D = p->D, P = p->P;
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    for (int d = 3; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        L.Fadj = ifgf_dalloc(p, (size_t)L.nact * P * p->max_nrhs * eb);
+        if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
+        // targets
+        {
+            Scratch cnt, off;
+            if (!cnt.alloc((size_t)(n + 1) * 4) || !off.alloc((size_t)(n + 1) * 4)) return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(n + 1) * 4, st));
+            k_point_cousin_count<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+            CK(cudaGetLastError());
+            ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, n + 1, st);
+            if (s != IFGF_OK) return s;
+            int m = 0;
+            CK(cudaMemcpy(&m, (int *)off.ptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+            Scratch keys, vals;
+            if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+            k_emit_tlist<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)off.ptr, (int *)keys.ptr, (int *)vals.ptr);
+            CK(cudaGetLastError());
+            int *start = nullptr, *list = nullptr;
+            s = sort_to_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, &start, &list, st);
+            if (s != IFGF_OK) return s;
+            L.tl_start = start;
+            L.tl = list;
+        }
+        if (d >= 4) {
+            LevelDev &Lp = pd.lev[d - 1];
+            Scratch cnt, off;
+            if (!cnt.alloc((size_t)(Lp.nact + 1) * 4) || !off.alloc((size_t)(Lp.nact + 1) * 4)) return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(Lp.nact + 1) * 4, st));
+            k_parent_slot_count<<<nblocks(Lp.nact), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+            CK(cudaGetLastError());
+            ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, Lp.nact + 1, st);
+            if (s != IFGF_OK) return s;
+            int m = 0;
+            CK(cudaMemcpy(&m, (int *)off.ptr + Lp.nact, sizeof(int), cudaMemcpyDeviceToHost));
+            Scratch keys, vals;
+            if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+            int64_t nt = (int64_t)Lp.nact * P;
+            k_emit_ulist<<<nblocks(nt), kThreads, 0, st>>>(pd, d, (int *)off.ptr, (int *)keys.ptr, (int *)vals.ptr);
+            CK(cudaGetLastError());
+            int *start = nullptr, *list = nullptr;
+            s = sort_to_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, &start, &list, st);
+            if (s != IFGF_OK) return s;
+            L.ul_start = start;
+            L.ul = list;
+        }
+    }
+    int herr = 0;
+    CK(cudaMemcpy(&herr, pd.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) { p->last_error = "adjoint lists: a cone lookup missed"; return IFGF_EINTERNAL; }
+    p->adjoint_ready = true;
+    return IFGF_OK;
+}

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/ifgf.h declares.  No compute call (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(ifgf_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libifgf():
+    from paper_2010_02857_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(libifgf):
+    declared = _declared()
+    assert "ifgf_plan_create" in declared and "ifgf_apply_adjoint" in declared
+    for name in declared:
+        assert hasattr(libifgf, name), name
+
+
+def test_binding_mirrors_the_header():
+    import paper_2010_02857_gb300 as pkg
+    assert sorted(pkg.EXPORTS) == _declared()
+
+
+def test_last_error_without_plan_is_safe(libifgf):
+    libifgf.ifgf_last_error.restype = ctypes.c_char_p
+    libifgf.ifgf_last_error.argtypes = [ctypes.c_void_p]
+    assert isinstance(libifgf.ifgf_last_error(None), bytes)
+
+
+def test_invalid_arguments_rejected_before_any_device_work(libifgf):
+    import paper_2010_02857_gb300 as pkg
+    import numpy as np
+    pts = np.zeros((1, 3))
+    with pytest.raises(pkg.IFGFError) as e:
+        pkg.plan_create(pts, 1.0, 4)
+    assert e.value.status == 1
+    pts = np.random.default_rng(0).normal(size=(10, 3))
+    for kw in [dict(levels=2), dict(levels=21), dict(kappa=-1.0), dict(p_radial=2, p_angular=2)]:
+        args = dict(kappa=1.0, levels=4)
+        args.update(kw)
+        with pytest.raises(pkg.IFGFError) as e:
+            pkg.plan_create(pts, args.pop("kappa"), args.pop("levels"), **args)
+        assert e.value.status == 1

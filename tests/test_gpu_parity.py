@@ -1,0 +1,200 @@
+"""GPU parity against the CPU oracle (through the C ABI).
+
+Tolerances:
+  * tree, neighbour, cousin and relevant-cone arrays: bit-exact (integer work);
+  * FP64 plans vs the oracle's serial IFGF: 1e-10 relative (max-norm over outputs).
+    Both evaluate the same interpolants with the same cone choices; they differ only
+    in summation order, FMA contraction and the last bits of libm vs CUDA
+    transcendentals: ~1e-16 per operation times a few thousand terms;
+  * IFGF vs the direct sum (Eq. field1): 1e-3 relative l2 (the accuracy target);
+  * mixed plans (FP32 values, FP64 geometry) vs the FP64 oracle IFGF: 2e-5 relative
+    l2: FP32 rounding (6e-8) accumulated over ~10^3 terms per output and per level.
+"""
+import numpy as np
+import pytest
+
+import ifgf_inputs as wi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2010_02857_gb300 as p
+    return p
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def maxrel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+CASES = [
+    # n, wavelengths, D, leaf_ns, leaf_nc
+    (2000, 2, 4, 1, 2),
+    (3001, 4, 4, 2, 4),
+    (4099, 3, 5, 1, 2),
+    (2500, 0, 4, 1, 2),   # kappa = 0 (Laplace)
+]
+
+
+def _make(case, nrhs=1):
+    n, nl, D, ns, nc = case
+    wl = wi.small_sphere(n, nl, D, leaf_ns=ns, leaf_nc=nc, nrhs=nrhs)
+    return wl, wl.points(), wl.densities()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_tree_and_cones_bit_exact(pkg, torch_cuda, case):
+    wl, pts, _ = _make(case)
+    n, nl, D, ns, nc = case
+    g = pkg.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    H1, corner = g.geometry()
+    oH1, ocorner = o.geometry()
+    assert H1 == oH1 and np.array_equal(corner, ocorner)
+    assert np.array_equal(g.perm(), o.perm())
+    for d in range(1, D + 1):
+        gk, gs = g.boxes(d)
+        ok, os_ = o.boxes(d)
+        assert np.array_equal(gk, ok) and np.array_equal(gs, os_), d
+    for d in range(3, D + 1):
+        gs, gl = g.cousins(d)
+        os_, ol = o.cousins(d)
+        assert np.array_equal(gs, os_) and np.array_equal(gl, ol), d
+        ga, gc = g.active(d)
+        oa, oc = o.active(d)
+        li, oli = g.level_info(d), o.level_info(d)
+        assert (li["ns"], li["nc"]) == (oli["ns"], oli["nc"])
+        assert np.array_equal(ga, oa) and np.array_equal(gc, oc), d
+    assert g.check() == 0
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp64_apply_matches_oracle_and_direct(pkg, torch_cuda, case):
+    torch = torch_cuda
+    wl, pts, sigma = _make(case, nrhs=1)
+    n, nl, D, ns, nc = case
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, D, 3, 5, ns, nc)
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    s = torch.from_numpy(sigma).cuda()
+    # stage-wise: near field, far field, and cone values of every level
+    un = g.apply_partial(s, 1).cpu().numpy()
+    assert maxrel(un, o.apply(sigma, mode=1)) < 1e-12
+    uf = g.apply_partial(s, 2).cpu().numpy()
+    of = o.apply(sigma, mode=2)
+    assert maxrel(uf, of) < 1e-10
+    for d in range(3, D + 1):
+        assert maxrel(g.values(d), o.F(d)) < 1e-10, d
+    u = g.apply(s).cpu().numpy()
+    uo = o.apply(sigma)
+    assert maxrel(u, uo) < 1e-10
+    ex = oracle.direct(pts, wl.kappa, sigma)
+    assert rel(u, ex) < 1e-3
+    assert g.check() == 0
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_fp64_adjoint_matches_oracle(pkg, torch_cuda, case):
+    torch = torch_cuda
+    wl, pts, _ = _make(case)
+    n, nl, D, ns, nc = case
+    v = wi.complex_normal(31, (1, n))
+    s = wi.complex_normal(32, (1, n))
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, D, 3, 5, ns, nc)
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    vg = torch.from_numpy(v).cuda()
+    for mode in (1, 2):
+        assert maxrel(g.apply_partial(vg, mode, adjoint=True).cpu().numpy(),
+                      o.apply_adjoint(v, mode=mode)) < 1e-10, mode
+    w = g.apply_adjoint(vg).cpu().numpy()
+    assert maxrel(w, o.apply_adjoint(v)) < 1e-10
+    # dot-product test on the GPU operator itself
+    u = g.apply(torch.from_numpy(s).cuda()).cpu().numpy()
+    assert abs(np.vdot(v, u) - np.vdot(w, s)) < 1e-12 * abs(np.vdot(v, u))
+    assert g.check() == 0
+
+
+def test_multiple_rhs_and_ragged_chunks(pkg, torch_cuda):
+    torch = torch_cuda
+    wl, pts, _ = _make((2600, 3, 4, 1, 2))
+    o = oracle.Plan(pts, wl.kappa, 4, 3, 5, 1, 2)
+    for prec, nrhs, tol in [("fp64", 3, 1e-10), ("fp64", 6, 1e-10), ("mixed", 11, 2e-5)]:
+        g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 4, 3, 5, 1, 2, max_nrhs=16, precision=prec)
+        sig = wi.complex_normal(40 + nrhs, (nrhs, wl.n))
+        u = g.apply(torch.from_numpy(sig).cuda()).cpu().numpy()
+        uo = o.apply(sig)
+        for r in range(nrhs):
+            assert rel(u[r], uo[r]) < tol, (prec, nrhs, r)
+        w = g.apply_adjoint(torch.from_numpy(sig).cuda()).cpu().numpy()
+        wo = o.apply_adjoint(sig)
+        for r in range(nrhs):
+            assert rel(w[r], wo[r]) < tol, (prec, nrhs, r)
+        assert g.check() == 0
+
+
+def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
+    torch = torch_cuda
+    wl, pts, sigma = _make((2000, 2, 4, 1, 2))
+    g = pkg.Plan(pts, wl.kappa, 4, 3, 5, 1, 2)
+    u_host = g.apply(sigma)
+    u_dev = g.apply(torch.from_numpy(sigma).cuda()).cpu().numpy()
+    assert np.array_equal(u_host, u_dev)
+    # bitwise reproducible run to run
+    assert np.array_equal(g.apply(sigma), u_host)
+    w1 = g.apply_adjoint(sigma)
+    assert np.array_equal(g.apply_adjoint(sigma), w1)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_mixed_precision_matches_fp64_oracle(pkg, torch_cuda, case):
+    torch = torch_cuda
+    wl, pts, sigma = _make(case)
+    n, nl, D, ns, nc = case
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, D, 3, 5, ns, nc, precision="mixed")
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    u = g.apply(torch.from_numpy(sigma).cuda()).cpu().numpy()
+    assert rel(u, o.apply(sigma)) < 2e-5
+    v = wi.complex_normal(7, (1, n))
+    w = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert rel(w, o.apply_adjoint(v)) < 2e-5
+    assert g.check() == 0
+
+
+def test_autograd_gradient_matches_finite_differences(pkg, torch_cuda):
+    # L = ||A sigma||^2 is quadratic, so central differences are exact up to rounding
+    torch = torch_cuda
+    wl, pts, sigma = _make((3000, 4, 4, 2, 4))
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 4, 3, 5, 2, 4)
+    s = torch.from_numpy(sigma[0]).cuda().requires_grad_(True)
+    u = pkg.ifgf_apply_autograd(s[None, :], g)
+    loss = (u.abs() ** 2).sum()
+    loss.backward()
+    grad = s.grad.cpu().numpy()
+    idx = wi.sample_targets(wl.n, 16, 300)
+    h = 1e-3
+    base = sigma[0].copy()
+
+    def L(x):
+        return float((np.abs(g.apply(torch.from_numpy(x[None, :]).cuda()).cpu().numpy()) ** 2).sum())
+
+    for m in idx:
+        for part, unit in ((0, 1.0), (1, 1j)):
+            xp = base.copy(); xp[m] += h * unit
+            xm = base.copy(); xm[m] -= h * unit
+            fd = (L(xp) - L(xm)) / (2 * h)
+            an = grad[m].real if part == 0 else grad[m].imag
+            assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + 1e-6 * np.abs(grad).max(), (m, part, fd, an)
