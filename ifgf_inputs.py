@@ -243,6 +243,10 @@ WORKLOADS = {
     "sphere_4lambda": Workload("sphere_4lambda", 24_576, wavelengths_to_kappa(2.0, 4), 4,
                                leaf_ns=2, leaf_nc=4, targets=24_576, seed=1, surface="sphere",
                                description="Fibonacci sphere N=24576, 4 lambda, D=4, FP64"),
+    # unit sphere, diameter 8 wavelengths, D = 6 (H_D = lambda/4, the paper's Sec. 4 setup)
+    "sphere_8lambda": Workload("sphere_8lambda", 98_304, wavelengths_to_kappa(2.0, 8), 6,
+                               leaf_ns=1, leaf_nc=2, targets=2_000, seed=6, surface="sphere",
+                               description="Fibonacci sphere N=98304, 8 lambda, D=6, FP64"),
     # unit sphere, diameter 32 wavelengths, D = 8
     "sphere_32lambda": Workload("sphere_32lambda", 393_216, wavelengths_to_kappa(2.0, 32), 8,
                                 leaf_ns=1, leaf_nc=2, targets=2_000, seed=2, surface="sphere",
