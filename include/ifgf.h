@@ -119,6 +119,30 @@ ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *v, void *w, int nrhs
 ifgf_status ifgf_apply_partial(ifgf_plan *plan, const void *in, void *out, int nrhs, int mode,
                                int adjoint, void *stream);
 
+/*
+ * u = A sigma like ifgf_apply, but allocating nothing.  The paper has no
+ * counterpart; this entry point exists for callers that may not allocate device
+ * memory during an evaluation (their memory belongs to a framework pool or a fixed
+ * budget, or they cannot afford an allocation's implicit synchronisation): it calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   - All scratch of the evaluation (densities and fields in Morton order, the cone
+ *     values of every level) comes from one fixed device array of 64 MiB,
+ *     2 N nrhs + sum_d A_d P nrhs complex elements (each part rounded up to 256
+ *     bytes); a plan whose evaluation needs more is rejected with IFGF_EINVAL.
+ *     The array is a static device variable of the library: every GPU that loads
+ *     the library holds it until the process exits.
+ *   - sigma and u must be device pointers ([nrhs][N] complex, as for ifgf_apply).
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream
+ *     capture.
+ *   - Every call shares the array and it keeps the last call's contents; each call
+ *     overwrites all of the scratch it reads, so nothing is cleared.  Calls whose
+ *     work overlaps on the GPU (different streams, or different threads) race on
+ *     the array and give wrong results: serialise them.
+ * Errors: IFGF_EINVAL (sizes, host pointers, scratch limit), IFGF_ECUDA.
+ */
+ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma, void *u, int nrhs, void *stream);
+
 /* Release every device and host resource of the plan.  NULL is accepted. */
 ifgf_status ifgf_plan_destroy(ifgf_plan *plan);
 

@@ -32,7 +32,7 @@ STATUS = {0: "IFGF_OK", 1: "IFGF_EINVAL", 2: "IFGF_ENOMEM", 3: "IFGF_ECUDA", 4: 
           5: "IFGF_EINTERNAL"}
 
 # every symbol include/ifgf.h declares
-EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_partial",
+EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_partial", "ifgf_apply_noalloc",
            "ifgf_plan_destroy", "ifgf_plan_level_info", "ifgf_plan_get_perm", "ifgf_plan_get_boxes",
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_geometry",
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_timings",
@@ -66,6 +66,7 @@ def lib():
         L.ifgf_apply.argtypes = [P, P, P, i, P]
         L.ifgf_apply_adjoint.argtypes = [P, P, P, i, P]
         L.ifgf_apply_partial.argtypes = [P, P, P, i, i, i, P]
+        L.ifgf_apply_noalloc.argtypes = [P, P, P, i, P]
         L.ifgf_plan_destroy.argtypes = [P]
         L.ifgf_plan_level_info.argtypes = [P, i, P]
         L.ifgf_plan_get_perm.argtypes = [P, P]
@@ -151,6 +152,13 @@ def apply_adjoint(handle, v, w, nrhs: int, stream=None):
 def apply_partial(handle, x, y, nrhs: int, mode: int, adjoint: bool = False, stream=None):
     _check(lib().ifgf_apply_partial(handle, _ptr(x), _ptr(y), int(nrhs), int(mode), int(bool(adjoint)),
                                     stream if stream is not None else _stream(x)), handle)
+
+
+def apply_noalloc(handle, sigma, u, nrhs: int, stream=None):
+    """ifgf_apply_noalloc: like apply(), with all scratch in the library's fixed 64 MiB
+    device array (device tensors only; the library allocates nothing)."""
+    _check(lib().ifgf_apply_noalloc(handle, _ptr(sigma), _ptr(u), int(nrhs),
+                                    stream if stream is not None else _stream(sigma)), handle)
 
 
 def plan_destroy(handle):
