@@ -66,6 +66,7 @@ def lib():
             L.oracle_node_pos.argtypes = [P, i, i64, i, P, P]
             L.oracle_node_pos.restype = d
             L.oracle_box_center.argtypes = [P, i, ctypes.c_uint64, P]
+            L.oracle_node_rel_child.argtypes = [P, i, i64, i, i, P]
             L.oracle_green.argtypes = [P, P, d, P]
             L.oracle_analytic_factor.argtypes = [P, P, P, d, P]
             L.oracle_cheb_nodes.argtypes = [i, P]
@@ -254,6 +255,13 @@ class Plan:
         q = np.zeros(3)
         R = lib().oracle_node_pos(self.h, d, int(cone), int(node), _p(x), _p(q))
         return q, R
+
+    def node_rel_child(self, d: int, cone: int, node: int, octant: int):
+        """Interpolation point of a level-(d-1) parent cone relative to the centre of the
+        child (level d) in the given octant."""
+        v = np.zeros(3)
+        lib().oracle_node_rel_child(self.h, d, int(cone), int(node), int(octant), _p(v))
+        return v
 
     def box_center(self, d: int, key: int):
         c = np.zeros(3)

@@ -44,6 +44,10 @@
  *       (Sec. 3.3.2, first paragraph), not whole-segment overlap.
  *   R8  D counts the root as level 1; cones exist at levels 3..D; the upward
  *       step runs only for d > 3 (Algorithm 1).
+ *   R9  A parent cone's interpolation point seen from a child centre is
+ *       evaluated as R dir - delta, delta = (+-H_d/2)^3 (Eq. interp_pts with
+ *       Eq. defboxsizesandcenters), not as the difference of two rounded
+ *       absolute positions; the result is independent of the boxes' location.
  *
  * Floating-point contract for the index path (box and cone indices): only the
  * correctly rounded operations + - * / sqrt are used, in the order written, and
@@ -293,11 +297,10 @@ static void box_center(const oplan *p, int d, uint64_t key, double *c)
 /* Cone cell of point y relative to centre c at level d (reading R4).  Returns the
  * linear id (g1 * nc + g2) * 2nc + g3 and, if loc != NULL, the local coordinates
  * in [-1, 1] of (s, theta, phi) within the cell. */
-static int64_t cone_of(const oplan *p, int d, const double *y, const double *c, int64_t *g,
-                       double *loc)
+static int64_t cone_of_vec(const oplan *p, int d, const double *v, int64_t *g, double *loc)
 {
     const olevel *L = &p->lev[d];
-    double vx = y[0] - c[0], vy = y[1] - c[1], vz = y[2] - c[2];
+    double vx = v[0], vy = v[1], vz = v[2];
     double rho2 = vx * vx + vy * vy;
     double r = sqrt(rho2 + vz * vz);
     double rho = sqrt(rho2);
@@ -344,6 +347,13 @@ static int64_t cone_of(const oplan *p, int d, const double *y, const double *c, 
     return (g1 * nc + g2) * (2 * nc) + g3;
 }
 
+/* Cone cell of point y relative to centre c at level d: the vector y - c. */
+static int64_t cone_of(const oplan *p, int d, const double *y, const double *c, int64_t *g, double *loc)
+{
+    double v[3] = {y[0] - c[0], y[1] - c[1], y[2] - c[2]};
+    return cone_of_vec(p, d, v, g, loc);
+}
+
 /* Interpolation point p = (a, b, c) of cone `cone` around centre x at level d,
  * Eq. (interp_pts): x^d(s_a, theta_b, phi_c) + x.  Returns |point - x| as the
  * table radius h_d / s_a. */
@@ -362,6 +372,38 @@ static double node_pos(const oplan *p, int d, int64_t cone, int node, const doub
     q[1] = x[1] + R * (st * sp);
     q[2] = x[2] + R * ct;
     return R;
+}
+
+/* Interpolation point `node` of the level-(d-1) cone `cone` of a parent box, relative
+ * to the centre of its child box with octant bits `oct` (bit 0: x, 1: y, 2: z) at
+ * level d.  By Eq. (interp_pts) the point is x_j + R dir with R = h_{d-1}/s_a, and by
+ * Eq. (defboxsizesandcenters) the child centre is x_j + delta with
+ * delta_i = +H_d/2 (bit set) or -H_d/2, so the point relative to the child centre
+ * is R dir - delta.  It is evaluated in that form, which does not depend on where
+ * the boxes are.  Returns R; dir receives the unit direction. */
+static double node_rel_child(const oplan *p, int d, int64_t cone, int node, int oct, double *v, double *dir)
+{
+    const olevel *L = &p->lev[d - 1];
+    int nc = L->nc, Pa = p->Pang;
+    int64_t g3 = cone % (2 * nc);
+    int64_t g2 = (cone / (2 * nc)) % nc;
+    int64_t g1 = cone / (2 * nc) / nc;
+    int a = node / (Pa * Pa), b = (node / Pa) % Pa, c = node % Pa;
+    double R = L->nodeR[g1 * p->Ps + a];
+    double st = L->sth[g2 * Pa + b], ct = L->cth[g2 * Pa + b];
+    double sp = L->sph[g3 * Pa + c], cp = L->cph[g3 * Pa + c];
+    double hh = p->lev[d].H * 0.5;
+    double dx = st * cp, dy = st * sp, dz = ct;
+    v[0] = R * dx - ((oct & 1) ? hh : -hh);
+    v[1] = R * dy - ((oct & 2) ? hh : -hh);
+    v[2] = R * dz - ((oct & 4) ? hh : -hh);
+    if (dir) { dir[0] = dx; dir[1] = dy; dir[2] = dz; }
+    return R;
+}
+
+void oracle_node_rel_child(void *h, int d, int64_t cone, int node, int oct, double *v)
+{
+    node_rel_child(h, d, cone, node, oct, v, NULL);
 }
 
 /* slot of cone id in box b's relevant list, or -1 */
@@ -623,13 +665,12 @@ void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int 
             if (d >= 4) {
                 olevel *Lp = &p->lev[d - 1];
                 int64_t pb = L->parent[k];
-                double xp[3];
-                box_center(p, d - 1, Lp->key[pb], xp);
+                int oct = (int)(L->key[k] & 7u);
                 for (int64_t sl = Lp->act_start[pb]; sl < Lp->act_start[pb + 1]; ++sl)
                     for (int node = 0; node < p->P; ++node) {
-                        double q[3];
-                        node_pos(p, d - 1, Lp->act_cone[sl], node, xp, q);
-                        ipush(&ids, cone_of(p, d, q, xk, NULL, NULL));
+                        double v[3];
+                        node_rel_child(p, d, Lp->act_cone[sl], node, oct, v, NULL);
+                        ipush(&ids, cone_of_vec(p, d, v, NULL, NULL));
                     }
             }
             box_cnt[k] = sort_unique(ids.v, ids.n);
@@ -770,22 +811,20 @@ int oracle_apply(void *h, int nrhs, const double *sigma_in, double *u_out, int m
                 int64_t uev = 0;
 #pragma omp parallel for schedule(dynamic, 2) reduction(+ : uev, err)
                 for (int64_t j = 0; j < Lp->nbox; ++j) {
-                    double xj[3];
-                    box_center(p, d - 1, Lp->key[j], xj);
                     for (int64_t sl = Lp->act_start[j]; sl < Lp->act_start[j + 1]; ++sl)
                         for (int node = 0; node < P; ++node) {
-                            double q[3];
-                            node_pos(p, d - 1, Lp->act_cone[sl], node, xj, q);
                             cplx *Fp = Lp->F + (sl * P + node) * nrhs;
                             for (int64_t k = Lp->child0[j]; k < Lp->child0[j + 1]; ++k) {
-                                double xk[3], loc[3];
-                                box_center(p, d, Ld->key[k], xk);
-                                int64_t cone = cone_of(p, d, q, xk, NULL, loc);
+                                /* the point x relative to x_k^d, its cone and local coordinates */
+                                double vk[3], loc[3];
+                                double rj = node_rel_child(p, d, Lp->act_cone[sl], node, (int)(Ld->key[k] & 7u), vk, NULL);
+                                int64_t cone = cone_of_vec(p, d, vk, NULL, loc);
                                 int64_t csl = find_slot(Ld, k, cone);
                                 if (csl < 0) { err++; continue; }
                                 cplx v[nrhs];
                                 interp(p, Ld->F + csl * P * nrhs, loc, nrhs, v);
-                                double rk = dist3(q, xk), rj = dist3(q, xj);
+                                /* G(x, x_k^d) / G(x, x_j^{d-1}) with |x - x_j| = rj, |x - x_k| = rk */
+                                double rk = sqrt(vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2]);
                                 cplx fac = (rj / rk) * cexp(I * kappa * (rk - rj));
                                 for (int r = 0; r < nrhs; ++r) Fp[r] += fac * v[r];
                                 uev++;
@@ -887,20 +926,18 @@ int oracle_apply_adjoint(void *h, int nrhs, const double *v_in, double *w_out, i
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : err)
                 for (int64_t k = 0; k < Ld->nbox; ++k) {
                     int64_t j = Ld->parent[k];
-                    double xk[3], xj[3];
-                    box_center(p, d, Ld->key[k], xk);
-                    box_center(p, d - 1, Lp->key[j], xj);
+                    int oct = (int)(Ld->key[k] & 7u);
                     for (int64_t sl = Lp->act_start[j]; sl < Lp->act_start[j + 1]; ++sl)
                         for (int node = 0; node < P; ++node) {
-                            double q[3], loc[3], wsd[64], wt[64], wp[64];
-                            node_pos(p, d - 1, Lp->act_cone[sl], node, xj, q);
-                            int64_t cone = cone_of(p, d, q, xk, NULL, loc);
+                            double vk[3], loc[3], wsd[64], wt[64], wp[64];
+                            double rj = node_rel_child(p, d, Lp->act_cone[sl], node, oct, vk, NULL);
+                            int64_t cone = cone_of_vec(p, d, vk, NULL, loc);
                             int64_t csl = find_slot(Ld, k, cone);
                             if (csl < 0) { err++; continue; }
                             lagrange(p->Ps, p->ts, loc[0], wsd);
                             lagrange(p->Pang, p->ta, loc[1], wt);
                             lagrange(p->Pang, p->ta, loc[2], wp);
-                            double rk = dist3(q, xk), rj = dist3(q, xj);
+                            double rk = sqrt(vk[0] * vk[0] + vk[1] * vk[1] + vk[2] * vk[2]);
                             cplx fac = conj((rj / rk) * cexp(I * kappa * (rk - rj)));
                             const cplx *src = Lp->Fadj + (sl * P + node) * nrhs;
                             for (int a = 0; a < p->Ps; ++a)

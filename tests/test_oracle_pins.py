@@ -332,6 +332,30 @@ def test_nodes_lie_in_their_cone(small_plan):
                 assert abs((2 * (s / lp["ds"] - g[0]) - 1) - tnodes_s[a]) < 1e-12
 
 
+def test_parent_node_relative_to_child_centre(small_plan):
+    # R dir - delta (reading R9) is the parent node minus the child centre, for every
+    # child octant: compare with the absolute positions of real boxes.
+    wl, pts, P = small_plan
+    for d in range(4, wl.levels + 1):
+        pkeys, _ = P.boxes(d - 1)
+        ckeys, _ = P.boxes(d)
+        a_s, a_c = P.active(d - 1)
+        parent_of = {}
+        for ck in ckeys:
+            parent_of.setdefault(int(ck >> np.uint64(3)), []).append(int(ck))
+        for jb in range(0, len(pkeys), max(1, len(pkeys) // 5)):
+            xj = P.box_center(d - 1, int(pkeys[jb]))
+            for ck in parent_of[int(pkeys[jb])]:
+                xk = P.box_center(d, ck)
+                assert np.allclose(xk - xj, [(0.5 if (ck >> b) & 1 else -0.5) * P.level_params(d)["H"]
+                                             for b in range(3)], rtol=0, atol=1e-15)
+                for sl in range(a_s[jb], min(a_s[jb + 1], a_s[jb] + 3)):
+                    for node in (0, 40, 74):
+                        q, R = P.node_pos(d - 1, int(a_c[sl]), node, xj)
+                        v = P.node_rel_child(d, int(a_c[sl]), node, ck & 7)
+                        assert np.allclose(v, q - xk, rtol=0, atol=1e-14 * R)
+
+
 def test_relevant_cones_rule_i_and_cousin_radius(small_plan):
     # Level 3 has only rule (i): relevant cones are exactly the cones of cousin points,
     # and every cousin point has s <= eta (Sec. 3.3.2).
