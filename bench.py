@@ -36,13 +36,19 @@ DEFAULT_WORKLOAD = "sphere_32lambda"
 METRIC = "IFGF apply time and equivalent interactions/s (N^2/t) at rel.err<=1e-3 vs FP64 direct"
 UNIT = "interactions/s"
 
-# Algorithmic FP64 work of one upward evaluation (one parent interpolation point
-# interpolated from one child cone), counted as floating-point operations of the
-# method's arithmetic: 75-term sum-factorised contraction 2*(75+15+3)*2 = 372,
-# Lagrange weights 3*(2+1)+2*5*(4+1) = 59, three local coordinates 12, the
-# re-centring factor 14, complex multiply-accumulate 8; transcendental and
-# correctly-rounded calls (2 sqrt, 3 div, 2 atan2, 1 sincos, 1 rint) counted as 1 each.
-UPWARD_FLOPS_PER_EVAL = 372 + 59 + 12 + 14 + 8 + 9
+# Algorithmic work of one upward evaluation (one parent interpolation point
+# interpolated from one child cone and re-centred): the sum-factorised 75-term
+# contraction, 2 * (75 + 15 + 3) = 186 real FMAs = 372 flops, plus the complex
+# multiply-accumulate by the re-centring factor, 8 flops.  The geometry (child cone,
+# Lagrange weights, factor) is box-independent and tabulated per level where that
+# pays, so it is not counted.
+UPWARD_FLOPS_PER_EVAL = 372 + 8
+
+# FP64 FMA throughput per SM per clock on GB300: the nominal 1.25 TFLOP/s at the
+# 2070 MHz maximum SM clock over 152 SMs is 1.25e12 / (2 * 152 * 2.07e9) = 1.99,
+# i.e. 2 FMAs per clock per SM.
+FP64_FMA_PER_CLK_PER_SM = 2
+NUM_SMS = 152
 
 
 def _dist_env():
@@ -116,14 +122,11 @@ def measured_peaks() -> dict:
     return {}
 
 
-def fp64_peak_tflops() -> tuple[float, str]:
-    """FP64 FMA-pipe peak of this GPU (measured by the committed probe summary)."""
-    path = os.path.join(ROOT, "profiles", "fp64_peak.json")
-    if os.path.exists(path):
-        with open(path) as f:
-            d = json.load(f)
-        return float(d["fp64_tflops"]), "measured (profiles/fp64_peak.json)"
-    return 1.25, "nominal GB300 FP64 (no measurement committed)"
+def fp64_peak_tflops(sm_mhz) -> tuple[float, str]:
+    """FP64 peak derived from unit counts and the sampled SM clock."""
+    f = sm_mhz if sm_mhz else 2070.0
+    peak = 2 * FP64_FMA_PER_CLK_PER_SM * NUM_SMS * f * 1e6 / 1e12
+    return peak, f"derived: {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk/SM x {NUM_SMS} SMs x {f:.0f} MHz"
 
 
 def run_reference(args, wl: wi.Workload):
@@ -267,7 +270,7 @@ def main():
     up_ms = st["upward"]["ms"] / calls
     up_launches = st["upward"]["launches"] / calls
     up_evals = sum(lv["upward_evals"] for lv in stats["level"])
-    peak, peak_src = fp64_peak_tflops()
+    peak, peak_src = fp64_peak_tflops(clk.get("sm_mhz"))
     achieved = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
     roofline = {"bound": "alu", "kernel": "k_upward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": None,

@@ -67,7 +67,10 @@ typedef struct {
     int leaf_nc;    /* n_{C,D}: polar intervals at the leaf level (2 n_C azimuthal); 0 = default */
     int max_nrhs;   /* largest nrhs a later apply may use; 0 = 1 */
     int precision;  /* an ifgf_precision */
-    int flags;      /* bit 0: build the adjoint's transpose lists at plan time */
+    int flags;      /* bit 0: build the adjoint's transpose lists at plan time;
+                       bit 1: no upward tables (compute the upward geometry per
+                       evaluation; by default a level whose geometry table is at most
+                       half its evaluation count gets one) */
 } ifgf_options;
 
 /*

@@ -7,3 +7,15 @@ cudaError_t ifgf_run_typed_f64(const PlanDev &pd, int nrhs, const void *in_user,
 {
     return ifgf::run_typed<double>(pd, nrhs, in_user, out_user, in_sorted, out_sorted, mode, adjoint, st, tm);
 }
+
+cudaError_t ifgf_build_uptable_f64(const PlanDev &pd, int d, void *tab, cudaStream_t st)
+{
+    return ifgf::build_uptable<double>(pd, d, tab, st);
+}
+
+size_t ifgf_uptable_entry_bytes(int precision, int Ps, int Pang)
+{
+    bool big = (Ps == 4 && Pang == 7);
+    if (precision == IFGF_FP64) return big ? sizeof(UpEntry<double, 18>) : sizeof(UpEntry<double, 13>);
+    return big ? sizeof(UpEntry<float, 18>) : sizeof(UpEntry<float, 13>);
+}

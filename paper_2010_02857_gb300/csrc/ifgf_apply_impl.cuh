@@ -183,37 +183,85 @@ __global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int nrhs, const void *
 // ---------------------------------------------------------------------------------
 // Upward step d -> d-1 (d > 3)
 // ---------------------------------------------------------------------------------
-template <typename T, int R, int PS, int PA>
+
+// Geometry of one upward evaluation: the parent node (cone id `pcone`, node) seen from
+// the child centre in octant `oct`: child cone id, Lagrange weights, re-centring
+// factor.  Returns false if r = 0 (cannot happen for s <= 1 nodes).
+template <typename T, int PS, int PA>
+__device__ __forceinline__ int up_geometry(const PlanDev &pd, const LevelDev &L, const LevelDev &Lp, int pcone,
+                                           int node, int oct, T *w, cpx<T> &f)
+{
+    const double hh = L.H * 0.5;
+    double v[3], dir[3];
+    double Rj = node_rel(Lp, PS, PA, pcone, node, hh, oct, v, dir);
+    ConeGeom g = cone_of(L, v[0], v[1], v[2]);
+    double loc[3];
+    local_coords(L, g, v[0], v[1], v[2], loc);
+    weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+    f = recentre<T>(pd.kappa, Rj, dir, g.r, (oct & 1) ? hh : -hh, (oct & 2) ? hh : -hh, (oct & 4) ? hh : -hh);
+    return g.cone;
+}
+
+template <typename T, int PS, int PA>
+__global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, UpEntry<T, PS + 2 * PA> *tab)
+{
+    constexpr int P = PS * PA * PA;
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)L.urows * 8 * P) return;
+    int node = (int)(t % P);
+    int oct = (int)((t / P) % 8);
+    int row = (int)(t / (8 * P));
+    UpEntry<T, PS + 2 * PA> e;
+    cpx<T> f;
+    e.cone = up_geometry<T, PS, PA>(pd, L, Lp, L.uids[row], node, oct, e.w, f);
+    e.fr = f.x;
+    e.fi = f.y;
+    tab[t] = e;
+}
+
+template <typename T, int R, int PS, int PA, bool TAB>
 __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
 {
     constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
     const LevelDev &L = pd.lev[d];
     const LevelDev &Lp = pd.lev[d - 1];
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)Lp.nact * P) return;
     int slot = (int)(t / P), node = (int)(t % P);
     int j = Lp.act_box[slot];
-    const double *cj = Lp.center + 3 * (size_t)j;
-    double q[3], dir[3];
-    double Rj = node_pos(Lp, PS, PA, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, dir);
+    const int pcone = Lp.act_cone[slot];
+    const UpEntry<T, NW> *tab = nullptr;
+    if constexpr (TAB) {
+        int row = table_row(L.ubits, L.urank, pcone);
+        if (row < 0) { atomicAdd(pd.err, 1); return; }
+        tab = (const UpEntry<T, NW> *)L.utab + (size_t)row * 8 * P + node;
+    }
     const int k0 = Lp.child_start[j], k1 = Lp.child_start[j + 1];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
         for (int k = k0; k < k1; ++k) {
-            const double *ck = L.center + 3 * (size_t)k;
-            double vx = __dsub_rn(q[0], ck[0]), vy = __dsub_rn(q[1], ck[1]), vz = __dsub_rn(q[2], ck[2]);
-            ConeGeom g = cone_of(L, vx, vy, vz);
-            int sl = cone_slot(L, k, g.cone);
+            const int oct = (int)(L.key[k] & 7u);
+            T w[NW];
+            cpx<T> f;
+            int cone;
+            if constexpr (TAB) {
+                const UpEntry<T, NW> &e = tab[(size_t)oct * P];
+#pragma unroll
+                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
+                f = {e.fr, e.fi};
+                cone = e.cone;
+            } else {
+                cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
+            }
+            int sl = cone_slot(L, k, cone);
             if (sl < 0) { atomicAdd(pd.err, 1); continue; }
-            double loc[3];
-            local_coords(L, g, vx, vy, vz, loc);
-            T ws[PS], wt[PA], wp[PA];
-            weights3<T, PS, PA>(pd, loc, ws, wt, wp);
             cpx<T> val[R];
-            contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, ws, wt, wp, val);
-            cpx<T> f = recentre<T>(pd.kappa, Rj, dir, g.r, ck[0] - cj[0], ck[1] - cj[1], ck[2] - cj[2]);
+            contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, w, w + PS, w + PS + PA, val);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 cpx<T> m = cmul(f, val[r]);
@@ -338,33 +386,38 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
                     int e = e0 + lane;
                     if (e < e_end) {
                         int item = lst[e];
-                        double px, py, pz;
-                        double Rj = 0, dir[3] = {0, 0, 0};
-                        const double *cj = nullptr;
                         int psl = 0, pnode = 0;
+                        T w[NW];
+                        cpx<T> f;
                         if (pass == 0) {
-                            px = pd.xs[item]; py = pd.ys[item]; pz = pd.zs[item];
+                            double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
+                                   vz = __dsub_rn(pd.zs[item], ck[2]);
+                            ConeGeom g = cone_of(L, vx, vy, vz);
+                            double loc[3];
+                            local_coords(L, g, vx, vy, vz, loc);
+                            weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+                            f = cconj(green_r<T>(pd.kappa, g.r));
                         } else {
                             const LevelDev &Lp = pd.lev[d - 1];
                             psl = item / P;
                             pnode = item % P;
-                            int j = Lp.act_box[psl];
-                            cj = Lp.center + 3 * (size_t)j;
-                            double q[3];
-                            Rj = node_pos(Lp, PS, PA, Lp.act_cone[psl], pnode, cj[0], cj[1], cj[2], q, dir);
-                            px = q[0]; py = q[1]; pz = q[2];
+                            const int oct = (int)(L.key[k] & 7u);
+                            const int pcone = Lp.act_cone[psl];
+                            int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
+                            if (row >= 0) {
+                                const UpEntry<T, NW> &en =
+                                    ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
+#pragma unroll
+                                for (int m = 0; m < NW; ++m) w[m] = en.w[m];
+                                f = cconj(cpx<T>{en.fr, en.fi});
+                            } else {
+                                cpx<T> ff;
+                                up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
+                                f = cconj(ff);
+                            }
                         }
-                        double vx = __dsub_rn(px, ck[0]), vy = __dsub_rn(py, ck[1]), vz = __dsub_rn(pz, ck[2]);
-                        ConeGeom g = cone_of(L, vx, vy, vz);
-                        double loc[3];
-                        local_coords(L, g, vx, vy, vz, loc);
-                        T w[NW];
-                        weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
 #pragma unroll
                         for (int m = 0; m < NW; ++m) sw[warp][lane][m] = w[m];
-                        cpx<T> f;
-                        if (pass == 0) f = cconj(green_r<T>(pd.kappa, g.r));
-                        else f = cconj(recentre<T>(pd.kappa, Rj, dir, g.r, ck[0] - cj[0], ck[1] - cj[1], ck[2] - cj[2]));
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             cpx<T> src = {T(0), T(0)};
@@ -487,7 +540,10 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
         int nl = 0;
         for (int d = pd.D; d >= 4; --d) {
             int64_t np = (int64_t)pd.lev[d - 1].nact * P;
-            if (np > 0) { k_upward<T, R, PS, PA><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs); ++nl; }
+            if (np == 0) continue;
+            if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+            else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+            ++nl;
         }
         tm.mark(STAGE_UPWARD, nl, st);
     }
@@ -527,6 +583,20 @@ cudaError_t launch_orders(const PlanDev &pd, int nrhs, const void *in, void *out
     constexpr int RB = sizeof(T) == 8 ? 4 : 8;
     return adjoint ? launch_adjoint<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm)
                    : launch_forward<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm);
+}
+
+template <typename T>
+cudaError_t build_uptable(const PlanDev &pd, int d, void *tab, cudaStream_t st)
+{
+    int64_t n = (int64_t)pd.lev[d].urows * 8 * pd.P;
+    if (n == 0) return cudaSuccess;
+    if (pd.Ps == 3 && pd.Pang == 5)
+        k_build_uptable<T, 3, 5><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (UpEntry<T, 13> *)tab);
+    else if (pd.Ps == 4 && pd.Pang == 7)
+        k_build_uptable<T, 4, 7><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (UpEntry<T, 18> *)tab);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 // entry used by the per-type translation units

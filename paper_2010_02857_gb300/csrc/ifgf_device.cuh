@@ -128,6 +128,40 @@ __device__ __forceinline__ double node_pos(const LevelDev &L, int Ps, int Pang, 
     return R;
 }
 
+// Interpolation point `node` of the level-(d-1) cone `cone` (level params Lp) seen
+// from the centre of the child box in octant `oct` (bit 0: x, 1: y, 2: z): the point
+// is x_j + R dir (Eq. interp_pts) and the child centre x_j + delta with
+// delta_i = +-H_d/2 exactly (Eq. defboxsizesandcenters), so v = R dir - delta.  This
+// form does not depend on where the boxes are, which makes the upward geometry of
+// a level a function of (cone, node, octant) only.  hh = H_d / 2.
+__device__ __forceinline__ double node_rel(const LevelDev &Lp, int Ps, int Pang, int cone, int node,
+                                           double hh, int oct, double *v, double *dir)
+{
+    const int nc = Lp.nc;
+    int g3 = cone % (2 * nc);
+    int g2 = (cone / (2 * nc)) % nc;
+    int g1 = cone / (2 * nc) / nc;
+    int a = node / (Pang * Pang), b = (node / Pang) % Pang, c = node % Pang;
+    double R = Lp.nodeR[g1 * Ps + a];
+    double st = Lp.sth[g2 * Pang + b], ct = Lp.cth[g2 * Pang + b];
+    double sp = Lp.sph[g3 * Pang + c], cp = Lp.cph[g3 * Pang + c];
+    double dx = __dmul_rn(st, cp), dy = __dmul_rn(st, sp);
+    v[0] = __dsub_rn(__dmul_rn(R, dx), (oct & 1) ? hh : -hh);
+    v[1] = __dsub_rn(__dmul_rn(R, dy), (oct & 2) ? hh : -hh);
+    v[2] = __dsub_rn(__dmul_rn(R, ct), (oct & 4) ? hh : -hh);
+    if (dir) { dir[0] = dx; dir[1] = dy; dir[2] = ct; }
+    return R;
+}
+
+// Row of cone id `cone` in a level's upward table (union bitmap + rank), -1 if absent.
+__device__ __forceinline__ int table_row(const uint64_t *ubits, const int *urank, int cone)
+{
+    uint64_t word = ubits[cone >> 6];
+    uint64_t bit = 1ull << (cone & 63);
+    if (!(word & bit)) return -1;
+    return urank[cone >> 6] + __popcll(word & (bit - 1));
+}
+
 // Slot of cone id `cone` of box b via the bitmap rank directory; -1 if not relevant.
 __device__ __forceinline__ int cone_slot(const LevelDev &L, int b, int cone)
 {

@@ -64,6 +64,15 @@ struct LevelDev {
     const int *tl = nullptr;
     const int *ul_start = nullptr;     // adjoint: per slot, parent (slot*P + node) landing in it
     const int *ul = nullptr;
+    // Upward table of the step from this level d to d-1 (absent: computed on the fly).
+    // Rows are the distinct relevant cone ids of level d-1 (union bitmap + rank);
+    // entry (row, octant, node) holds the child cone id, the Lagrange weights of the
+    // node in that child cone and the re-centring factor.
+    int urows = 0;
+    const uint64_t *ubits = nullptr;   // [words of level d-1]
+    const int *urank = nullptr;        // [words of level d-1]
+    const int *uids = nullptr;         // [urows] cone id of each row
+    const void *utab = nullptr;        // [urows][8][P] entries
 };
 
 struct PlanDev {
@@ -104,6 +113,7 @@ struct LevelHost {
     int ns = 0, nc = 0;
     int64_t cousin_evals = 0, upward_evals = 0;
     int64_t words = 0;
+    int64_t table_rows = 0;   // rows of the upward table of step d -> d-1 (0: none)
 };
 
 struct ifgf_plan {
@@ -138,10 +148,21 @@ struct ifgf_plan {
 // complex element size of the plan's data type
 inline size_t ifgf_elem_bytes(int precision) { return precision == IFGF_FP64 ? 16 : 8; }
 
+// Upward-table entry for value type T and NW = P_s + 2 P_ang weights.
+template <typename T, int NW> struct UpEntry {
+    T w[NW];
+    T fr, fi;
+    int cone;
+};
+
 // plan.cu
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
 void *ifgf_dalloc(ifgf_plan *p, size_t bytes);
+// apply_*.cu: fill the upward table of level d (entries already allocated)
+cudaError_t ifgf_build_uptable_f64(const PlanDev &pd, int d, void *tab, cudaStream_t st);
+cudaError_t ifgf_build_uptable_f32(const PlanDev &pd, int d, void *tab, cudaStream_t st);
+size_t ifgf_uptable_entry_bytes(int precision, int Ps, int Pang);
 // apply.cu
 ifgf_status ifgf_run_apply(ifgf_plan *p, const void *sigma, void *u, int nrhs, int mode,
                            int adjoint, cudaStream_t st);

@@ -280,14 +280,22 @@ __global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
     if (t >= (int64_t)Lp.nact * pd.P) return;
     int slot = (int)(t / pd.P), node = (int)(t % pd.P);
     int j = Lp.act_box[slot];
-    const double *cj = Lp.center + 3 * (size_t)j;
-    double q[3];
-    node_pos(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, nullptr);
+    const double hh = L.H * 0.5;
     for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k) {
-        const double *c = L.center + 3 * (size_t)k;
-        ConeGeom g = cone_of(L, __dsub_rn(q[0], c[0]), __dsub_rn(q[1], c[1]), __dsub_rn(q[2], c[2]));
+        double v[3];
+        node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
+        ConeGeom g = cone_of(L, v[0], v[1], v[2]);
         set_bit(bits, L.words, k, g.cone);
     }
+}
+
+// union over boxes of a level's relevant-cone bitmaps
+__global__ void k_union_bits(const uint64_t *bits, int nbox, int words, uint64_t *ubits)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nbox * words) return;
+    uint64_t v = bits[t];
+    if (v) atomicOr((unsigned long long *)&ubits[t % words], (unsigned long long)v);
 }
 
 __global__ void k_popc(const uint64_t *bits, int64_t nw, int *cnt)
@@ -432,13 +440,12 @@ __global__ void k_emit_ulist(PlanDev pd, int d, const int *off, int *keys, int *
     int slot = (int)(t / pd.P), node = (int)(t % pd.P);
     int j = Lp.act_box[slot];
     int nch = Lp.child_start[j + 1] - Lp.child_start[j];
-    const double *cj = Lp.center + 3 * (size_t)j;
-    double q[3];
-    node_pos(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, cj[0], cj[1], cj[2], q, nullptr);
+    const double hh = L.H * 0.5;
     int o = off[slot] + node * nch;
     for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k, ++o) {
-        const double *c = L.center + 3 * (size_t)k;
-        ConeGeom g = cone_of(L, __dsub_rn(q[0], c[0]), __dsub_rn(q[1], c[1]), __dsub_rn(q[2], c[2]));
+        double v[3];
+        node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
+        ConeGeom g = cone_of(L, v[0], v[1], v[2]);
         int sl = cone_slot(L, k, g.cone);
         if (sl < 0) { atomicAdd(pd.err, 1); sl = 0; }
         keys[o] = sl;
@@ -799,6 +806,50 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaMemcpyAsync(h, a, sizeof(h), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int d = 4; d <= D; ++d) p->lh[d].upward_evals = (int64_t)h[d];
+    }
+
+    // Upward tables: the geometry of the step d -> d-1 depends only on (parent cone id,
+    // child octant, node).  Tabulate it where the table has at most half as many
+    // entries as the level has upward evaluations per apply.
+    const size_t entry_bytes = ifgf_uptable_entry_bytes(p->precision, Ps, Pang);
+    for (int d = 4; d <= D; ++d) {
+        LevelDev &L = pd.lev[d];
+        LevelDev &Lp = pd.lev[d - 1];
+        int64_t nw = Lp.words;
+        DALLOC(ubits, uint64_t, nw);
+        CK(cudaMemsetAsync(ubits, 0, nw * sizeof(uint64_t), st));
+        int64_t tot = (int64_t)Lp.nbox * Lp.words;
+        k_union_bits<<<nblocks(tot), kThreads, 0, st>>>(Lp.bits, Lp.nbox, Lp.words, ubits);
+        CK(cudaGetLastError());
+        Scratch cnt;
+        if (!cnt.alloc((size_t)(nw + 1) * 4)) return IFGF_ENOMEM;
+        CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nw + 1) * 4, st));
+        k_popc<<<nblocks(nw), kThreads, 0, st>>>(ubits, nw, (int *)cnt.ptr);
+        CK(cudaGetLastError());
+        DALLOC(urank, int, nw + 1);
+        ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, urank, nw + 1, st);
+        if (s != IFGF_OK) return s;
+        int rows = 0;
+        CK(cudaMemcpy(&rows, urank + nw, sizeof(int), cudaMemcpyDeviceToHost));
+        int64_t entries = (int64_t)rows * 8 * P;
+        size_t bytes = (size_t)entries * entry_bytes;
+        if ((p->flags & 2) || rows == 0 || 2 * entries > p->lh[d].upward_evals || bytes > ((size_t)8 << 30)) continue;
+        DALLOC(uids, int, rows);
+        Scratch dummy;
+        if (!dummy.alloc((size_t)rows * 4)) return IFGF_ENOMEM;
+        k_expand<<<nblocks(nw), kThreads, 0, st>>>(ubits, urank, nw, Lp.words, uids, (int *)dummy.ptr);
+        CK(cudaGetLastError());
+        void *tab = ifgf_dalloc(p, bytes);
+        if (!tab) { p->last_error = "upward table"; return IFGF_ENOMEM; }
+        L.ubits = ubits;
+        L.urank = urank;
+        L.uids = uids;
+        L.urows = rows;
+        CK(p->precision == IFGF_FP64 ? ifgf_build_uptable_f64(pd, d, tab, st)
+                                     : ifgf_build_uptable_f32(pd, d, tab, st));
+        L.utab = tab;
+        p->lh[d].table_rows = rows;
+        CK(cudaStreamSynchronize(st));
     }
 
     // value buffers

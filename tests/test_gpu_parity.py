@@ -146,6 +146,24 @@ def test_multiple_rhs_and_ragged_chunks(pkg, torch_cuda):
         assert g.check() == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-5)])
+def test_upward_tables_match_on_the_fly_geometry(pkg, torch_cuda, precision, tol):
+    torch = torch_cuda
+    wl, pts, sigma = _make((6000, 4, 6, 1, 2))
+    a = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, precision=precision)
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, precision=precision, flags=2)
+    assert any(lv["table_rows"] > 0 for lv in a.stats()["level"])
+    assert all(lv["table_rows"] == 0 for lv in b.stats()["level"])
+    s = torch.from_numpy(sigma).cuda()
+    ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
+    assert rel(ua, ub) < tol
+    wa, wb = a.apply_adjoint(s).cpu().numpy(), b.apply_adjoint(s).cpu().numpy()
+    assert rel(wa, wb) < tol
+    o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    assert rel(ua, o.apply(sigma)) < (1e-10 if precision == "fp64" else 2e-5)
+    assert a.check() == 0 and b.check() == 0
+
+
 def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     torch = torch_cuda
     wl, pts, sigma = _make((2000, 2, 4, 1, 2))
