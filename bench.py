@@ -191,6 +191,8 @@ def main():
     ap.add_argument("--ref-targets", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="override the workload's precision")
     args = ap.parse_args()
     wl = wi.WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -206,7 +208,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    precision = {"fp64": "fp64", "mixed": "mixed", "batched": "mixed"}[wl.precision]
+    precision = args.precision or {"fp64": "fp64", "mixed": "mixed", "batched": "mixed"}[wl.precision]
     pts = torch.from_numpy(wl.points()).to(dev)
     t0 = time.perf_counter()
     plan = pkg.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc,

@@ -178,6 +178,17 @@ ifgf_status ifgf_plan_get_active(const ifgf_plan *plan, int level, int64_t *star
  * [nact][P][nrhs] complex of the plan's data type (host). */
 ifgf_status ifgf_plan_get_values(const ifgf_plan *plan, int level, void *out);
 
+/*
+ * Cone cells (Eq. defconedomain, defconedomainproduct) of the vectors v[n][3]
+ * (host; a vector is a point minus a box centre) at level d >= 3, by the two
+ * device paths the library uses: exact[i] from correctly rounded FP64 operations
+ * (plan construction) and fast[i] from Newton-refined estimates with a correctly
+ * rounded fallback near cell boundaries (evaluation).  Both are linear cone ids
+ * (g1 n_C + g2) 2 n_C + g3 and must be equal; for tests.
+ */
+ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int64_t n, const double *v,
+                               int32_t *exact, int32_t *fast);
+
 /* Root cube: geom[0] = H_1, geom[1..3] = lower corner. */
 ifgf_status ifgf_plan_geometry(const ifgf_plan *plan, double *geom);
 

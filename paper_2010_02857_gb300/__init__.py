@@ -34,7 +34,8 @@ STATUS = {0: "IFGF_OK", 1: "IFGF_EINVAL", 2: "IFGF_ENOMEM", 3: "IFGF_ECUDA", 4: 
 # every symbol include/ifgf.h declares
 EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_partial", "ifgf_apply_noalloc",
            "ifgf_plan_destroy", "ifgf_plan_level_info", "ifgf_plan_get_perm", "ifgf_plan_get_boxes",
-           "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_geometry",
+           "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
+           "ifgf_plan_geometry",
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_timings",
            "ifgf_last_error"]
 STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
@@ -74,6 +75,7 @@ def lib():
         L.ifgf_plan_get_cousins.argtypes = [P, i, P, P]
         L.ifgf_plan_get_active.argtypes = [P, i, P, P]
         L.ifgf_plan_get_values.argtypes = [P, i, P]
+        L.ifgf_plan_cone_ids.argtypes = [P, i, i64, P, P, P]
         L.ifgf_plan_geometry.argtypes = [P, P]
         L.ifgf_plan_stats.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
         L.ifgf_plan_check.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
@@ -276,6 +278,14 @@ class Plan:
         out = np.zeros((li["nact"], self.P, nrhs), dtype=self.numpy_dtype)
         _check(lib().ifgf_plan_get_values(self.handle, d, _ptr(out)), self.handle)
         return out
+
+    def cone_ids(self, d, v):
+        """Cone ids of the vectors v [n,3] at level d: (exact path, fast path)."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        ex = np.zeros(v.shape[0], dtype=np.int32)
+        fa = np.zeros(v.shape[0], dtype=np.int32)
+        _check(lib().ifgf_plan_cone_ids(self.handle, d, v.shape[0], _ptr(v), _ptr(ex), _ptr(fa)), self.handle)
+        return ex, fa
 
     def geometry(self):
         g = np.zeros(4)

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "ifgf_internal.h"
+#include "ifgf_device.cuh"
 
 cudaError_t ifgf_run_typed_f64(const PlanDev &pd, int nrhs, const void *in_user, void *out_user,
                                void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
@@ -372,6 +372,45 @@ extern "C" ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors)
     if (cudaMemset(plan->dev.err, 0, sizeof(int)) != cudaSuccess) return IFGF_ECUDA;
     *device_errors = h;
     return IFGF_OK;
+}
+
+__global__ void k_cone_ids(PlanDev pd, int d, int n, const double *v, int *exact, int *fast)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const LevelDev &L = pd.lev[d];
+    double x = v[3 * (size_t)i], y = v[3 * (size_t)i + 1], z = v[3 * (size_t)i + 2];
+    exact[i] = ifgf::cone_of(L, x, y, z).cone;
+    fast[i] = ifgf::cone_of_fast(L, x, y, z).cone;
+}
+
+extern "C" ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int64_t n, const double *v,
+                                          int32_t *exact, int32_t *fast)
+{
+    if (!level_ok(plan, level, 3) || n < 0 || n > (1 << 30) || (n > 0 && (!v || !exact || !fast)))
+        return IFGF_EINVAL;
+    if (n == 0) return IFGF_OK;
+    ifgf_plan *p = (ifgf_plan *)plan;
+    double *dv = nullptr;
+    int *de = nullptr;
+    if (cudaMalloc(&dv, (size_t)n * 3 * sizeof(double)) != cudaSuccess) return IFGF_ENOMEM;
+    if (cudaMalloc(&de, (size_t)n * 2 * sizeof(int)) != cudaSuccess) {
+        cudaFree(dv);
+        return IFGF_ENOMEM;
+    }
+    ifgf_status st = IFGF_OK;
+    if (cudaMemcpy(dv, v, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) st = IFGF_ECUDA;
+    if (st == IFGF_OK) {
+        k_cone_ids<<<(int)((n + 255) / 256), 256>>>(p->dev, level, (int)n, dv, de, de + n);
+        if (cudaDeviceSynchronize() != cudaSuccess) st = IFGF_ECUDA;
+    }
+    if (st == IFGF_OK && (cudaMemcpy(exact, de, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                          cudaMemcpy(fast, de + n, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+        st = IFGF_ECUDA;
+    cudaFree(dv);
+    cudaFree(de);
+    if (st != IFGF_OK) p->last_error = "cone id evaluation failed";
+    return st;
 }
 
 extern "C" ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on)

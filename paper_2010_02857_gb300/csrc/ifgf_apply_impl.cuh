@@ -93,13 +93,49 @@ __device__ __forceinline__ void contract(const void *F, size_t base, int nrhs, i
     }
 }
 
+// |v| in FP64.  Double plans: correctly rounded sqrt.  Float plans: FP32 rsqrt plus
+// one FP64 Newton step (relative error < 1e-13), enough for phase arguments.
+template <typename T> __device__ __forceinline__ double dist(double dx, double dy, double dz)
+{
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if constexpr (sizeof(T) == 8) {
+        return sqrt(r2);
+    } else {
+        double y = (double)rsqrtf((float)r2);
+        y = y * (1.5 - 0.5 * r2 * y * y);
+        return r2 * y;
+    }
+}
+
 // e^{i kappa r} / (4 pi r)
 template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, double r)
 {
     T c, s;
     expi(kappa * r, c, s);
-    T a = (T)(kInv4Pi / r);
+    T a;
+    if constexpr (sizeof(T) == 8) a = kInv4Pi / r;
+    else a = (float)kInv4Pi / (float)r;
     return {a * c, a * s};
+}
+
+// cone cell (bit-identical to cone_of), Lagrange weights and distance of the vector v
+template <typename T, int PS, int PA>
+__device__ __forceinline__ ConeGeom geom_weights(const PlanDev &pd, const LevelDev &L, double vx, double vy,
+                                                 double vz, T *w)
+{
+    ConeGeom g = cone_of_fast(L, vx, vy, vz);
+    if constexpr (sizeof(T) == 8) {
+        double loc[3];
+        local_coords(L, g, vx, vy, vz, loc);
+        weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+    } else {
+        float t[3];
+        local_coords_f32(L, g, vx, vy, vz, t);
+        lagrange<float>(PS, pd.ts, pd.its, t[0], w);
+        lagrange<float>(PA, pd.ta, pd.ita, t[1], w + PS);
+        lagrange<float>(PA, pd.ta, pd.ita, t[2], w + PS + PA);
+    }
+    return g;
 }
 
 // Re-centring factor G(q, x_k) / G(q, x_j) = (r_j / r_k) e^{i kappa (r_k - r_j)} for the
@@ -115,7 +151,9 @@ __device__ __forceinline__ cpx<T> recentre(double kappa, double Rj, const double
     double diff = (dd - 2.0 * Rj * yd) / (rk + Rj);
     T c, s;
     expi(kappa * diff, c, s);
-    T a = (T)(Rj / rk);
+    T a;
+    if constexpr (sizeof(T) == 8) a = Rj / rk;
+    else a = (float)Rj / (float)rk;
     return {a * c, a * s};
 }
 
@@ -160,10 +198,12 @@ __global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int nrhs, const void *
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
         for (int j = j0; j < j1; ++j) {
             double dx = q[0] - pd.xs[j], dy = q[1] - pd.ys[j], dz = q[2] - pd.zs[j];
-            double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+            double r1 = dist<T>(dx, dy, dz);
             T cc, ss;
             expi(pd.kappa * (r1 - R0), cc, ss);
-            T a = (T)(R0 / r1);
+            T a;
+            if constexpr (sizeof(T) == 8) a = R0 / r1;
+            else a = (float)R0 / (float)r1;
             cpx<T> g = {a * cc, a * ss};
 #pragma unroll
             for (int r = 0; r < R; ++r)
@@ -194,10 +234,7 @@ __device__ __forceinline__ int up_geometry(const PlanDev &pd, const LevelDev &L,
     const double hh = L.H * 0.5;
     double v[3], dir[3];
     double Rj = node_rel(Lp, PS, PA, pcone, node, hh, oct, v, dir);
-    ConeGeom g = cone_of(L, v[0], v[1], v[2]);
-    double loc[3];
-    local_coords(L, g, v[0], v[1], v[2], loc);
-    weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+    ConeGeom g = geom_weights<T, PS, PA>(pd, L, v[0], v[1], v[2], w);
     f = recentre<T>(pd.kappa, Rj, dir, g.r, (oct & 1) ? hh : -hh, (oct & 2) ? hh : -hh, (oct & 4) ? hh : -hh);
     return g.cone;
 }
@@ -216,6 +253,13 @@ __global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, UpEntr
     UpEntry<T, PS + 2 * PA> e;
     cpx<T> f;
     e.cone = up_geometry<T, PS, PA>(pd, L, Lp, L.uids[row], node, oct, e.w, f);
+    // the table's cone id must be the one relevance rule (ii) marked: take the
+    // correctly rounded cell (cone_of_fast agrees by construction; this is a check)
+    {
+        double v[3];
+        node_rel(Lp, PS, PA, L.uids[row], node, L.H * 0.5, oct, v, nullptr);
+        if (cone_of(L, v[0], v[1], v[2]).cone != e.cone) atomicAdd(pd.err, 1);
+    }
     e.fr = f.x;
     e.fi = f.y;
     tab[t] = e;
@@ -297,8 +341,7 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
                 if (k < 0) break;
                 for (int j = LD.start[k]; j < LD.start[k + 1]; ++j) {
                     if (j == i) continue;
-                    double dx = x - pd.xs[j], dy = y - pd.ys[j], dz = z - pd.zs[j];
-                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    double r1 = dist<T>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]);
                     cpx<T> G = green_r<T>(pd.kappa, r1);
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -318,15 +361,12 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
                     int k = L.cous[e];
                     const double *ck = L.center + 3 * (size_t)k;
                     double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
-                    ConeGeom g = cone_of(L, vx, vy, vz);
+                    T w[PS + 2 * PA];
+                    ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
                     int sl = cone_slot(L, k, g.cone);
                     if (sl < 0) { atomicAdd(pd.err, 1); continue; }
-                    double loc[3];
-                    local_coords(L, g, vx, vy, vz, loc);
-                    T ws[PS], wt[PA], wp[PA];
-                    weights3<T, PS, PA>(pd, loc, ws, wt, wp);
                     cpx<T> val[R];
-                    contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, ws, wt, wp, val);
+                    contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, w, w + PS, w + PS + PA, val);
                     cpx<T> G = green_r<T>(pd.kappa, g.r);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
@@ -392,10 +432,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
                         if (pass == 0) {
                             double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
                                    vz = __dsub_rn(pd.zs[item], ck[2]);
-                            ConeGeom g = cone_of(L, vx, vy, vz);
-                            double loc[3];
-                            local_coords(L, g, vx, vy, vz, loc);
-                            weights3<T, PS, PA>(pd, loc, w, w + PS, w + PS + PA);
+                            ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
                             f = cconj(green_r<T>(pd.kappa, g.r));
                         } else {
                             const LevelDev &Lp = pd.lev[d - 1];
@@ -480,8 +517,7 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
                 if (k < 0) break;
                 for (int i = LD.start[k]; i < LD.start[k + 1]; ++i) {
                     if (i == j) continue;
-                    double dx = pd.xs[i] - x, dy = pd.ys[i] - y, dz = pd.zs[i] - z;
-                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    double r1 = dist<T>(pd.xs[i] - x, pd.ys[i] - y, pd.zs[i] - z);
                     cpx<T> G = cconj(green_r<T>(pd.kappa, r1));
 #pragma unroll
                     for (int r = 0; r < R; ++r)
@@ -500,11 +536,12 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
                 for (int node = 0; node < P; ++node) {
                     double q[3];
                     double R0 = node_pos(LD, PS, PA, cone, node, c[0], c[1], c[2], q, nullptr);
-                    double dx = q[0] - x, dy = q[1] - y, dz = q[2] - z;
-                    double r1 = sqrt(dx * dx + dy * dy + dz * dz);
+                    double r1 = dist<T>(q[0] - x, q[1] - y, q[2] - z);
                     T cc, ss;
                     expi(pd.kappa * (r1 - R0), cc, ss);
-                    T a = (T)(R0 / r1);
+                    T a;
+                    if constexpr (sizeof(T) == 8) a = R0 / r1;
+                    else a = (float)R0 / (float)r1;
                     cpx<T> g = {a * cc, -a * ss};
 #pragma unroll
                     for (int r = 0; r < R; ++r)

@@ -90,6 +90,104 @@ __device__ __forceinline__ ConeGeom cone_of(const LevelDev &L, double vx, double
     return o;
 }
 
+// ----------------------------------------------------------------------------------
+// Fast cone cell: the same cell as cone_of, for a fraction of its FP64 cost.
+// 1/r and 1/rho start from FP32 rsqrt (relative error < 2^-22) and take one FP64
+// Newton step (error < 1.5 * 2^-44 < 1e-13), so s/Delta_s, v_z/r and v_x/rho are
+// known to better than 1e-13 relative.  When every such estimate is farther than
+// 1e-11 (relative for s/Delta_s, absolute for the cosines) from the cell boundaries
+// that decide it, the cells equal those of the correctly rounded path; otherwise the
+// correctly rounded cone_of decides.  The estimates of r, rho and s/Delta_s feed
+// the value path (1e-13 relative).
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ int count_le(const double *tab, int lo, int hi, double x)
+{
+    // number of k in [lo, hi) with x <= tab[k], tab strictly decreasing
+    int a = lo, b = hi;
+    while (a < b) {
+        int mid = (a + b) >> 1;
+        if (x <= tab[mid]) a = mid + 1; else b = mid;
+    }
+    return a - lo;
+}
+
+__device__ __forceinline__ bool near_edge(double x, const double *tab, int k, int lo, int hi)
+{
+    // x lies within 1e-11 of tab[k-1] or tab[k] (the boundaries around position k)
+    const double m = 1e-11;
+    return (k - 1 >= lo && fabs(x - tab[k - 1]) < m) || (k < hi && fabs(x - tab[k]) < m);
+}
+
+__device__ __forceinline__ ConeGeom cone_of_fast(const LevelDev &L, double vx, double vy, double vz)
+{
+    const int nc = L.nc, ns = L.ns;
+    float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+    float rho2f = fx * fx + fy * fy;
+    float r2f = rho2f + fz * fz;
+    if (!(rho2f > 1e-30f) || !(r2f > 1e-30f)) return cone_of(L, vx, vy, vz);
+    double rho2 = vx * vx + vy * vy;
+    double r2 = rho2 + vz * vz;
+    double ri = (double)rsqrtf(r2f);
+    ri = ri * (1.5 - 0.5 * r2 * ri * ri);
+    double hi = (double)rsqrtf(rho2f);
+    hi = hi * (1.5 - 0.5 * rho2 * hi * hi);
+    ConeGeom o;
+    o.r = r2 * ri;
+    o.rho = rho2 * hi;
+    double q = L.hds * ri;
+    o.s_over_ds = q;
+    double fq = floor(q);
+    double fr = q - fq;
+    double mq = 1e-11 * fmax(q, 1.0);
+    bool edge = (fr < mq) || (1.0 - fr < mq);
+    o.g1 = fq < 0.0 ? 0 : (fq > (double)(ns - 1) ? ns - 1 : (int)fq);
+    double ct = vz * ri;
+    int m2 = count_le(L.cosk, 1, nc, ct);
+    edge = edge || near_edge(ct, L.cosk, m2 + 1, 1, nc);
+    o.g2 = m2;
+    double cp = vx * hi;
+    if (vy >= 0.0) {
+        int m3 = count_le(L.cosk, 1, nc + 1, cp);
+        edge = edge || near_edge(cp, L.cosk, m3 + 1, 1, nc + 1);
+        o.g3 = m3;
+    } else {
+        // -cosk increasing: count j in [1, nc-1] with cp >= -cosk[j]  <=>  -cp <= cosk[j]
+        int m3 = count_le(L.cosk, 1, nc, -cp);
+        edge = edge || near_edge(-cp, L.cosk, m3 + 1, 1, nc);
+        o.g3 = nc + m3;
+    }
+    if (edge) {
+        ConeGeom e = cone_of(L, vx, vy, vz);
+        e.r = o.r;
+        e.rho = o.rho;
+        e.s_over_ds = q;
+        return e;
+    }
+    o.cone = (o.g1 * nc + o.g2) * (2 * nc) + o.g3;
+    return o;
+}
+
+// Local coordinates with FP32 angles: the polar and azimuthal angles are rotated to
+// the start of their cell in FP64 (no input rounding), and only the in-cell angle,
+// in [0, Delta_theta), goes through FP32 atan2 (relative error ~1e-7 of the in-cell
+// angle, i.e. ~2e-7 in the local coordinate).
+__device__ __forceinline__ void local_coords_f32(const LevelDev &L, const ConeGeom &g, double vx, double vy,
+                                                 double vz, float *t)
+{
+    t[0] = (float)(2.0 * (g.s_over_ds - (double)g.g1) - 1.0);
+    double c2 = L.cs_edge[2 * g.g2], s2 = L.cs_edge[2 * g.g2 + 1];
+    // angle from the z axis measured from theta_g2 = g2 Delta_theta
+    double yt = g.rho * c2 - vz * s2, xt = vz * c2 + g.rho * s2;
+    t[1] = 2.0f * (atan2f((float)yt, (float)xt) * L.inv_dth) - 1.0f;
+    if (g.rho == 0.0) {
+        t[2] = 0.0f;
+    } else {
+        double c3 = L.cs_edge[2 * g.g3], s3 = L.cs_edge[2 * g.g3 + 1];
+        double yp = vy * c3 - vx * s3, xp = vx * c3 + vy * s3;
+        t[2] = 2.0f * (atan2f((float)yp, (float)xp) * L.inv_dth) - 1.0f;
+    }
+}
+
 // Local coordinates in [-1, 1] of (s, theta, phi) inside the cell (value path).
 __device__ __forceinline__ void local_coords(const LevelDev &L, const ConeGeom &g, double vx,
                                              double vy, double vz, double *t)

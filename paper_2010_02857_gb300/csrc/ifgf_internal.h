@@ -53,6 +53,9 @@ struct LevelDev {
     const double *nodeR = nullptr;     // [ns*Ps]
     const double *sth = nullptr, *cth = nullptr;  // [nc*Pang]
     const double *sph = nullptr, *cph = nullptr;  // [2nc*Pang]
+    const double *cs_edge = nullptr;   // [2nc+1][2] cos, sin of k pi / n_C (cell start angles)
+    double hds = 0;                    // h / Delta_s
+    float inv_dth = 0;                 // 1 / Delta_theta
     const uint64_t *bits = nullptr;    // [nbox*words]
     const int *rank = nullptr;         // [nbox*words]
     const int *act_start = nullptr;    // [nbox+1]

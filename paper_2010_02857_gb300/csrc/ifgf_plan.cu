@@ -740,11 +740,20 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         size_t o_cph = tab.size();
         for (int g = 0; g < 2 * nc[d]; ++g)
             for (int c = 0; c < Pang; ++c) tab.push_back(cos(L.dth * ((double)g + (1.0 + pd.ta[c]) * 0.5)));
+        size_t o_cs = tab.size();
+        for (int k = 0; k <= 2 * nc[d]; ++k) {
+            double a = ((double)k * M_PI) / (double)nc[d];
+            tab.push_back(cos(a));
+            tab.push_back(sin(a));
+        }
+        L.hds = L.h / L.ds;
+        L.inv_dth = (float)(1.0 / L.dth);
         DALLOC(dtab, double, tab.size());
         CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         L.cosk = dtab + o_cosk; L.nodeR = dtab + o_R;
         L.sth = dtab + o_sth; L.cth = dtab + o_cth; L.sph = dtab + o_sph; L.cph = dtab + o_cph;
+        L.cs_edge = dtab + o_cs;
     }
 
     // relevant cones, top-down

@@ -164,6 +164,38 @@ def test_upward_tables_match_on_the_fly_geometry(pkg, torch_cuda, precision, tol
     assert a.check() == 0 and b.check() == 0
 
 
+def test_cone_index_fast_path_is_exact_on_cell_boundaries(pkg, torch_cuda):
+    # vectors on and next to every kind of cell boundary (s, theta, phi, the poles):
+    # the GPU's correctly rounded path must equal the oracle bit for bit, and the
+    # fast path must equal both
+    wl, pts, _ = _make((3000, 8, 6, 1, 2))
+    g = pkg.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    rng = np.random.default_rng(5)
+    for d in range(3, 7):
+        lp = o.level_params(d)
+        li = o.level_info(d)
+        ns, nc = li["ns"], li["nc"]
+        vecs = []
+        eps = [0.0, 1e-16, -1e-16, 1e-14, -1e-14, 1e-12, -1e-12, 1e-11, -1e-11, 1e-9, -1e-9]
+        for _ in range(600):
+            m = rng.integers(0, ns + 1)
+            k = rng.integers(0, nc + 1)
+            j = rng.integers(0, 2 * nc + 1)
+            e = rng.choice(eps, size=3)
+            s = max(m, 0.05) * lp["ds"] * (1 + e[0])
+            th = k * lp["dth"] * (1 + e[1]) if k else abs(e[1])
+            ph = j * lp["dth"] * (1 + e[2])
+            r = lp["h"] / s
+            vecs.append([r * np.sin(th) * np.cos(ph), r * np.sin(th) * np.sin(ph), r * np.cos(th)])
+        vecs += [[0, 0, 3 * lp["H"]], [0, 0, -3 * lp["H"]], [1e-300, 0, 2 * lp["H"]]]
+        vecs = np.array(vecs)
+        ex, fa = g.cone_ids(d, vecs)
+        ref = np.array([o.cone_of(d, v, np.zeros(3))[0][3] for v in vecs])
+        assert np.array_equal(ex, ref), d
+        assert np.array_equal(fa, ref), d
+
+
 def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     torch = torch_cuda
     wl, pts, sigma = _make((2000, 2, 4, 1, 2))
