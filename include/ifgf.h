@@ -58,7 +58,11 @@ typedef enum {
      * complex64 data */
     IFGF_MIXED = 1,
     /* IFGF_MIXED with the per-cone interpolation contraction on tensor cores
-     * (BF16 operands, FP32 accumulate); meant for many right-hand sides */
+     * (tcgen05, BF16 hi+lo operand split, FP32 accumulate), grouped by source cone;
+     * for many right-hand sides.  Used by ifgf_apply for even nrhs <= 64 (other
+     * nrhs and the adjoint run the IFGF_MIXED kernels); requires (P_s, P_ang) =
+     * (3, 5).  Contributions are added with asynchronous bulk reductions, so the
+     * last bits of the result vary from run to run. */
     IFGF_BATCHED_BF16 = 2
 } ifgf_precision;
 

@@ -16,6 +16,9 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
                                void *in_sorted, void *out_sorted, int mode, int adjoint, cudaStream_t st,
                                StageTimer &tm);
 
+cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
+                             void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
+
 static thread_local std::string g_create_error;
 
 static bool is_device_pointer(const void *ptr)
@@ -64,6 +67,10 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     if (levels < 3 || levels > IFGF_MAX_LEVELS) { g_create_error = "levels must be in [3, 20]"; return IFGF_EINVAL; }
     if (!((p_radial == 3 && p_angular == 5) || (p_radial == 4 && p_angular == 7))) {
         g_create_error = "supported (P_s, P_ang): (3, 5) and (4, 7)";
+        return IFGF_EINVAL;
+    }
+    if (opt && opt->precision == IFGF_BATCHED_BF16 && !(p_radial == 3 && p_angular == 5)) {
+        g_create_error = "IFGF_BATCHED_BF16 plans support (P_s, P_ang) = (3, 5)";
         return IFGF_EINVAL;
     }
     ifgf_options o = {0, 0, 1, IFGF_FP64, 0};
@@ -122,7 +129,8 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         if (o.leaf_nc == 0) p->lh[levels].nc = nc;
     }
     ifgf_status s = ifgf_build_plan(p, points, st);
-    if (s == IFGF_OK && (o.flags & 1)) s = ifgf_build_adjoint_lists(p, st);
+    // batched plans group evaluations by source cone with the transpose lists
+    if (s == IFGF_OK && ((o.flags & 1) || o.precision == IFGF_BATCHED_BF16)) s = ifgf_build_adjoint_lists(p, st);
     if (s != IFGF_OK) {
         g_create_error = p->last_error;
         cudaStreamSynchronize(st);
@@ -173,11 +181,13 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         if (s != IFGF_OK) return s;
     }
     p->timer.n = 0;
-    cudaError_t e = p->precision == IFGF_FP64
-                        ? ifgf_run_typed_f64(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st,
-                                             p->timer)
-                        : ifgf_run_typed_f32(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st,
-                                             p->timer);
+    cudaError_t e;
+    if (p->precision == IFGF_FP64)
+        e = ifgf_run_typed_f64(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+    else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nrhs % 2 == 0 && nrhs <= 64)
+        e = ifgf_run_batched(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
+    else
+        e = ifgf_run_typed_f32(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
     if (e != cudaSuccess) {
         p->last_error = std::string("kernel launch failed: ") + cudaGetErrorString(e);
         return IFGF_ECUDA;

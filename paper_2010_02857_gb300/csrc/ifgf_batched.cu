@@ -1,0 +1,485 @@
+// Batched right-hand sides on tensor cores (IFGF_BATCHED_BF16 plans).
+//
+// With many right-hand sides the interpolation of Algorithm 1 is a set of small
+// dense contractions that share their cone values: every evaluation that reads
+// relevant cone s of level d (a cousin target of Algorithm 1's target step, or a
+// parent interpolation point of its upward step) computes
+//     out[row][r] = f_row * sum_p W[row][p] F_s^d[p][r],   p < P = 75,
+// with real Lagrange weights W (Eq. defchebyshevinterpooperator, Lagrange form) and
+// a complex factor f_row (the centred factor G(x, x_k^d) of Eq. I_k for targets,
+// the re-centring factor G(x, x_k^d)/G(x, x_j^{d-1}) for parent points).  Grouping
+// the rows by source cone turns this into one GEMM per cone,
+//     D (rows x 2 nrhs) = A (rows x 80) * B (80 x 2 nrhs),
+// with B = the cone's values (re/im interleaved, 75 rows padded to 80) loaded once.
+//
+// k_cone_mma: one persistent CTA per SM walks the relevant cones of a level.  For
+// each cone it loads B into shared memory as BF16 hi + lo parts, and for each chunk
+// of 128 rows it writes A (hi + lo) and issues tcgen05.mma (kind::f16, BF16 inputs,
+// FP32 accumulation in tensor memory): Ahi Bhi + Ahi Blo + Alo Bhi per K block of
+// 16, which keeps ~16 significant bits of both operands.  The epilogue reads the
+// accumulator with tcgen05.ld, multiplies each row by its complex factor and adds
+// the row to its destination with one bulk asynchronous reduction
+// (cp.reduce.async.bulk ... add.f32) per row.  Destinations receive contributions
+// from several cones, so the summation order (and the last bits of the result)
+// varies from run to run on this path.
+//
+// The level-D direct sums (near field) and the leaf analytic factors are computed on
+// CUDA cores by warp-cooperative kernels: lanes own right-hand sides, and each
+// Green-function or analytic-factor value is computed once per pair and broadcast.
+#include <cuda_bf16.h>
+
+#include "ifgf_apply_impl.cuh"
+
+namespace ifgf {
+namespace batched {
+
+constexpr int kP = 75;        // nodes per cone (P_s = 3, P_ang = 5)
+constexpr int kK = 80;        // K padded to 5 blocks of 16
+constexpr int kM = 128;       // rows per MMA
+constexpr int kThreads = 128;
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor, no swizzle: start address, LBO = byte
+// stride between 8x16-byte core matrices along K, SBO = byte stride along M/N.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor: FP32 accumulate, BF16 A and B, A K-major, B MN-major
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void bf16_split(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// A (kM x kK, K-major): element (m, k) at (m/8)*SBO_A + (k/8)*128 + (m%8)*16 + (k%8)*2
+constexpr uint32_t SBO_A = (kK / 8) * 128;
+__device__ __forceinline__ uint32_t a_off(int m, int k) { return (m >> 3) * SBO_A + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2; }
+// B (kK x Npad, MN-major): element (k, n) at (k/8)*LBO_B + (n/8)*128 + (k%8)*16 + (n%8)*2, LBO_B = Npad/8*128
+__device__ __forceinline__ uint32_t b_off(int k, int n, uint32_t lbo_b)
+{
+    return (k >> 3) * lbo_b + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;
+}
+
+struct ConeKernelArgs {
+    int d;            // level of the cones
+    int nrhs;
+    int npad;         // 2 nrhs rounded up to a multiple of 16, <= 256
+    int tmem_cols;    // power of two >= max(32, npad)
+    int do_targets;   // cousin targets of level d -> u
+    int do_upward;    // parent interpolation points (d > 3) -> F^{d-1}
+    float2 *u;        // sorted fields [N][nrhs]
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernelArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const LevelDev &L = pd.lev[a.d];
+    const int npad = a.npad, nrhs = a.nrhs;
+    const uint32_t lbo_b = (uint32_t)(npad / 8) * 128;
+    unsigned char *A_hi = sm;
+    unsigned char *A_lo = A_hi + kM * kK * 2;
+    unsigned char *B_hi = A_lo + kM * kK * 2;
+    unsigned char *B_lo = B_hi + kK * npad * 2;
+    const int stage_stride = npad * 4 + 16;
+    unsigned char *stage = B_lo + kK * npad * 2;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // padding rows p = 75..79 of B stay zero for the whole kernel
+    for (int idx = tid; idx < (kK - kP) * npad; idx += kThreads) {
+        int p = kP + idx / npad, n = idx % npad;
+        *(__nv_bfloat16 *)(B_hi + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
+        *(__nv_bfloat16 *)(B_lo + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tbase;
+    const uint32_t idesc = umma_idesc(kM, npad);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    const LevelDev *Lp = a.d > 3 ? &pd.lev[a.d - 1] : nullptr;
+    const bool tab = a.do_upward && a.d > 3 && L.utab != nullptr;
+
+    for (int slot = blockIdx.x; slot < L.nact && !failed; slot += gridDim.x) {
+        const int t0 = a.do_targets ? L.tl_start[slot] : 0;
+        const int rows_t = a.do_targets ? L.tl_start[slot + 1] - t0 : 0;
+        const int u0 = (a.do_upward && a.d > 3) ? L.ul_start[slot] : 0;
+        const int rows_u = (a.do_upward && a.d > 3) ? L.ul_start[slot + 1] - u0 : 0;
+        const int rows = rows_t + rows_u;
+        if (rows == 0) continue;
+        // B: the cone's values, complex -> (re, im) columns 2r, 2r+1
+        const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
+        for (int idx = tid; idx < kP * (npad / 2); idx += kThreads) {
+            int p = idx / (npad / 2), r = idx % (npad / 2);
+            float2 v = r < nrhs ? F[(size_t)p * nrhs + r] : make_float2(0.f, 0.f);
+            __nv_bfloat16 h0, l0, h1, l1;
+            bf16_split(v.x, h0, l0);
+            bf16_split(v.y, h1, l1);
+            uint32_t off = b_off(p, 2 * r, lbo_b);
+            *(uint32_t *)(B_hi + off) = pack2(h0, h1);
+            *(uint32_t *)(B_lo + off) = pack2(l0, l1);
+        }
+        const int k = L.act_box[slot];
+        const double *ck = L.center + 3 * (size_t)k;
+        const int oct = (int)(L.key[k] & 7u);
+        for (int c0 = 0; c0 < rows; c0 += kM) {
+            const int row = c0 + tid;
+            const bool valid = row < rows;
+            float w[13];
+            cpx<float> f = {0.f, 0.f};
+            float2 *dest = nullptr;
+            if (valid) {
+                if (row < rows_t) {
+                    int i = L.tl[t0 + row];
+                    double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]),
+                           vz = __dsub_rn(pd.zs[i], ck[2]);
+                    ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
+                    f = green_r<float>(pd.kappa, g.r);
+                    dest = a.u + (size_t)i * nrhs;
+                } else {
+                    int e = L.ul[u0 + row - rows_t];
+                    int psl = e / kP, node = e % kP;
+                    int pcone = Lp->act_cone[psl];
+                    int trow = tab ? table_row(L.ubits, L.urank, pcone) : -1;
+                    if (trow >= 0) {
+                        const UpEntry<float, 13> &en = ((const UpEntry<float, 13> *)L.utab)[((size_t)trow * 8 + oct) * kP + node];
+#pragma unroll
+                        for (int m = 0; m < 13; ++m) w[m] = en.w[m];
+                        f = {en.fr, en.fi};
+                    } else {
+                        up_geometry<float, 3, 5>(pd, L, *Lp, pcone, node, oct, w, f);
+                    }
+                    dest = (float2 *)Lp->F + ((size_t)psl * kP + node) * nrhs;
+                }
+            }
+            // A row: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c; 16-byte stores of 8 k
+#pragma unroll
+            for (int kc = 0; kc < kK / 8; ++kc) {
+                uint32_t hv[4], lv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float x2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        int p = kc * 8 + q * 2 + h;
+                        float x = 0.f;
+                        if (valid && p < kP) {
+                            int ia = p / 25, ib = (p / 5) % 5, ic = p % 5;
+                            x = w[ia] * w[3 + ib] * w[8 + ic];
+                        }
+                        x2[h] = x;
+                    }
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    bf16_split(x2[0], h0, l0);
+                    bf16_split(x2[1], h1, l1);
+                    hv[q] = pack2(h0, h1);
+                    lv[q] = pack2(l0, l1);
+                }
+                uint32_t off = a_off(tid, kc * 8);
+                *(uint4 *)(A_hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                *(uint4 *)(A_lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            // this thread's previous bulk reduction must have read its stage row
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
+#pragma unroll
+                for (int kb = 0; kb < kK / 16; ++kb) {
+                    uint64_t dah = umma_desc(ah + kb * 256, 128, SBO_A);
+                    uint64_t dal = umma_desc(al + kb * 256, 128, SBO_A);
+                    uint64_t dbh = umma_desc(bh + kb * 2 * lbo_b, lbo_b, 128);
+                    uint64_t dbl = umma_desc(bl + kb * 2 * lbo_b, lbo_b, 128);
+                    uint32_t acc0 = kb > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0)
+                        : "memory");
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dah), "l"(dbl), "r"(idesc), "r"(1u)
+                        : "memory");
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mbar))
+                             : "memory");
+            }
+            uint32_t done = 0;
+            for (int it = 0; it < kWaitLimit && !done; ++it) {
+                asm volatile(
+                    "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+                    : "=r"(done)
+                    : "r"(smem_u32(&mbar)), "r"(phase)
+                    : "memory");
+            }
+            // the decision must be the same for every thread of the CTA
+            if (__syncthreads_or(done ? 0 : 1)) {
+                if (tid == 0) atomicAdd(pd.err, 1);
+                failed = true;
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // epilogue: row tid of the accumulator, times its factor, to the stage row
+            float *srow = (float *)(stage + (size_t)tid * stage_stride);
+            for (int cb = 0; cb < npad; cb += 32) {
+                uint32_t v[32];
+                uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        if (cb + j < 2 * nrhs) {  // the stage row holds 2 nrhs floats
+                            float re = __uint_as_float(v[j]), im = __uint_as_float(v[j + 1]);
+                            srow[cb + j] = f.x * re - f.y * im;
+                            srow[cb + j + 1] = f.x * im + f.y * re;
+                        }
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (valid) {
+                asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                                 (uint64_t)__cvta_generic_to_global(dest)),
+                             "r"(smem_u32(srow)), "r"((uint32_t)(nrhs * 8))
+                             : "memory");
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// Near field, one warp per target: lanes compute G for 32 sources at a time, then
+// every lane accumulates its right-hand sides r = lane, lane + 32, ...
+template <int RPL>
+__global__ void __launch_bounds__(128) k_near_batched(PlanDev pd, int nrhs, const float2 *sig, float2 *us, int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= pd.n) return;
+    cpx<float> acc[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) acc[q] = {0.f, 0.f};
+    if (mode & 1) {
+        const LevelDev &LD = pd.lev[pd.D];
+        const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+        const int b = LD.pt_box[i];
+        for (int e = 0; e < 27; ++e) {
+            int k = LD.nbr[27 * (size_t)b + e];
+            if (k < 0) break;
+            const int j1 = LD.start[k + 1];
+            for (int j0 = LD.start[k]; j0 < j1; j0 += 32) {
+                int j = j0 + lane;
+                cpx<float> G = {0.f, 0.f};
+                if (j < j1 && j != i) G = green_r<float>(pd.kappa, dist<float>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]));
+                int cnt = min(32, j1 - j0);
+                for (int t = 0; t < cnt; ++t) {
+                    float gx = __shfl_sync(0xffffffffu, G.x, t), gy = __shfl_sync(0xffffffffu, G.y, t);
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) {
+                        int r = lane + 32 * q;
+                        if (r < nrhs) {
+                            float2 s = sig[(size_t)(j0 + t) * nrhs + r];
+                            acc[q].x += gx * s.x - gy * s.y;
+                            acc[q].y += gx * s.y + gy * s.x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        int r = lane + 32 * q;
+        if (r < nrhs) us[(size_t)i * nrhs + r] = make_float2(acc[q].x, acc[q].y);
+    }
+}
+
+// Leaf analytic factors, one warp per (relevant leaf cone, interpolation point).
+template <int RPL>
+__global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, const float2 *sig)
+{
+    const LevelDev &L = pd.lev[pd.D];
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)L.nact * kP) return;
+    const int slot = (int)(w / kP), node = (int)(w % kP);
+    const int b = L.act_box[slot];
+    const double *c = L.center + 3 * (size_t)b;
+    double q[3];
+    const double R0 = node_pos(L, 3, 5, L.act_cone[slot], node, c[0], c[1], c[2], q, nullptr);
+    cpx<float> acc[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) acc[t] = {0.f, 0.f};
+    const int j1 = L.start[b + 1];
+    for (int j0 = L.start[b]; j0 < j1; j0 += 32) {
+        int j = j0 + lane;
+        float gx = 0.f, gy = 0.f;
+        if (j < j1) {
+            double r1 = dist<float>(q[0] - pd.xs[j], q[1] - pd.ys[j], q[2] - pd.zs[j]);
+            float cc, ss;
+            expi(pd.kappa * (r1 - R0), cc, ss);
+            float amp = (float)R0 / (float)r1;
+            gx = amp * cc;
+            gy = amp * ss;
+        }
+        int cnt = min(32, j1 - j0);
+        for (int t = 0; t < cnt; ++t) {
+            float ax = __shfl_sync(0xffffffffu, gx, t), ay = __shfl_sync(0xffffffffu, gy, t);
+#pragma unroll
+            for (int u = 0; u < RPL; ++u) {
+                int r = lane + 32 * u;
+                if (r < nrhs) {
+                    float2 s = sig[(size_t)(j0 + t) * nrhs + r];
+                    acc[u].x += ax * s.x - ay * s.y;
+                    acc[u].y += ax * s.y + ay * s.x;
+                }
+            }
+        }
+    }
+    float2 *F = (float2 *)L.F + ((size_t)slot * kP + node) * nrhs;
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) {
+        int r = lane + 32 * u;
+        if (r < nrhs) F[r] = make_float2(acc[u].x, acc[u].y);
+    }
+}
+
+template <int RPL>
+cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, float2 *us, int mode, cudaStream_t st,
+                             StageTimer &tm)
+{
+    if (mode & 2) {
+        int64_t warps = (int64_t)pd.lev[pd.D].nact * kP;
+        if (warps > 0) k_leaf_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig);
+        tm.mark(STAGE_LEAF, warps > 0, st);
+    }
+    int64_t warps = pd.n;
+    k_near_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
+    tm.mark(STAGE_EVAL, 1, st);
+    return cudaGetLastError();
+}
+
+}  // namespace batched
+}  // namespace ifgf
+
+// Shared memory of k_cone_mma for npad columns.
+static size_t cone_mma_smem(int npad)
+{
+    using namespace ifgf::batched;
+    return (size_t)2 * kM * kK * 2 + (size_t)2 * kK * npad * 2 + (size_t)kM * (npad * 4 + 16);
+}
+
+// Forward apply of a batched plan (device pointers to Morton-ordered buffers).
+cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
+                             void *out_sorted, int mode, cudaStream_t st, StageTimer &tm)
+{
+    using namespace ifgf;
+    using namespace ifgf::batched;
+    const int n = pd.n;
+    int64_t tot = (int64_t)n * nrhs;
+    tm.mark(-1, 0, st);
+    k_permute_in<float><<<grid_for(tot, 256), 256, 0, st>>>(in_user, in_sorted, pd.perm, n, nrhs);
+    tm.mark(STAGE_PERMUTE_IN, 1, st);
+    const float2 *sig = (const float2 *)in_sorted;
+    float2 *us = (float2 *)out_sorted;
+    cudaError_t e;
+    int rpl = (nrhs + 31) / 32;
+    if (rpl <= 1) e = launch_cuda_core<1>(pd, nrhs, sig, us, mode, st, tm);
+    else if (rpl <= 2) e = launch_cuda_core<2>(pd, nrhs, sig, us, mode, st, tm);
+    else e = launch_cuda_core<4>(pd, nrhs, sig, us, mode, st, tm);
+    if (e != cudaSuccess) return e;
+    if (mode & 2) {
+        const int npad = ((2 * nrhs + 15) / 16) * 16;
+        int tcols = 32;
+        while (tcols < npad) tcols *= 2;
+        const size_t smem = cone_mma_smem(npad);
+        e = cudaFuncSetAttribute(k_cone_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int nl = 0;
+        for (int d = pd.D; d >= 3; --d) {
+            const LevelDev &L = pd.lev[d];
+            if (d > 3) {
+                const LevelDev &Lp = pd.lev[d - 1];
+                e = cudaMemsetAsync(Lp.F, 0, (size_t)Lp.nact * kP * nrhs * sizeof(float2), st);
+                if (e != cudaSuccess) return e;
+            }
+            if (L.nact == 0) continue;
+            ConeKernelArgs a;
+            a.d = d;
+            a.nrhs = nrhs;
+            a.npad = npad;
+            a.tmem_cols = tcols;
+            a.do_targets = 1;
+            a.do_upward = d > 3;
+            a.u = us;
+            int grid = std::min(L.nact, 152);
+            k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
+            ++nl;
+        }
+        tm.mark(STAGE_UPWARD, nl, st);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_permute_out<float><<<grid_for(tot, 256), 256, 0, st>>>(out_sorted, out_user, pd.perm, n, nrhs);
+    tm.mark(STAGE_PERMUTE_OUT, 1, st);
+    return cudaGetLastError();
+}

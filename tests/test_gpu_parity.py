@@ -196,6 +196,31 @@ def test_cone_index_fast_path_is_exact_on_cell_boundaries(pkg, torch_cuda):
         assert np.array_equal(fa, ref), d
 
 
+@pytest.mark.parametrize("nrhs", [2, 8, 64])
+def test_batched_tensor_core_path_matches_mixed_and_oracle(pkg, torch_cuda, nrhs):
+    # BF16 hi+lo operands keep ~16 significant bits: the contraction error is
+    # ~2^-16 times the Lebesgue constant of the 3x5x5 interpolant (< 10), so 2e-4
+    # relative l2 against the FP32 path; and <= 1e-3 against the direct sum
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    sig = wi.complex_normal(60 + nrhs, (nrhs, wl.n))
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched")
+    m = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="mixed")
+    s = torch.from_numpy(sig).cuda()
+    ub = b.apply(s).cpu().numpy()
+    um = m.apply(s).cpu().numpy()
+    assert b.check() == 0
+    for r in range(nrhs):
+        assert rel(ub[r], um[r]) < 2e-4, (r, rel(ub[r], um[r]))
+    # stage-wise: near field only is exact FP32 work, far field alone
+    assert rel(b.apply_partial(s, 1).cpu().numpy(), m.apply_partial(s, 1).cpu().numpy()) < 1e-6
+    assert rel(b.apply_partial(s, 2).cpu().numpy(), m.apply_partial(s, 2).cpu().numpy()) < 2e-4
+    ex = oracle.direct(pts, wl.kappa, sig[:2])
+    for r in range(2):
+        assert rel(ub[r], ex[r]) < 1e-3
+    assert b.check() == 0
+
+
 def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     torch = torch_cuda
     wl, pts, sigma = _make((2000, 2, 4, 1, 2))
