@@ -191,7 +191,7 @@ def main():
     ap.add_argument("--ref-targets", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched"],
                     help="override the workload's precision")
     args = ap.parse_args()
     wl = wi.WORKLOADS[args.workload]
@@ -208,7 +208,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    precision = args.precision or {"fp64": "fp64", "mixed": "mixed", "batched": "mixed"}[wl.precision]
+    precision = args.precision or wl.precision
     pts = torch.from_numpy(wl.points()).to(dev)
     t0 = time.perf_counter()
     plan = pkg.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc,
@@ -266,19 +266,40 @@ def main():
     e2e_s = float(np.median(e2e_times))
     eb = 16 if precision == "fp64" else 8
 
-    # roofline of the dominant stage (upward interpolation, FP64-pipe bound)
+    # roofline of the dominant kernel
     st = timings["stages"]
     calls = max(1, timings["calls"])
     up_ms = st["upward"]["ms"] / calls
     up_launches = st["upward"]["launches"] / calls
     up_evals = sum(lv["upward_evals"] for lv in stats["level"])
-    peak, peak_src = fp64_peak_tflops(clk.get("sm_mhz"))
-    achieved = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_upward", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": peak_src,
-                "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
-                        f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+    cousin_evals = sum(lv["cousin_evals"] for lv in stats["level"])
+    f_mhz = clk.get("sm_mhz") or 2070.0
+    if precision == "batched":
+        # tcgen05 cone kernels: every cousin and upward evaluation is one GEMM row of
+        # 75 weights x 2 nrhs real columns (useful flops; the BF16 hi/lo split and
+        # the padding of K to 80 are not counted)
+        rows = up_evals + cousin_evals
+        flops = rows * 2 * 75 * 2 * nrhs
+        peak = float(measured_peaks().get("bf16_tflops", 1900.0))
+        roofline = {"bound": "tensor", "kernel": "k_cone_mma", "peak_source": "measured bf16 dense (burst)",
+                    "work": f"{rows} GEMM rows x {2 * 75 * 2 * nrhs} flops per apply, "
+                            f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+    elif precision == "mixed":
+        flops = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs
+        peak = 2 * 128 * NUM_SMS * f_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source":
+                    f"derived FP32: 128 FMA/clk/SM x {NUM_SMS} SMs x {f_mhz:.0f} MHz",
+                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP32 flops per RHS, "
+                            f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+    else:
+        flops = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs
+        peak, psrc = fp64_peak_tflops(clk.get("sm_mhz"))
+        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source": psrc,
+                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
+                            f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+    achieved = flops / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
+    roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None})
 
     check = None
     if args.check:
@@ -292,7 +313,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if precision == "fp64" else "f32+f64",
+                "dtype": {"fp64": "f64", "mixed": "f32+f64", "batched": "bf16x3+f32+f64"}[precision],
                 "data": "synthetic",
                 "config": {"workload": wl.name, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
                            "p_radial": wl.p_radial, "p_angular": wl.p_angular,

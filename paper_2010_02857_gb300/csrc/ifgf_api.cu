@@ -180,6 +180,10 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         ifgf_status s = ifgf_build_adjoint_lists(p, st);
         if (s != IFGF_OK) return s;
     }
+    if (adjoint && !p->adjoint_values_ready) {
+        ifgf_status s = ifgf_alloc_adjoint_values(p);
+        if (s != IFGF_OK) return s;
+    }
     p->timer.n = 0;
     cudaError_t e;
     if (p->precision == IFGF_FP64)

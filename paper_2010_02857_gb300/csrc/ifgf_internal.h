@@ -139,6 +139,7 @@ struct ifgf_plan {
     void *stage_in = nullptr;     // staging for host-pointer calls
     void *stage_out = nullptr;
     bool adjoint_ready = false;
+    bool adjoint_values_ready = false;
     int last_nrhs = 1;
     cudaStream_t build_stream = nullptr;
     std::string last_error;
@@ -161,6 +162,7 @@ template <typename T, int NW> struct UpEntry {
 // plan.cu
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
+ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p);
 void *ifgf_dalloc(ifgf_plan *p, size_t bytes);
 // apply_*.cu: fill the upward table of level d (entries already allocated)
 cudaError_t ifgf_build_uptable_f64(const PlanDev &pd, int d, void *tab, cudaStream_t st);

@@ -906,16 +906,29 @@ static ifgf_status sort_to_csr(ifgf_plan *p, int *keys, int *vals, int64_t m, in
     return IFGF_OK;
 }
 
+// adjoint cone-value buffers (allocated on the first adjoint call)
+ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p)
+{
+    if (p->adjoint_values_ready) return IFGF_OK;
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    for (int d = 3; d <= p->D; ++d) {
+        LevelDev &L = p->dev.lev[d];
+        L.Fadj = ifgf_dalloc(p, (size_t)L.nact * p->P * p->max_nrhs * eb);
+        if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
+    }
+    p->adjoint_values_ready = true;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
 {
     if (p->adjoint_ready) return IFGF_OK;
     PlanDev &pd = p->dev;
     const int n = (int)p->n, D = p->D, P = p->P;
     const size_t eb = ifgf_elem_bytes(p->precision);
+    (void)eb;
     for (int d = 3; d <= D; ++d) {
         LevelDev &L = pd.lev[d];
-        L.Fadj = ifgf_dalloc(p, (size_t)L.nact * P * p->max_nrhs * eb);
-        if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
         // targets
         {
             Scratch cnt, off;
