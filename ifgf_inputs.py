@@ -247,6 +247,11 @@ WORKLOADS = {
     "sphere_8lambda": Workload("sphere_8lambda", 98_304, wavelengths_to_kappa(2.0, 8), 6,
                                leaf_ns=1, leaf_nc=2, targets=2_000, seed=6, surface="sphere",
                                description="Fibonacci sphere N=98304, 8 lambda, D=6, FP64"),
+    # the same sphere with 16 right-hand sides on the tensor-core path (profiling size)
+    "sphere_8lambda_16rhs": Workload("sphere_8lambda_16rhs", 98_304, wavelengths_to_kappa(2.0, 8), 6,
+                                     leaf_ns=1, leaf_nc=2, nrhs=16, targets=1_000, seed=7, surface="sphere",
+                                     precision="batched",
+                                     description="Fibonacci sphere N=98304, 8 lambda, D=6, 16 RHS batched"),
     # unit sphere, diameter 32 wavelengths, D = 8
     "sphere_32lambda": Workload("sphere_32lambda", 393_216, wavelengths_to_kappa(2.0, 32), 8,
                                 leaf_ns=1, leaf_nc=2, targets=2_000, seed=2, surface="sphere",

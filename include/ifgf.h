@@ -74,7 +74,10 @@ typedef struct {
     int flags;      /* bit 0: build the adjoint's transpose lists at plan time;
                        bit 1: no upward tables (compute the upward geometry per
                        evaluation; by default a level whose geometry table is at most
-                       half its evaluation count gets one) */
+                       half its evaluation count gets one);
+                       bit 2: IFGF_BATCHED_BF16 plans do not cache the cousin
+                       targets' local coordinates and centred factors at plan time
+                       (24 bytes per cousin evaluation; cached by default) */
 } ifgf_options;
 
 /*

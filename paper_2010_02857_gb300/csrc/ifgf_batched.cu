@@ -18,8 +18,9 @@
 // FP32 accumulation in tensor memory): Ahi Bhi + Ahi Blo + Alo Bhi per K block of
 // 16, which keeps ~16 significant bits of both operands.  The epilogue reads the
 // accumulator with tcgen05.ld, multiplies each row by its complex factor and adds
-// the row to its destination with one bulk asynchronous reduction
-// (cp.reduce.async.bulk ... add.f32) per row.  Destinations receive contributions
+// the row to its destination with bulk asynchronous reductions
+// (cp.reduce.async.bulk ... add.f32, 16 right-hand sides per reduction; faster here
+// than per-thread vector reductions).  Destinations receive contributions
 // from several cones, so the summation order (and the last bits of the result)
 // varies from run to run on this path.
 //
@@ -38,6 +39,7 @@ constexpr int kK = 80;        // K padded to 5 blocks of 16
 constexpr int kM = 128;       // rows per MMA
 constexpr int kThreads = 128;
 constexpr int kWaitLimit = 1 << 22;
+constexpr int kStageStride = 32 * 4 + 16;  // one epilogue pass: 32 floats per row, padded
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -89,7 +91,7 @@ struct ConeKernelArgs {
     float2 *u;        // sorted fields [N][nrhs]
 };
 
-__global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernelArgs a)
+__global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernelArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -102,7 +104,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
     unsigned char *A_lo = A_hi + kM * kK * 2;
     unsigned char *B_hi = A_lo + kM * kK * 2;
     unsigned char *B_lo = B_hi + kK * npad * 2;
-    const int stage_stride = npad * 4 + 16;
     unsigned char *stage = B_lo + kK * npad * 2;
 
     if (tid == 0) {
@@ -162,11 +163,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
             float2 *dest = nullptr;
             if (valid) {
                 if (row < rows_t) {
-                    int i = L.tl[t0 + row];
-                    double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]),
-                           vz = __dsub_rn(pd.zs[i], ck[2]);
-                    ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
-                    f = green_r<float>(pd.kappa, g.r);
+                    const int e = t0 + row;
+                    const int i = L.tl[e];
+                    if (L.tl_loc) {
+                        float4 t = L.tl_loc[e];
+                        float2 G = L.tl_fac[e];
+                        lagrange<float>(3, pd.ts, pd.its, t.x, w);
+                        lagrange<float>(5, pd.ta, pd.ita, t.y, w + 3);
+                        lagrange<float>(5, pd.ta, pd.ita, t.z, w + 8);
+                        f = {G.x, G.y};
+                    } else {
+                        double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]),
+                               vz = __dsub_rn(pd.zs[i], ck[2]);
+                        ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
+                        f = green_r<float>(pd.kappa, g.r);
+                    }
                     dest = a.u + (size_t)i * nrhs;
                 } else {
                     int e = L.ul[u0 + row - rows_t];
@@ -212,8 +223,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
                 *(uint4 *)(A_lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            // this thread's previous bulk reduction must have read its stage row
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -261,9 +270,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
             }
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // epilogue: row tid of the accumulator, times its factor, to the stage row
-            float *srow = (float *)(stage + (size_t)tid * stage_stride);
-            for (int cb = 0; cb < npad; cb += 32) {
+            // epilogue, 32 accumulator columns (16 right-hand sides) per pass: row tid
+            // times its factor goes to the stage row and is added to its destination by
+            // one bulk asynchronous reduction per pass
+            float *srow = (float *)(stage + (size_t)tid * kStageStride);
+            for (int cb = 0; cb < 2 * nrhs; cb += 32) {
                 uint32_t v[32];
                 uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
                 asm volatile(
@@ -276,25 +287,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
                       "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // the previous pass's reduction must have read the stage row
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                const int ncol = min(32, 2 * nrhs - cb);
                 if (valid) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 2) {
-                        if (cb + j < 2 * nrhs) {  // the stage row holds 2 nrhs floats
+                        if (j < ncol) {
                             float re = __uint_as_float(v[j]), im = __uint_as_float(v[j + 1]);
-                            srow[cb + j] = f.x * re - f.y * im;
-                            srow[cb + j + 1] = f.x * im + f.y * re;
+                            srow[j] = f.x * re - f.y * im;
+                            srow[j + 1] = f.x * im + f.y * re;
                         }
                     }
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (valid) {
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                                     (uint64_t)__cvta_generic_to_global((float *)dest + cb)),
+                                 "r"(smem_u32(srow)), "r"((uint32_t)(ncol * 4))
+                                 : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (valid) {
-                asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                                 (uint64_t)__cvta_generic_to_global(dest)),
-                             "r"(smem_u32(srow)), "r"((uint32_t)(nrhs * 8))
-                             : "memory");
-            }
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
@@ -305,6 +319,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_cone_mma(PlanDev pd, ConeKernel
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// Plan-time cache of the target rows' geometry: for every entry e of the transpose
+// list of level d (cousin target i of the box k of slot s), the local coordinates of
+// x_i in its cone and the centred factor G(x_i, x_k^d).  These do not depend on the
+// densities; the apply then only expands the Lagrange weights.
+__global__ void k_cache_target_geometry(PlanDev pd, int d, float4 *loc, float2 *fac, int64_t m)
+{
+    const LevelDev &L = pd.lev[d];
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    // slot of entry e: last s with tl_start[s] <= e
+    int lo = 0, hi = L.nact;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (L.tl_start[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int k = L.act_box[lo];
+    const int i = L.tl[e];
+    const double *ck = L.center + 3 * (size_t)k;
+    double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]), vz = __dsub_rn(pd.zs[i], ck[2]);
+    ConeGeom g = cone_of_fast(L, vx, vy, vz);
+    if (g.cone != L.act_cone[lo]) atomicAdd(pd.err, 1);
+    float t[3];
+    local_coords_f32(L, g, vx, vy, vz, t);
+    loc[e] = make_float4(t[0], t[1], t[2], 0.f);
+    cpx<float> G = green_r<float>(pd.kappa, g.r);
+    fac[e] = make_float2(G.x, G.y);
 }
 
 // Near field, one warp per target: lanes compute G for 32 sources at a time, then
@@ -425,7 +467,7 @@ cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, flo
 static size_t cone_mma_smem(int npad)
 {
     using namespace ifgf::batched;
-    return (size_t)2 * kM * kK * 2 + (size_t)2 * kK * npad * 2 + (size_t)kM * (npad * 4 + 16);
+    return (size_t)2 * kM * kK * 2 + (size_t)2 * kK * npad * 2 + (size_t)kM * kStageStride;
 }
 
 // Forward apply of a batched plan (device pointers to Morton-ordered buffers).
@@ -471,7 +513,7 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
             a.do_targets = 1;
             a.do_upward = d > 3;
             a.u = us;
-            int grid = std::min(L.nact, 152);
+            int grid = std::min(L.nact, 2 * 152);
             k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
             ++nl;
         }
@@ -481,5 +523,12 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
     }
     k_permute_out<float><<<grid_for(tot, 256), 256, 0, st>>>(out_sorted, out_user, pd.perm, n, nrhs);
     tm.mark(STAGE_PERMUTE_OUT, 1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t ifgf_cache_target_geometry(const PlanDev &pd, int d, float4 *loc, float2 *fac, int64_t m, cudaStream_t st)
+{
+    if (m == 0) return cudaSuccess;
+    ifgf::batched::k_cache_target_geometry<<<(int)((m + 255) / 256), 256, 0, st>>>(pd, d, loc, fac, m);
     return cudaGetLastError();
 }

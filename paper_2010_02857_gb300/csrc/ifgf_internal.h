@@ -67,6 +67,10 @@ struct LevelDev {
     const int *tl = nullptr;
     const int *ul_start = nullptr;     // adjoint: per slot, parent (slot*P + node) landing in it
     const int *ul = nullptr;
+    // batched plans: per entry of tl, the target's local coordinates in its cone
+    // (x, y, z = s, theta, phi in [-1, 1]) and its centred factor G(x, x_k^d)
+    const float4 *tl_loc = nullptr;
+    const float2 *tl_fac = nullptr;
     // Upward table of the step from this level d to d-1 (absent: computed on the fly).
     // Rows are the distinct relevant cone ids of level d-1 (union bitmap + rank);
     // entry (row, octant, node) holds the child cone id, the Lagrange weights of the
@@ -163,6 +167,7 @@ template <typename T, int NW> struct UpEntry {
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
 ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p);
+cudaError_t ifgf_cache_target_geometry(const PlanDev &pd, int d, float4 *loc, float2 *fac, int64_t m, cudaStream_t st);
 void *ifgf_dalloc(ifgf_plan *p, size_t bytes);
 // apply_*.cu: fill the upward table of level d (entries already allocated)
 cudaError_t ifgf_build_uptable_f64(const PlanDev &pd, int d, void *tab, cudaStream_t st);

@@ -949,6 +949,13 @@ ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
             if (s != IFGF_OK) return s;
             L.tl_start = start;
             L.tl = list;
+            if (p->precision == IFGF_BATCHED_BF16 && !(p->flags & 4) && m > 0) {
+                DALLOC(tloc, float4, m);
+                DALLOC(tfac, float2, m);
+                CK(ifgf_cache_target_geometry(pd, d, tloc, tfac, m, st));
+                L.tl_loc = tloc;
+                L.tl_fac = tfac;
+            }
         }
         if (d >= 4) {
             LevelDev &Lp = pd.lev[d - 1];

@@ -210,6 +210,11 @@ def test_batched_tensor_core_path_matches_mixed_and_oracle(pkg, torch_cuda, nrhs
     ub = b.apply(s).cpu().numpy()
     um = m.apply(s).cpu().numpy()
     assert b.check() == 0
+    # without the plan-time target geometry cache the result is the same
+    b2 = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched",
+                  flags=4)
+    assert rel(b2.apply(s).cpu().numpy(), ub) < 1e-5
+    assert b2.check() == 0
     for r in range(nrhs):
         assert rel(ub[r], um[r]) < 2e-4, (r, rel(ub[r], um[r]))
     # stage-wise: near field only is exact FP32 work, far field alone
