@@ -268,7 +268,7 @@ WORKLOADS = {
                             description="three-cube union N=1572864, lambda=1, 64 RHS"),
     # unit sphere, diameter 256 wavelengths, D = 9, 8 RHS
     "sphere_256lambda": Workload("sphere_256lambda", 25_165_824, wavelengths_to_kappa(2.0, 256), 9,
-                                 leaf_ns=4, leaf_nc=8, nrhs=8, targets=1_024, seed=5, surface="sphere",
+                                 leaf_ns=3, leaf_nc=6, nrhs=8, targets=1_024, seed=5, surface="sphere",
                                  precision="mixed",
                                  description="Fibonacci sphere N=25165824, 256 lambda, D=9, 8 RHS"),
 }

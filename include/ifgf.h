@@ -77,7 +77,16 @@ typedef struct {
                        half its evaluation count gets one);
                        bit 2: IFGF_BATCHED_BF16 plans do not cache the cousin
                        targets' local coordinates and centred factors at plan time
-                       (24 bytes per cousin evaluation; cached by default) */
+                       (24 bytes per cousin evaluation; cached by default);
+                       bit 3: keep only two levels' cone values (always on when the
+                       values of all levels exceed the budget below);
+                       bit 4: process at most 2 right-hand sides per pass (testing) */
+    long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
+                       memory at plan time.  When the values of every level for
+                       max_nrhs right-hand sides exceed it, the plan keeps two levels
+                       (d and d-1) and applies right-hand sides in chunks that fit; the
+                       per-level values returned by ifgf_plan_get_values are then those
+                       of the last two levels written */
 } ifgf_options;
 
 /*

@@ -33,7 +33,7 @@ static bool is_device_pointer(const void *ptr)
 
 static void free_plan(ifgf_plan *p)
 {
-    for (int i = 0; i < 64; ++i)
+    for (int i = 0; i < StageTimer::kMax; ++i)
         if (p->timer.ev[i]) cudaEventDestroy(p->timer.ev[i]);
     for (void *ptr : p->allocs) cudaFree(ptr);
     p->allocs.clear();
@@ -73,8 +73,9 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         g_create_error = "IFGF_BATCHED_BF16 plans support (P_s, P_ang) = (3, 5)";
         return IFGF_EINVAL;
     }
-    ifgf_options o = {0, 0, 1, IFGF_FP64, 0};
+    ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0};
     if (opt) o = *opt;
+    if (o.value_budget_bytes < 0) { g_create_error = "value_budget_bytes must be >= 0"; return IFGF_EINVAL; }
     if (o.max_nrhs <= 0) o.max_nrhs = 1;
     if (o.max_nrhs > 1024) { g_create_error = "max_nrhs must be <= 1024"; return IFGF_EINVAL; }
     if (o.precision != IFGF_FP64 && o.precision != IFGF_MIXED && o.precision != IFGF_BATCHED_BF16) {
@@ -96,6 +97,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     p->precision = o.precision;
     p->max_nrhs = o.max_nrhs;
     p->flags = o.flags;
+    p->value_budget = (size_t)o.value_budget_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     p->build_stream = st;
     // leaf cones need H_D, known only after the root cube: the builder reads lh[D]
@@ -185,13 +187,20 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         if (s != IFGF_OK) return s;
     }
     p->timer.n = 0;
-    cudaError_t e;
-    if (p->precision == IFGF_FP64)
-        e = ifgf_run_typed_f64(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
-    else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nrhs % 2 == 0 && nrhs <= 64)
-        e = ifgf_run_batched(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
-    else
-        e = ifgf_run_typed_f32(p->dev, nrhs, din, dout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+    cudaError_t e = cudaSuccess;
+    // right-hand sides in chunks of at most rhs_chunk: a chunk is a contiguous block
+    // of rows of the caller's [nrhs][N] arrays
+    for (int c0 = 0; c0 < nrhs && e == cudaSuccess; c0 += p->rhs_chunk) {
+        const int nc = std::min(p->rhs_chunk, nrhs - c0);
+        const void *cin = (const char *)din + (size_t)c0 * p->n * eb;
+        void *cout = (char *)dout + (size_t)c0 * p->n * eb;
+        if (p->precision == IFGF_FP64)
+            e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+        else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nc % 2 == 0 && nc <= 64)
+            e = ifgf_run_batched(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
+        else
+            e = ifgf_run_typed_f32(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+    }
     if (e != cudaSuccess) {
         p->last_error = std::string("kernel launch failed: ") + cudaGetErrorString(e);
         return IFGF_ECUDA;
@@ -354,9 +363,11 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
     char tmp[512];
     snprintf(tmp, sizeof tmp,
              "\"n\": %lld, \"levels\": %d, \"P\": %d, \"kappa\": %.17g, \"precision\": %d, \"max_nrhs\": %d, "
-             "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, \"level\": [",
+             "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, "
+             "\"pingpong\": %d, \"rhs_chunk\": %d, \"level\": [",
              (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
-             (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes);
+             (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes,
+             plan->pingpong ? 1 : 0, plan->rhs_chunk);
     s += tmp;
     for (int d = 1; d <= plan->D; ++d) {
         const LevelHost &h = plan->lh[d];
@@ -431,7 +442,7 @@ extern "C" ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on)
 {
     if (!plan) return IFGF_EINVAL;
     if (on && !plan->timer.ev[0]) {
-        for (int i = 0; i < 64; ++i)
+        for (int i = 0; i < StageTimer::kMax; ++i)
             if (cudaEventCreate(&plan->timer.ev[i]) != cudaSuccess) {
                 plan->last_error = "event creation failed";
                 return IFGF_ECUDA;

@@ -118,6 +118,35 @@ template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, do
     return {a * c, a * s};
 }
 
+// Analytic factor g(q, x_j) = (R/|q - x_j|) e^{i kappa (|q - x_j| - R)} (Eq. factored_f) for
+// an interpolation point q = x_k + R dir of a leaf cone and a source x_j = x_k + delta in
+// the same leaf box.  Double plans evaluate it as written.  Float plans use
+// |q - x_j| - R = (|delta|^2 - 2 R dir.delta) / (|q - x_j| + R): the numerator, where the
+// cancellation of the plain difference lives, is formed in FP64 from the stored FP64
+// offset; the denominator and the rest need only FP32 relative accuracy.
+template <typename T>
+__device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const double *q, const double *dir, int j)
+{
+    if constexpr (sizeof(T) == 8) {
+        double r1 = dist<T>(q[0] - pd.xs[j], q[1] - pd.ys[j], q[2] - pd.zs[j]);
+        double c, s;
+        expi(pd.kappa * (r1 - R), c, s);
+        double a = R / r1;
+        return {a * c, a * s};
+    } else {
+        const dbl4 o = pd.leaf_off[j];
+        double num = fma(-2.0 * R, dir[0] * o.x + dir[1] * o.y + dir[2] * o.z, o.w);
+        float Rf = (float)R;
+        float r1 = sqrtf(fmaxf(Rf * Rf + (float)num, 0.f));
+        float den = r1 + Rf;
+        float ph = (float)(pd.kappa * num * (double)(1.0f / den));
+        float c, s;
+        sincosf(ph, &s, &c);
+        float a = Rf / r1;
+        return {a * c, a * s};
+    }
+}
+
 // cone cell (bit-identical to cone_of), Lagrange weights and distance of the vector v
 template <typename T, int PS, int PA>
 __device__ __forceinline__ ConeGeom geom_weights(const PlanDev &pd, const LevelDev &L, double vx, double vy,
@@ -189,22 +218,15 @@ __global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int nrhs, const void *
     int slot = (int)(t / P), node = (int)(t % P);
     int b = L.act_box[slot];
     const double *c = L.center + 3 * (size_t)b;
-    double q[3];
-    double R0 = node_pos(L, PS, PA, L.act_cone[slot], node, c[0], c[1], c[2], q, nullptr);
+    double q[3], dir[3];
+    double R0 = node_pos(L, PS, PA, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
     const int j0 = L.start[b], j1 = L.start[b + 1];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
         for (int j = j0; j < j1; ++j) {
-            double dx = q[0] - pd.xs[j], dy = q[1] - pd.ys[j], dz = q[2] - pd.zs[j];
-            double r1 = dist<T>(dx, dy, dz);
-            T cc, ss;
-            expi(pd.kappa * (r1 - R0), cc, ss);
-            T a;
-            if constexpr (sizeof(T) == 8) a = R0 / r1;
-            else a = (float)R0 / (float)r1;
-            cpx<T> g = {a * cc, a * ss};
+            cpx<T> g = leaf_factor<T>(pd, R0, q, dir, j);
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 if (R == 1 || r0 + r < nrhs) {
@@ -323,7 +345,8 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
 // Targets: near field + interpolation from every cousin box of every level
 // ---------------------------------------------------------------------------------
 template <typename T, int R, int PS, int PA>
-__global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *sig, void *us, int mode)
+__global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *sig, void *us, int mode, int d_hi,
+                                              int d_lo, int accumulate)
 {
     constexpr int P = PS * PA * PA;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,7 +377,7 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
             }
         }
         if (mode & 2) {
-            for (int d = pd.D; d >= 3; --d) {
+            for (int d = d_hi; d >= d_lo; --d) {
                 const LevelDev &L = pd.lev[d];
                 int b = L.pt_box[i];
                 for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
@@ -379,7 +402,15 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (R == 1 || r0 + r < nrhs) st<T>(us, (size_t)i * nrhs + r0 + r, acc[r]);
+            if (R == 1 || r0 + r < nrhs) {
+                size_t o = (size_t)i * nrhs + r0 + r;
+                if (accumulate) {
+                    cpx<T> prev = ld<T>(us, o);
+                    acc[r].x += prev.x;
+                    acc[r].y += prev.y;
+                }
+                st<T>(us, o, acc[r]);
+            }
     }
 }
 
@@ -534,15 +565,9 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
             for (int slot = LD.act_start[b]; slot < LD.act_start[b + 1]; ++slot) {
                 int cone = LD.act_cone[slot];
                 for (int node = 0; node < P; ++node) {
-                    double q[3];
-                    double R0 = node_pos(LD, PS, PA, cone, node, c[0], c[1], c[2], q, nullptr);
-                    double r1 = dist<T>(q[0] - x, q[1] - y, q[2] - z);
-                    T cc, ss;
-                    expi(pd.kappa * (r1 - R0), cc, ss);
-                    T a;
-                    if constexpr (sizeof(T) == 8) a = R0 / r1;
-                    else a = (float)R0 / (float)r1;
-                    cpx<T> g = {a * cc, -a * ss};
+                    double q[3], dir[3];
+                    double R0 = node_pos(LD, PS, PA, cone, node, c[0], c[1], c[2], q, dir);
+                    cpx<T> g = cconj(leaf_factor<T>(pd, R0, q, dir, j));
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (R == 1 || r0 + r < nrhs) {
@@ -569,23 +594,48 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
                            StageTimer &tm)
 {
     constexpr int P = PS * PA * PA;
+    if (!pd.pingpong) {
+        if (mode & 2) {
+            const LevelDev &L = pd.lev[pd.D];
+            int64_t nt = (int64_t)L.nact * P;
+            if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
+            tm.mark(STAGE_LEAF, nt > 0, st);
+            int nl = 0;
+            for (int d = pd.D; d >= 4; --d) {
+                int64_t np = (int64_t)pd.lev[d - 1].nact * P;
+                if (np == 0) continue;
+                if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+                else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+                ++nl;
+            }
+            tm.mark(STAGE_UPWARD, nl, st);
+        }
+        k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode, pd.D, 3, 0);
+        tm.mark(STAGE_EVAL, 1, st);
+        return cudaGetLastError();
+    }
+    // two alternating level buffers: each level's targets are evaluated before the
+    // upward step overwrites the buffer of level d-1's parent
+    k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode & 1, pd.D, 3, 0);
+    tm.mark(STAGE_EVAL, 1, st);
     if (mode & 2) {
         const LevelDev &L = pd.lev[pd.D];
         int64_t nt = (int64_t)L.nact * P;
         if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
         tm.mark(STAGE_LEAF, nt > 0, st);
-        int nl = 0;
-        for (int d = pd.D; d >= 4; --d) {
-            int64_t np = (int64_t)pd.lev[d - 1].nact * P;
-            if (np == 0) continue;
-            if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
-            else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
-            ++nl;
+        for (int d = pd.D; d >= 3; --d) {
+            k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, 2, d, d, 1);
+            tm.mark(STAGE_EVAL, 1, st);
+            if (d > 3) {
+                int64_t np = (int64_t)pd.lev[d - 1].nact * P;
+                if (np > 0) {
+                    if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+                    else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+                }
+                tm.mark(STAGE_UPWARD, np > 0, st);
+            }
         }
-        tm.mark(STAGE_UPWARD, nl, st);
     }
-    k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
-    tm.mark(STAGE_EVAL, 1, st);
     return cudaGetLastError();
 }
 

@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, cons
     const int slot = (int)(w / kP), node = (int)(w % kP);
     const int b = L.act_box[slot];
     const double *c = L.center + 3 * (size_t)b;
-    double q[3];
-    const double R0 = node_pos(L, 3, 5, L.act_cone[slot], node, c[0], c[1], c[2], q, nullptr);
+    double q[3], dir[3];
+    const double R0 = node_pos(L, 3, 5, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
     cpx<float> acc[RPL];
 #pragma unroll
     for (int t = 0; t < RPL; ++t) acc[t] = {0.f, 0.f};
@@ -416,12 +416,9 @@ __global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, cons
         int j = j0 + lane;
         float gx = 0.f, gy = 0.f;
         if (j < j1) {
-            double r1 = dist<float>(q[0] - pd.xs[j], q[1] - pd.ys[j], q[2] - pd.zs[j]);
-            float cc, ss;
-            expi(pd.kappa * (r1 - R0), cc, ss);
-            float amp = (float)R0 / (float)r1;
-            gx = amp * cc;
-            gy = amp * ss;
+            cpx<float> g = leaf_factor<float>(pd, R0, q, dir, j);
+            gx = g.x;
+            gy = g.y;
         }
         int cnt = min(32, j1 - j0);
         for (int t = 0; t < cnt; ++t) {

@@ -31,6 +31,11 @@
 #include "ifgf.h"
 
 #define IFGF_MAX_LEVELS 20
+
+// four doubles, 32-byte aligned (point offset from its leaf centre and its squared norm)
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
 #define IFGF_MAX_P 8
 
 struct LevelDev {
@@ -84,10 +89,12 @@ struct LevelDev {
 
 struct PlanDev {
     int n = 0, D = 0, Ps = 0, Pang = 0, P = 0;
+    int pingpong = 0;   // level buffers alternate: target evaluation runs level by level
     double kappa = 0;
     double ts[IFGF_MAX_P] = {}, ta[IFGF_MAX_P] = {};    // Chebyshev nodes
     double its[IFGF_MAX_P] = {}, ita[IFGF_MAX_P] = {};  // 1 / prod_{e != a} (t_a - t_e)
     const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
+    const dbl4 *leaf_off = nullptr;   // [N] x_j - centre of its leaf box, and its squared norm
     const int *perm = nullptr;
     int *err = nullptr;                                  // device invariant-failure counter
     LevelDev lev[IFGF_MAX_LEVELS + 1];
@@ -100,14 +107,15 @@ enum IfgfStage {
 };
 
 struct StageTimer {
+    static constexpr int kMax = 512;
     bool on = false;
     int n = 0;
-    cudaEvent_t ev[64] = {};
-    int stage[64] = {};
-    int launches[64] = {};
+    cudaEvent_t ev[kMax] = {};
+    int stage[kMax] = {};
+    int launches[kMax] = {};
     void mark(int s, int nlaunch, cudaStream_t st)
     {
-        if (!on || n >= 64) return;
+        if (!on || n >= kMax) return;
         cudaEventRecord(ev[n], st);
         stage[n] = s;
         launches[n] = nlaunch;
@@ -130,6 +138,9 @@ struct ifgf_plan {
     int precision = IFGF_FP64;
     int max_nrhs = 1;
     int flags = 0;
+    size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
+    bool pingpong = false;     // two alternating level buffers instead of one per level
+    int rhs_chunk = 1;         // right-hand sides per internal pass
     double H1 = 0, corner[3] = {0, 0, 0};
     PlanDev dev;
     LevelHost lh[IFGF_MAX_LEVELS + 1];

@@ -149,6 +149,17 @@ __global__ void k_level_boxes(const uint64_t *leafkey, const int *incl, int n, i
     if (i == n - 1) start[b + 1] = n;
 }
 
+// offset of every point from the centre of its leaf box, and its squared norm
+__global__ void k_leaf_offsets(PlanDev pd, dbl4 *off)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    const LevelDev &L = pd.lev[pd.D];
+    const double *c = L.center + 3 * (size_t)L.pt_box[i];
+    double dx = pd.xs[i] - c[0], dy = pd.ys[i] - c[1], dz = pd.zs[i] - c[2];
+    off[i] = dbl4{dx, dy, dz, dx * dx + dy * dy + dz * dz};
+}
+
 __global__ void k_parents(const int *start, int nbox, const int *pt_box_parent, int *parent)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -670,6 +681,12 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         L.parent = parent;
         Lp.child_start = cstart;
     }
+    {
+        DALLOC(off, dbl4, n);
+        k_leaf_offsets<<<nblocks(n), kThreads, 0, st>>>(pd, off);
+        CK(cudaGetLastError());
+        pd.leaf_off = off;
+    }
     // cousins of levels 3..D
     for (int d = 3; d <= D; ++d) {
         LevelDev &L = pd.lev[d];
@@ -861,16 +878,58 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
     }
 
-    // value buffers
+    // Value buffers.  All levels stay resident when that fits the budget; otherwise
+    // two buffers alternate between levels d and d-1 (the only two an evaluation
+    // step reads and writes), and right-hand sides are processed in chunks.
     const size_t eb = ifgf_elem_bytes(p->precision);
+    size_t all_levels = 0, max_pair = 0, max_level = 0;
     for (int d = 3; d <= D; ++d) {
-        LevelDev &L = pd.lev[d];
-        size_t bytes = (size_t)L.nact * P * p->max_nrhs * eb;
-        L.F = ifgf_dalloc(p, bytes);
-        if (!L.F) { p->last_error = "cone value buffer"; return IFGF_ENOMEM; }
+        size_t b = (size_t)pd.lev[d].nact * P * eb;
+        all_levels += b;
+        max_level = std::max(max_level, b);
+        if (d > 3) max_pair = std::max(max_pair, b + (size_t)pd.lev[d - 1].nact * P * eb);
     }
-    p->sig_sorted = ifgf_dalloc(p, (size_t)n * p->max_nrhs * eb);
-    p->u_sorted = ifgf_dalloc(p, (size_t)n * p->max_nrhs * eb);
+    if (D == 3) max_pair = max_level;
+    size_t budget = p->value_budget;
+    if (budget == 0) {
+        size_t freeb = 0, totalb = 0;
+        CK(cudaMemGetInfo(&freeb, &totalb));
+        size_t sorted = (size_t)2 * n * p->max_nrhs * eb;
+        budget = freeb > sorted ? (size_t)((freeb - sorted) * 0.6) : 0;
+    }
+    if (all_levels * p->max_nrhs <= budget) {
+        p->pingpong = false;
+        p->rhs_chunk = p->max_nrhs;
+    } else {
+        p->pingpong = true;
+        int64_t c = max_pair ? (int64_t)(budget / max_pair) : p->max_nrhs;
+        if (c < 1) { p->last_error = "cone values of two levels do not fit in device memory"; return IFGF_ENOMEM; }
+        p->rhs_chunk = (int)std::min<int64_t>(c, p->max_nrhs);
+    }
+    if (p->flags & 8) {  // force ping-pong buffers (tests)
+        p->pingpong = true;
+        p->rhs_chunk = p->max_nrhs;
+    }
+    if (p->flags & 16) p->rhs_chunk = std::min(p->rhs_chunk, 2);  // force small chunks (tests)
+    pd.pingpong = p->pingpong ? 1 : 0;
+    if (!p->pingpong) {
+        for (int d = 3; d <= D; ++d) {
+            LevelDev &L = pd.lev[d];
+            L.F = ifgf_dalloc(p, (size_t)L.nact * P * p->rhs_chunk * eb);
+            if (!L.F) { p->last_error = "cone value buffer"; return IFGF_ENOMEM; }
+        }
+    } else {
+        size_t even = 0, odd = 0;
+        for (int d = 3; d <= D; ++d) {
+            size_t b = (size_t)pd.lev[d].nact * P * p->rhs_chunk * eb;
+            if (d & 1) odd = std::max(odd, b); else even = std::max(even, b);
+        }
+        void *bufs[2] = {ifgf_dalloc(p, even), ifgf_dalloc(p, odd)};
+        if (!bufs[0] || !bufs[1]) { p->last_error = "cone value buffers"; return IFGF_ENOMEM; }
+        for (int d = 3; d <= D; ++d) pd.lev[d].F = bufs[d & 1];
+    }
+    p->sig_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
+    p->u_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
     if (!p->sig_sorted || !p->u_sorted) { p->last_error = "sorted density buffers"; return IFGF_ENOMEM; }
     CK(cudaStreamSynchronize(st));
     int herr = 0;
@@ -911,10 +970,22 @@ ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p)
 {
     if (p->adjoint_values_ready) return IFGF_OK;
     const size_t eb = ifgf_elem_bytes(p->precision);
-    for (int d = 3; d <= p->D; ++d) {
-        LevelDev &L = p->dev.lev[d];
-        L.Fadj = ifgf_dalloc(p, (size_t)L.nact * p->P * p->max_nrhs * eb);
-        if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
+    if (!p->pingpong) {
+        for (int d = 3; d <= p->D; ++d) {
+            LevelDev &L = p->dev.lev[d];
+            L.Fadj = ifgf_dalloc(p, (size_t)L.nact * p->P * p->rhs_chunk * eb);
+            if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
+        }
+    } else {
+        // the adjoint needs levels d-1 and d at a time, like the forward step
+        size_t even = 0, odd = 0;
+        for (int d = 3; d <= p->D; ++d) {
+            size_t b = (size_t)p->dev.lev[d].nact * p->P * p->rhs_chunk * eb;
+            if (d & 1) odd = std::max(odd, b); else even = std::max(even, b);
+        }
+        void *bufs[2] = {ifgf_dalloc(p, even), ifgf_dalloc(p, odd)};
+        if (!bufs[0] || !bufs[1]) { p->last_error = "adjoint value buffers"; return IFGF_ENOMEM; }
+        for (int d = 3; d <= p->D; ++d) p->dev.lev[d].Fadj = bufs[d & 1];
     }
     p->adjoint_values_ready = true;
     return IFGF_OK;

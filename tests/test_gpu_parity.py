@@ -226,6 +226,36 @@ def test_batched_tensor_core_path_matches_mixed_and_oracle(pkg, torch_cuda, nrhs
     assert b.check() == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6), ("batched", 1e-5)])
+def test_two_level_buffers_and_rhs_chunks_match(pkg, torch_cuda, precision, tol):
+    # flags bit 3: only two levels' cone values resident; bit 4: 2 right-hand sides
+    # per pass.  Same operator, same result.
+    torch = torch_cuda
+    wl, pts, _ = _make((3500, 4, 5, 1, 2))
+    nrhs = 6
+    sig = wi.complex_normal(70, (nrhs, wl.n))
+    kw = dict(max_nrhs=nrhs, precision=precision)
+    a = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, **kw)
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, flags=8 | 16, **kw)
+    assert b.stats()["pingpong"] == 1 and b.stats()["rhs_chunk"] == 2
+    assert a.stats()["pingpong"] == 0
+    s = torch.from_numpy(sig).cuda()
+    ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
+    assert rel(ub, ua) < tol
+    wa, wb = a.apply_adjoint(s).cpu().numpy(), b.apply_adjoint(s).cpu().numpy()
+    assert rel(wb, wa) < tol
+    # a budget too small for all levels switches to two levels by itself
+    eb = 16 if precision == "fp64" else 8
+    lv = {x["d"]: x["nact"] * 75 * eb for x in a.stats()["level"] if x["d"] >= 3}
+    pair = max(lv[d] + lv[d - 1] for d in range(4, 6))
+    budget = int(1.5 * pair)
+    assert sum(lv.values()) * nrhs > budget
+    c = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, value_budget_bytes=budget, **kw)
+    assert c.stats()["pingpong"] == 1
+    assert rel(c.apply(s).cpu().numpy(), ua) < tol
+    assert a.check() == 0 and b.check() == 0 and c.check() == 0
+
+
 def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     torch = torch_cuda
     wl, pts, sigma = _make((2000, 2, 4, 1, 2))
