@@ -80,7 +80,13 @@ typedef struct {
                        (24 bytes per cousin evaluation; cached by default);
                        bit 3: keep only two levels' cone values (always on when the
                        values of all levels exceed the budget below);
-                       bit 4: process at most 2 right-hand sides per pass (testing) */
+                       bit 4: process at most 2 right-hand sides per pass (testing);
+                       bit 5: no evaluation caches.  By default, when they take at most a
+                       quarter of the free device memory, FP64 and IFGF_MIXED plans
+                       store at plan time each cousin-target evaluation's cone slot,
+                       weights (local coordinates for IFGF_MIXED) and centred factor,
+                       and the geometry of every upward evaluation of levels without an
+                       upward table; the evaluations then skip that geometry */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels

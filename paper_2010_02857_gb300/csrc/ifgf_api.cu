@@ -364,10 +364,10 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
     snprintf(tmp, sizeof tmp,
              "\"n\": %lld, \"levels\": %d, \"P\": %d, \"kappa\": %.17g, \"precision\": %d, \"max_nrhs\": %d, "
              "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, "
-             "\"pingpong\": %d, \"rhs_chunk\": %d, \"level\": [",
+             "\"pingpong\": %d, \"rhs_chunk\": %d, \"cache_bytes\": %zu, \"level\": [",
              (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
              (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes,
-             plan->pingpong ? 1 : 0, plan->rhs_chunk);
+             plan->pingpong ? 1 : 0, plan->rhs_chunk, plan->cache_bytes);
     s += tmp;
     for (int d = 1; d <= plan->D; ++d) {
         const LevelHost &h = plan->lh[d];

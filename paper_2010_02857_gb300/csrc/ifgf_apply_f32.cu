@@ -13,3 +13,8 @@ cudaError_t ifgf_build_uptable_f32(const PlanDev &pd, int d, void *tab, cudaStre
 {
     return ifgf::build_uptable<float>(pd, d, tab, st);
 }
+
+cudaError_t ifgf_build_evalcache_f32(const PlanDev &pd, int d, int which, cudaStream_t st)
+{
+    return ifgf::build_evalcache<float>(pd, d, which, st);
+}

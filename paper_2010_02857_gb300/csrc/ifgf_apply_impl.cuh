@@ -321,6 +321,13 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
                 for (int m = 0; m < NW; ++m) w[m] = e.w[m];
                 f = {e.fr, e.fi};
                 cone = e.cone;
+            } else if (L.ucache) {
+                const UpEntry<T, NW> &e =
+                    ((const UpEntry<T, NW> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)];
+#pragma unroll
+                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
+                f = {e.fr, e.fi};
+                cone = e.cone;
             } else {
                 cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
             }
@@ -383,14 +390,39 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
                 for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
                     int k = L.cous[e];
                     const double *ck = L.center + 3 * (size_t)k;
-                    double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
                     T w[PS + 2 * PA];
-                    ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
-                    int sl = cone_slot(L, k, g.cone);
-                    if (sl < 0) { atomicAdd(pd.err, 1); continue; }
+                    int sl;
+                    cpx<T> G;
+                    bool cached = false;
+                    if constexpr (PS + 2 * PA <= 13) {
+                        if (L.tcache) {
+                            const size_t o = (size_t)L.toff[i] + (e - L.cous_start[b]);
+                            if constexpr (sizeof(T) == 8) {
+                                const TEntry64 &en = ((const TEntry64 *)L.tcache)[o];
+#pragma unroll
+                                for (int m = 0; m < PS + 2 * PA; ++m) w[m] = en.w[m];
+                                G = {en.gr, en.gi};
+                                sl = en.slot;
+                            } else {
+                                const TEntry32 en = ((const TEntry32 *)L.tcache)[o];
+                                lagrange<float>(PS, pd.ts, pd.its, en.t[0], w);
+                                lagrange<float>(PA, pd.ta, pd.ita, en.t[1], w + PS);
+                                lagrange<float>(PA, pd.ta, pd.ita, en.t[2], w + PS + PA);
+                                G = {en.gr, en.gi};
+                                sl = en.slot;
+                            }
+                            cached = true;
+                        }
+                    }
+                    if (!cached) {
+                        double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
+                        ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
+                        sl = cone_slot(L, k, g.cone);
+                        if (sl < 0) { atomicAdd(pd.err, 1); continue; }
+                        G = green_r<T>(pd.kappa, g.r);
+                    }
                     cpx<T> val[R];
                     contract<T, R, PS, PA>(L.F, (size_t)sl * P, nrhs, r0, w, w + PS, w + PS + PA, val);
-                    cpx<T> G = green_r<T>(pd.kappa, g.r);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         cpx<T> m = cmul(G, val[r]);
@@ -670,6 +702,89 @@ cudaError_t launch_orders(const PlanDev &pd, int nrhs, const void *in, void *out
     constexpr int RB = sizeof(T) == 8 ? 4 : 8;
     return adjoint ? launch_adjoint<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm)
                    : launch_forward<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm);
+}
+
+// Evaluation caches.  which = 0: cousin targets of level d; which = 1: upward step
+// d -> d-1 per (parent slot, node, child).
+template <typename T, int PS, int PA>
+__global__ void __launch_bounds__(128) k_build_tcache(PlanDev pd, int d)
+{
+    constexpr int NW = PS + 2 * PA;
+    const LevelDev &L = pd.lev[d];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+    const int b = L.pt_box[i];
+    int o = L.toff[i];
+    for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e, ++o) {
+        const int k = L.cous[e];
+        const double *ck = L.center + 3 * (size_t)k;
+        double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
+        ConeGeom g = cone_of_fast(L, vx, vy, vz);
+        int sl = cone_slot(L, k, g.cone);
+        if (sl < 0) { atomicAdd(pd.err, 1); sl = 0; }
+        if constexpr (sizeof(T) == 8) {
+            TEntry64 en;
+            double loc[3];
+            local_coords(L, g, vx, vy, vz, loc);
+            weights3<double, PS, PA>(pd, loc, en.w, en.w + PS, en.w + PS + PA);
+            for (int m = NW; m < 13; ++m) en.w[m] = 0.0;
+            cpx<double> G = green_r<double>(pd.kappa, g.r);
+            en.gr = G.x;
+            en.gi = G.y;
+            en.slot = sl;
+            en.pad = 0;
+            ((TEntry64 *)L.tcache)[o] = en;
+        } else {
+            TEntry32 en;
+            local_coords_f32(L, g, vx, vy, vz, en.t);
+            cpx<float> G = green_r<float>(pd.kappa, g.r);
+            en.gr = G.x;
+            en.gi = G.y;
+            en.slot = sl;
+            ((TEntry32 *)L.tcache)[o] = en;
+        }
+    }
+}
+
+template <typename T, int PS, int PA>
+__global__ void __launch_bounds__(128) k_build_ucache(PlanDev pd, int d)
+{
+    constexpr int P = PS * PA * PA;
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Lp.nact * P) return;
+    const int slot = (int)(t / P), node = (int)(t % P);
+    const int j = Lp.act_box[slot];
+    const int k0 = Lp.child_start[j], k1 = Lp.child_start[j + 1];
+    const int pcone = Lp.act_cone[slot];
+    for (int k = k0; k < k1; ++k) {
+        const int oct = (int)(L.key[k] & 7u);
+        UpEntry<T, PS + 2 * PA> e;
+        cpx<T> f;
+        e.cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, e.w, f);
+        e.fr = f.x;
+        e.fi = f.y;
+        ((UpEntry<T, PS + 2 * PA> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)] = e;
+    }
+}
+
+template <typename T>
+cudaError_t build_evalcache(const PlanDev &pd, int d, int which, cudaStream_t st)
+{
+    int64_t n = which == 0 ? pd.n : (int64_t)pd.lev[d - 1].nact * pd.P;
+    if (n == 0) return cudaSuccess;
+    if (pd.Ps == 3 && pd.Pang == 5) {
+        if (which == 0) k_build_tcache<T, 3, 5><<<grid_for(n, 128), 128, 0, st>>>(pd, d);
+        else k_build_ucache<T, 3, 5><<<grid_for(n, 128), 128, 0, st>>>(pd, d);
+    } else if (pd.Ps == 4 && pd.Pang == 7) {
+        if (which == 0) return cudaSuccess;  // 18 weights do not fit the 13-weight target entry
+        k_build_ucache<T, 4, 7><<<grid_for(n, 128), 128, 0, st>>>(pd, d);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>

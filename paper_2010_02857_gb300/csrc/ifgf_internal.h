@@ -85,6 +85,14 @@ struct LevelDev {
     const int *urank = nullptr;        // [words of level d-1]
     const int *uids = nullptr;         // [urows] cone id of each row
     const void *utab = nullptr;        // [urows][8][P] entries
+    // Evaluation caches (plan time, when they fit the memory budget):
+    // cousin targets of level d: point i's evaluations, in cousin-list order, at
+    // tcache[toff[i] .. toff[i+1]); upward step d -> d-1 of an untabled level:
+    // (parent slot s, node q, child c) at ucache[uoff[s] + q * nchild + c].
+    const int *toff = nullptr;
+    const void *tcache = nullptr;
+    const int *uoff = nullptr;
+    const void *ucache = nullptr;
 };
 
 struct PlanDev {
@@ -140,6 +148,7 @@ struct ifgf_plan {
     int flags = 0;
     size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
     bool pingpong = false;     // two alternating level buffers instead of one per level
+    size_t cache_bytes = 0;    // evaluation caches (0: none)
     int rhs_chunk = 1;         // right-hand sides per internal pass
     double H1 = 0, corner[3] = {0, 0, 0};
     PlanDev dev;
@@ -174,6 +183,19 @@ template <typename T, int NW> struct UpEntry {
     int cone;
 };
 
+// Cached geometry of one cousin-target evaluation.  FP64 plans: the Lagrange weights
+// and the centred factor; float plans: the local coordinates and the factor.
+struct TEntry64 {
+    double w[13];
+    double gr, gi;
+    int slot, pad;
+};
+struct TEntry32 {
+    float t[3];
+    int slot;
+    float gr, gi;
+};
+
 // plan.cu
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
@@ -184,6 +206,9 @@ void *ifgf_dalloc(ifgf_plan *p, size_t bytes);
 cudaError_t ifgf_build_uptable_f64(const PlanDev &pd, int d, void *tab, cudaStream_t st);
 cudaError_t ifgf_build_uptable_f32(const PlanDev &pd, int d, void *tab, cudaStream_t st);
 size_t ifgf_uptable_entry_bytes(int precision, int Ps, int Pang);
+// fill the evaluation caches of level d (offsets and storage already set in pd)
+cudaError_t ifgf_build_evalcache_f64(const PlanDev &pd, int d, int which, cudaStream_t st);
+cudaError_t ifgf_build_evalcache_f32(const PlanDev &pd, int d, int which, cudaStream_t st);
 // apply.cu
 ifgf_status ifgf_run_apply(ifgf_plan *p, const void *sigma, void *u, int nrhs, int mode,
                            int adjoint, cudaStream_t st);

@@ -878,6 +878,66 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
     }
 
+    // Evaluation caches: the cousin targets' slots, weights and centred factors, and
+    // the geometry of untabled upward levels, computed once here instead of at every
+    // apply.  Built when they take at most a quarter of the free memory (flags bit 5
+    // turns them off; batched plans have their own target cache).
+    if (!(p->flags & 32) && p->precision != IFGF_BATCHED_BF16) {
+        const bool f64 = p->precision == IFGF_FP64;
+        const size_t te = Ps == 3 && Pang == 5 ? (f64 ? sizeof(TEntry64) : sizeof(TEntry32)) : 0;
+        const size_t ue = ifgf_uptable_entry_bytes(p->precision, Ps, Pang);
+        size_t need = 0;
+        bool fits32 = true;
+        for (int d = 3; d <= D; ++d) {
+            need += (size_t)p->lh[d].cousin_evals * te;
+            fits32 = fits32 && p->lh[d].cousin_evals < ((int64_t)1 << 31);
+            if (d >= 4 && !pd.lev[d].utab) {
+                need += (size_t)p->lh[d].upward_evals * ue;
+                fits32 = fits32 && p->lh[d].upward_evals < ((int64_t)1 << 31);
+            }
+        }
+        size_t freeb = 0, totalb = 0;
+        CK(cudaMemGetInfo(&freeb, &totalb));
+        if (fits32 && need > 0 && need <= freeb / 4) {
+            for (int d = 3; d <= D; ++d) {
+                LevelDev &L = pd.lev[d];
+                if (te > 0 && p->lh[d].cousin_evals > 0) {
+                    Scratch cnt;
+                    if (!cnt.alloc((size_t)(n + 1) * 4)) return IFGF_ENOMEM;
+                    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(n + 1) * 4, st));
+                    k_point_cousin_count<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+                    CK(cudaGetLastError());
+                    DALLOC(toff, int, n + 1);
+                    ifgf_status s2 = cub_exclusive_sum(p, (int *)cnt.ptr, toff, n + 1, st);
+                    if (s2 != IFGF_OK) return s2;
+                    void *tc = ifgf_dalloc(p, (size_t)p->lh[d].cousin_evals * te);
+                    if (!tc) { p->last_error = "target cache"; return IFGF_ENOMEM; }
+                    L.toff = toff;
+                    L.tcache = tc;
+                    CK(f64 ? ifgf_build_evalcache_f64(pd, d, 0, st) : ifgf_build_evalcache_f32(pd, d, 0, st));
+                }
+                if (d >= 4 && !L.utab && p->lh[d].upward_evals > 0) {
+                    LevelDev &Lp = pd.lev[d - 1];
+                    Scratch cnt;
+                    if (!cnt.alloc((size_t)(Lp.nact + 1) * 4)) return IFGF_ENOMEM;
+                    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(Lp.nact + 1) * 4, st));
+                    k_parent_slot_count<<<nblocks(Lp.nact), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+                    CK(cudaGetLastError());
+                    DALLOC(uoff, int, Lp.nact + 1);
+                    ifgf_status s2 = cub_exclusive_sum(p, (int *)cnt.ptr, uoff, Lp.nact + 1, st);
+                    if (s2 != IFGF_OK) return s2;
+                    void *uc = ifgf_dalloc(p, (size_t)p->lh[d].upward_evals * ue);
+                    if (!uc) { p->last_error = "upward cache"; return IFGF_ENOMEM; }
+                    L.uoff = uoff;
+                    L.ucache = uc;
+                    CK(f64 ? ifgf_build_evalcache_f64(pd, d, 1, st) : ifgf_build_evalcache_f32(pd, d, 1, st));
+                }
+            }
+            CK(cudaStreamSynchronize(st));
+            p->cache_bytes = need;
+        }
+    }
+
     // Value buffers.  All levels stay resident when that fits the budget; otherwise
     // two buffers alternate between levels d and d-1 (the only two an evaluation
     // step reads and writes), and right-hand sides are processed in chunks.

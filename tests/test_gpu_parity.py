@@ -256,6 +256,25 @@ def test_two_level_buffers_and_rhs_chunks_match(pkg, torch_cuda, precision, tol)
     assert a.check() == 0 and b.check() == 0 and c.check() == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-6)])
+def test_evaluation_caches_match_on_the_fly_geometry(pkg, torch_cuda, precision, tol):
+    # plan-time caches of cousin-target and untabled-upward geometry (default) vs none
+    # (flags bit 5), and vs the oracle; both ping-pong and resident levels
+    torch = torch_cuda
+    wl, pts, sigma = _make((5000, 4, 6, 1, 2))
+    s = torch.from_numpy(sigma).cuda()
+    o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    uo = o.apply(sigma)
+    for extra in (0, 8):
+        a = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, precision=precision, flags=extra)
+        b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, precision=precision, flags=32 | extra)
+        assert a.stats()["cache_bytes"] > 0 and b.stats()["cache_bytes"] == 0
+        ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
+        assert rel(ua, ub) < tol
+        assert rel(ua, uo) < (1e-10 if precision == "fp64" else 2e-5)
+        assert a.check() == 0 and b.check() == 0
+
+
 def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     torch = torch_cuda
     wl, pts, sigma = _make((2000, 2, 4, 1, 2))
