@@ -51,9 +51,15 @@ template <typename T> __device__ __forceinline__ void st(void *base, size_t i, c
 template <typename T, int PS, int PA>
 __device__ __forceinline__ void weights3(const PlanDev &pd, const double *loc, T *ws, T *wt, T *wp)
 {
-    lagrange<T>(PS, pd.ts, pd.its, (T)loc[0], ws);
-    lagrange<T>(PA, pd.ta, pd.ita, (T)loc[1], wt);
-    lagrange<T>(PA, pd.ta, pd.ita, (T)loc[2], wp);
+    if constexpr (sizeof(T) == 8) {
+        lagrange<T>(PS, pd.ts, pd.its, loc[0], ws);
+        lagrange<T>(PA, pd.ta, pd.ita, loc[1], wt);
+        lagrange<T>(PA, pd.ta, pd.ita, loc[2], wp);
+    } else {
+        lagrange(PS, pd.tsf, pd.itsf, (float)loc[0], ws);
+        lagrange(PA, pd.taf, pd.itaf, (float)loc[1], wt);
+        lagrange(PA, pd.taf, pd.itaf, (float)loc[2], wp);
+    }
 }
 
 // sum_{a,b,c} ws[a] wt[b] wp[c] F[(a PA + b) PA + c][r], sum-factorised (phi, theta, s)
@@ -160,9 +166,9 @@ __device__ __forceinline__ ConeGeom geom_weights(const PlanDev &pd, const LevelD
     } else {
         float t[3];
         local_coords_f32(L, g, vx, vy, vz, t);
-        lagrange<float>(PS, pd.ts, pd.its, t[0], w);
-        lagrange<float>(PA, pd.ta, pd.ita, t[1], w + PS);
-        lagrange<float>(PA, pd.ta, pd.ita, t[2], w + PS + PA);
+        lagrange(PS, pd.tsf, pd.itsf, t[0], w);
+        lagrange(PA, pd.taf, pd.itaf, t[1], w + PS);
+        lagrange(PA, pd.taf, pd.itaf, t[2], w + PS + PA);
     }
     return g;
 }
@@ -405,9 +411,9 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
                                 sl = en.slot;
                             } else {
                                 const TEntry32 en = ((const TEntry32 *)L.tcache)[o];
-                                lagrange<float>(PS, pd.ts, pd.its, en.t[0], w);
-                                lagrange<float>(PA, pd.ta, pd.ita, en.t[1], w + PS);
-                                lagrange<float>(PA, pd.ta, pd.ita, en.t[2], w + PS + PA);
+                                lagrange(PS, pd.tsf, pd.itsf, en.t[0], w);
+                                lagrange(PA, pd.taf, pd.itaf, en.t[1], w + PS);
+                                lagrange(PA, pd.taf, pd.itaf, en.t[2], w + PS + PA);
                                 G = {en.gr, en.gi};
                                 sl = en.slot;
                             }

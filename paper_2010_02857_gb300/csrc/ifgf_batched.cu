@@ -39,6 +39,7 @@ constexpr int kK = 80;        // K padded to 5 blocks of 16
 constexpr int kM = 128;       // rows per MMA
 constexpr int kThreads = 128;
 constexpr int kWaitLimit = 1 << 22;
+constexpr int kBatch = 16;     // cone-value loads in flight per thread
 constexpr int kStageStride = 32 * 4 + 16;  // one epilogue pass: 32 floats per row, padded
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -141,16 +142,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
         const int rows = rows_t + rows_u;
         if (rows == 0) continue;
         // B: the cone's values, complex -> (re, im) columns 2r, 2r+1
+        // batches of kBatch independent loads per thread before any conversion
         const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
-        for (int idx = tid; idx < kP * (npad / 2); idx += kThreads) {
-            int p = idx / (npad / 2), r = idx % (npad / 2);
-            float2 v = r < nrhs ? F[(size_t)p * nrhs + r] : make_float2(0.f, 0.f);
-            __nv_bfloat16 h0, l0, h1, l1;
-            bf16_split(v.x, h0, l0);
-            bf16_split(v.y, h1, l1);
-            uint32_t off = b_off(p, 2 * r, lbo_b);
-            *(uint32_t *)(B_hi + off) = pack2(h0, h1);
-            *(uint32_t *)(B_lo + off) = pack2(l0, l1);
+        const int half_n = npad / 2, tot = kP * half_n;
+        for (int base = tid; base < tot; base += kBatch * kThreads) {
+            float2 v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                int idx = base + u * kThreads;
+                int p = idx / half_n, r = idx - p * half_n;
+                v[u] = (idx < tot && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                int idx = base + u * kThreads;
+                if (idx < tot) {
+                    int p = idx / half_n, r = idx - p * half_n;
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    bf16_split(v[u].x, h0, l0);
+                    bf16_split(v[u].y, h1, l1);
+                    uint32_t off = b_off(p, 2 * r, lbo_b);
+                    *(uint32_t *)(B_hi + off) = pack2(h0, h1);
+                    *(uint32_t *)(B_lo + off) = pack2(l0, l1);
+                }
+            }
         }
         const int k = L.act_box[slot];
         const double *ck = L.center + 3 * (size_t)k;
@@ -168,9 +183,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
                     if (L.tl_loc) {
                         float4 t = L.tl_loc[e];
                         float2 G = L.tl_fac[e];
-                        lagrange<float>(3, pd.ts, pd.its, t.x, w);
-                        lagrange<float>(5, pd.ta, pd.ita, t.y, w + 3);
-                        lagrange<float>(5, pd.ta, pd.ita, t.z, w + 8);
+                        lagrange(3, pd.tsf, pd.itsf, t.x, w);
+                        lagrange(5, pd.taf, pd.itaf, t.y, w + 3);
+                        lagrange(5, pd.taf, pd.itaf, t.z, w + 8);
                         f = {G.x, G.y};
                     } else {
                         double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]),
@@ -270,10 +285,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
             }
             phase ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // epilogue, 32 accumulator columns (16 right-hand sides) per pass: row tid
-            // times its factor goes to the stage row and is added to its destination by
-            // one bulk asynchronous reduction per pass
+            // epilogue, 32 accumulator columns (16 right-hand sides) per pass: thread tid
+            // writes row tid times its factor to the warp's stage rows; then the warp adds
+            // four 128-byte row segments per instruction (red.global.add.v4.f32, 16 bytes
+            // per lane), so that the additions are coalesced per row
             float *srow = (float *)(stage + (size_t)tid * kStageStride);
+            const unsigned char *swarp = stage + (size_t)warp * 32 * kStageStride;
+            const unsigned long long dest_u = (unsigned long long)dest;
+            const int lane = tid & 31, lr = lane >> 3, lc = (lane & 7) * 4;
             for (int cb = 0; cb < 2 * nrhs; cb += 32) {
                 uint32_t v[32];
                 uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
@@ -287,34 +306,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
                       "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                // the previous pass's reduction must have read the stage row
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                const int ncol = min(32, 2 * nrhs - cb);
+                const int ncol = min(32, 2 * nrhs - cb);  // a multiple of 4: nrhs is even
+                __syncwarp();                             // the previous pass has read the stage
                 if (valid) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
+                    for (int j = 0; j < 32; j += 4) {
                         if (j < ncol) {
-                            float re = __uint_as_float(v[j]), im = __uint_as_float(v[j + 1]);
-                            srow[j] = f.x * re - f.y * im;
-                            srow[j + 1] = f.x * im + f.y * re;
+                            float r0 = __uint_as_float(v[j]), i0 = __uint_as_float(v[j + 1]);
+                            float r1 = __uint_as_float(v[j + 2]), i1 = __uint_as_float(v[j + 3]);
+                            *(float4 *)(srow + j) = make_float4(f.x * r0 - f.y * i0, f.x * i0 + f.y * r0,
+                                                                f.x * r1 - f.y * i1, f.x * i1 + f.y * r1);
                         }
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (valid) {
-                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                                     (uint64_t)__cvta_generic_to_global((float *)dest + cb)),
-                                 "r"(smem_u32(srow)), "r"((uint32_t)(ncol * 4))
-                                 : "memory");
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int rr = 4 * q + lr;  // the warp's row read by this lane
+                    const unsigned long long d = __shfl_sync(0xffffffffu, dest_u, rr);
+                    if (d != 0ull && lc < ncol) {
+                        float4 x = *(const float4 *)(swarp + (size_t)rr * kStageStride + lc * 4);
+                        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(
+                                         (float *)d + cb + lc),
+                                     "f"(x.x), "f"(x.y), "f"(x.z), "f"(x.w)
+                                     : "memory");
+                    }
                 }
-                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
         }
         __syncthreads();
     }
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)

@@ -290,6 +290,26 @@ __device__ __forceinline__ void lagrange(int n, const double *nodes, const doubl
     }
 }
 
+// The same in FP32 from FP32 copies of the nodes and weights, so that no call
+// converts from FP64.
+__device__ __forceinline__ void lagrange(int n, const float *nodes, const float *inv, float t, float *w)
+{
+    float d[IFGF_MAX_P];
+#pragma unroll
+    for (int e = 0; e < IFGF_MAX_P; ++e)
+        if (e < n) d[e] = t - nodes[e];
+#pragma unroll
+    for (int a = 0; a < IFGF_MAX_P; ++a) {
+        if (a < n) {
+            float v = inv[a];
+#pragma unroll
+            for (int e = 0; e < IFGF_MAX_P; ++e)
+                if (e < n && e != a) v *= d[e];
+            w[a] = v;
+        }
+    }
+}
+
 // exp(i arg) with the argument in FP64: full FP64 sincos for double results; for
 // float results the argument is reduced modulo 2 pi in FP64 (Cody-Waite, two-part
 // 2 pi) and the reduced angle goes to FP32 sincos.

@@ -101,6 +101,8 @@ struct PlanDev {
     double kappa = 0;
     double ts[IFGF_MAX_P] = {}, ta[IFGF_MAX_P] = {};    // Chebyshev nodes
     double its[IFGF_MAX_P] = {}, ita[IFGF_MAX_P] = {};  // 1 / prod_{e != a} (t_a - t_e)
+    float tsf[IFGF_MAX_P] = {}, taf[IFGF_MAX_P] = {};   // the same in FP32, for FP32 weights
+    float itsf[IFGF_MAX_P] = {}, itaf[IFGF_MAX_P] = {};
     const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     const dbl4 *leaf_off = nullptr;   // [N] x_j - centre of its leaf box, and its squared norm
     const int *perm = nullptr;

@@ -574,6 +574,12 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         for (int e = 0; e < Pang; ++e) if (e != a) v *= pd.ta[a] - pd.ta[e];
         pd.ita[a] = 1.0 / v;
     }
+    for (int a = 0; a < IFGF_MAX_P; ++a) {
+        pd.tsf[a] = (float)pd.ts[a];
+        pd.taf[a] = (float)pd.ta[a];
+        pd.itsf[a] = (float)pd.its[a];
+        pd.itaf[a] = (float)pd.ita[a];
+    }
     DALLOC(d_err, int, 1);
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     pd.err = d_err;
