@@ -12,17 +12,18 @@
 //     D (rows x 2 nrhs) = A (rows x 80) * B (80 x 2 nrhs),
 // with B = the cone's values (re/im interleaved, 75 rows padded to 80) loaded once.
 //
-// k_cone_mma: one persistent CTA per SM walks the relevant cones of a level.  For
-// each cone it loads B into shared memory as BF16 hi + lo parts, and for each chunk
-// of 128 rows it writes A (hi + lo) and issues tcgen05.mma (kind::f16, BF16 inputs,
-// FP32 accumulation in tensor memory): Ahi Bhi + Ahi Blo + Alo Bhi per K block of
-// 16, which keeps ~16 significant bits of both operands.  The epilogue reads the
-// accumulator with tcgen05.ld, multiplies each row by its complex factor and adds
-// the row to its destination with bulk asynchronous reductions
-// (cp.reduce.async.bulk ... add.f32, 16 right-hand sides per reduction; faster here
-// than per-thread vector reductions).  Destinations receive contributions
-// from several cones, so the summation order (and the last bits of the result)
-// varies from run to run on this path.
+// k_cone_mma: persistent CTAs (two per SM) walk the relevant cones of a level in
+// chunks of 128 rows.  For each cone B goes to shared memory as BF16 hi + lo parts;
+// for each chunk A (hi + lo) is written and one thread issues tcgen05.mma
+// (kind::f16, BF16 inputs, FP32 accumulation in tensor memory): Ahi Bhi + Ahi Blo +
+// Alo Bhi per K block of 16, which keeps ~16 significant bits of both operands.
+// While the tensor cores run, the threads compute the rows of the CTA's next chunk.
+// The epilogue reads the accumulator with tcgen05.ld, multiplies each row by its
+// complex factor, transposes 32 rows through shared memory and adds them to their
+// destinations with warp-coalesced red.global.add.v4.f32 (one 128-byte row segment
+// per 8 lanes).  Destinations receive contributions from several cones, so the
+// summation order (and the last bits of the result) varies from run to run on this
+// path.
 //
 // The level-D direct sums (near field) and the leaf analytic factors are computed on
 // CUDA cores by warp-cooperative kernels: lanes own right-hand sides, and each
@@ -92,6 +93,241 @@ struct ConeKernelArgs {
     float2 *u;        // sorted fields [N][nrhs]
 };
 
+// One CTA job: 128 rows (a chunk) of the evaluations that read relevant cone `slot`.
+struct ConeJob {
+    int slot, c0, rows, rows_t, t0, u0;
+};
+
+// the CTA's next job: the next chunk of this cone, else the first chunk of the next
+// cone (stride gridDim.x) with rows; false past the last cone
+__device__ __forceinline__ bool next_job(const LevelDev &L, const ConeKernelArgs &a, ConeJob &j)
+{
+    if (j.slot >= 0 && j.c0 + kM < j.rows) {
+        j.c0 += kM;
+        return true;
+    }
+    const bool up = a.do_upward && a.d > 3;
+    for (int s = j.slot < 0 ? (int)blockIdx.x : j.slot + (int)gridDim.x; s < L.nact; s += gridDim.x) {
+        const int t0 = a.do_targets ? L.tl_start[s] : 0;
+        const int rt = a.do_targets ? L.tl_start[s + 1] - t0 : 0;
+        const int u0 = up ? L.ul_start[s] : 0;
+        const int ru = up ? L.ul_start[s + 1] - u0 : 0;
+        if (rt + ru > 0) {
+            j.slot = s;
+            j.c0 = 0;
+            j.rows = rt + ru;
+            j.rows_t = rt;
+            j.t0 = t0;
+            j.u0 = u0;
+            return true;
+        }
+    }
+    j.slot = L.nact;
+    return false;
+}
+
+struct RowData {
+    float2 *dest;   // destination row (nrhs complex values), nullptr past the job's rows
+    float fr, fi;   // complex factor of the row
+};
+
+// Lagrange weights w[13] and factor of row `row` of job j: a cousin target (centred
+// factor G(x, x_k^d)) or a parent interpolation point (re-centring factor)
+__device__ __forceinline__ RowData row_geometry(const PlanDev &pd, const LevelDev &L, const LevelDev *Lp,
+                                                const ConeKernelArgs &a, const ConeJob &j, bool tab, int row,
+                                                float *w)
+{
+    RowData rd = {nullptr, 0.f, 0.f};
+    const int r = j.c0 + row;
+    if (r >= j.rows) return rd;
+    cpx<float> f;
+    if (r < j.rows_t) {
+        const int e = j.t0 + r;
+        const int i = L.tl[e];
+        if (L.tl_loc) {
+            float4 t = L.tl_loc[e];
+            float2 G = L.tl_fac[e];
+            lagrange(3, pd.tsf, pd.itsf, t.x, w);
+            lagrange(5, pd.taf, pd.itaf, t.y, w + 3);
+            lagrange(5, pd.taf, pd.itaf, t.z, w + 8);
+            f = {G.x, G.y};
+        } else {
+            const double *ck = L.center + 3 * (size_t)L.act_box[j.slot];
+            double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]), vz = __dsub_rn(pd.zs[i], ck[2]);
+            ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
+            f = green_r<float>(pd.kappa, g.r);
+        }
+        rd.dest = a.u + (size_t)i * a.nrhs;
+    } else {
+        const int e = L.ul[j.u0 + r - j.rows_t];
+        const int psl = e / kP, node = e % kP;
+        const int pcone = Lp->act_cone[psl];
+        const int oct = (int)(L.key[L.act_box[j.slot]] & 7u);
+        const int trow = tab ? table_row(L.ubits, L.urank, pcone) : -1;
+        if (trow >= 0) {
+            const UpEntry<float, 13> &en = ((const UpEntry<float, 13> *)L.utab)[((size_t)trow * 8 + oct) * kP + node];
+#pragma unroll
+            for (int m = 0; m < 13; ++m) w[m] = en.w[m];
+            f = {en.fr, en.fi};
+        } else {
+            up_geometry<float, 3, 5>(pd, L, *Lp, pcone, node, oct, w, f);
+        }
+        rd.dest = (float2 *)Lp->F + ((size_t)psl * kP + node) * a.nrhs;
+    }
+    rd.fr = f.x;
+    rd.fi = f.y;
+    return rd;
+}
+
+// A row `row` from its weights: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c, as BF16
+// hi and lo parts; zero for an empty row and for the padding columns p >= 75
+__device__ __forceinline__ void write_A_row(const float *w, bool valid, int row, unsigned char *A_hi,
+                                            unsigned char *A_lo)
+{
+#pragma unroll
+    for (int kc = 0; kc < kK / 8; ++kc) {
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float x2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int p = kc * 8 + q * 2 + h;
+                float x = 0.f;
+                if (valid && p < kP) {
+                    const int ia = p / 25, ib = (p / 5) % 5, ic = p % 5;
+                    x = w[ia] * w[3 + ib] * w[8 + ic];
+                }
+                x2[h] = x;
+            }
+            __nv_bfloat16 h0, l0, h1, l1;
+            bf16_split(x2[0], h0, l0);
+            bf16_split(x2[1], h1, l1);
+            hv[q] = pack2(h0, h1);
+            lv[q] = pack2(l0, l1);
+        }
+        const uint32_t off = a_off(row, kc * 8);
+        *(uint4 *)(A_hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *(uint4 *)(A_lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+}
+
+// The cone's values as B (hi, lo): complex -> (re, im) columns 2r, 2r+1; batches of
+// kBatch independent loads per thread before any conversion
+__device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrhs, int npad, uint32_t lbo_b,
+                                            unsigned char *B_hi, unsigned char *B_lo, int tid)
+{
+    const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
+    const int half_n = npad / 2, tot = kP * half_n;
+    for (int base = tid; base < tot; base += kBatch * kThreads) {
+        float2 v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = base + u * kThreads;
+            const int p = idx / half_n, r = idx - p * half_n;
+            v[u] = (idx < tot && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = base + u * kThreads;
+            if (idx < tot) {
+                const int p = idx / half_n, r = idx - p * half_n;
+                __nv_bfloat16 h0, l0, h1, l1;
+                bf16_split(v[u].x, h0, l0);
+                bf16_split(v[u].y, h1, l1);
+                const uint32_t off = b_off(p, 2 * r, lbo_b);
+                *(uint32_t *)(B_hi + off) = pack2(h0, h1);
+                *(uint32_t *)(B_lo + off) = pack2(l0, l1);
+            }
+        }
+    }
+}
+
+// 15 MMAs (5 K blocks x {hi.hi, hi.lo, lo.hi}) into the accumulator, then a commit
+// that arrives on mbar when they have completed
+__device__ __forceinline__ void issue_cone_mma(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                               uint32_t lbo_b, uint32_t idesc, uint32_t mbar)
+{
+#pragma unroll
+    for (int kb = 0; kb < kK / 16; ++kb) {
+        const uint64_t dah = umma_desc(ah + kb * 256, 128, SBO_A);
+        const uint64_t dal = umma_desc(al + kb * 256, 128, SBO_A);
+        const uint64_t dbh = umma_desc(bh + kb * 2 * lbo_b, lbo_b, 128);
+        const uint64_t dbl = umma_desc(bl + kb * 2 * lbo_b, lbo_b, 128);
+        const uint32_t acc0 = kb > 0 ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0)
+                     : "memory");
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dah), "l"(dbl), "r"(idesc), "r"(1u)
+                     : "memory");
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                     "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
+                     : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// Epilogue, 32 accumulator columns (16 right-hand sides) per pass: thread tid writes
+// row tid times its factor to the warp's stage rows; then the warp adds four 128-byte
+// row segments per instruction (red.global.add.v4.f32, 16 bytes per lane), so that
+// the additions are coalesced per row.  Columns 2 nrhs is a multiple of 4 (nrhs even).
+__device__ __forceinline__ void cone_epilogue(uint32_t tmem, int tid, int nrhs, const RowData &rd,
+                                              unsigned char *stage)
+{
+    const int warp = tid >> 5, lane = tid & 31, lr = lane >> 3, lc = (lane & 7) * 4;
+    float *srow = (float *)(stage + (size_t)tid * kStageStride);
+    const unsigned char *swarp = stage + (size_t)warp * 32 * kStageStride;
+    const unsigned long long dest_u = (unsigned long long)rd.dest;
+    for (int cb = 0; cb < 2 * nrhs; cb += 32) {
+        uint32_t v[32];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int ncol = min(32, 2 * nrhs - cb);
+        __syncwarp();  // the previous pass has read the stage
+        if (rd.dest) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                if (j < ncol) {
+                    const float r0 = __uint_as_float(v[j]), i0 = __uint_as_float(v[j + 1]);
+                    const float r1 = __uint_as_float(v[j + 2]), i1 = __uint_as_float(v[j + 3]);
+                    *(float4 *)(srow + j) = make_float4(rd.fr * r0 - rd.fi * i0, rd.fr * i0 + rd.fi * r0,
+                                                        rd.fr * r1 - rd.fi * i1, rd.fr * i1 + rd.fi * r1);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int rr = 4 * q + lr;  // the warp's row read by this lane
+            const unsigned long long d = __shfl_sync(0xffffffffu, dest_u, rr);
+            if (d != 0ull && lc < ncol) {
+                const float4 x = *(const float4 *)(swarp + (size_t)rr * kStageStride + lc * 4);
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"((float *)d + cb + lc), "f"(x.x),
+                             "f"(x.y), "f"(x.z), "f"(x.w)
+                             : "memory");
+            }
+        }
+    }
+}
+
+// k_cone_mma: two CTAs of 128 threads per SM; each walks its (cone, 128-row chunk)
+// jobs.  Per job: B (when the job starts a cone) and A are written to shared memory,
+// one thread issues the MMAs, and while the tensor cores run, every thread computes
+// its row of the next job (weights, factor, destination: the global loads of the
+// row), then drains this job's accumulator.
 __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernelArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -119,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     }
     // padding rows p = 75..79 of B stay zero for the whole kernel
     for (int idx = tid; idx < (kK - kP) * npad; idx += kThreads) {
-        int p = kP + idx / npad, n = idx % npad;
+        const int p = kP + idx / npad, n = idx % npad;
         *(__nv_bfloat16 *)(B_hi + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
         *(__nv_bfloat16 *)(B_lo + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
     }
@@ -128,215 +364,58 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
     const uint32_t idesc = umma_idesc(kM, npad);
-    uint32_t phase = 0;
-    bool failed = false;
-
     const LevelDev *Lp = a.d > 3 ? &pd.lev[a.d - 1] : nullptr;
     const bool tab = a.do_upward && a.d > 3 && L.utab != nullptr;
+    uint32_t phase = 0;
 
-    for (int slot = blockIdx.x; slot < L.nact && !failed; slot += gridDim.x) {
-        const int t0 = a.do_targets ? L.tl_start[slot] : 0;
-        const int rows_t = a.do_targets ? L.tl_start[slot + 1] - t0 : 0;
-        const int u0 = (a.do_upward && a.d > 3) ? L.ul_start[slot] : 0;
-        const int rows_u = (a.do_upward && a.d > 3) ? L.ul_start[slot + 1] - u0 : 0;
-        const int rows = rows_t + rows_u;
-        if (rows == 0) continue;
-        // B: the cone's values, complex -> (re, im) columns 2r, 2r+1
-        // batches of kBatch independent loads per thread before any conversion
-        const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
-        const int half_n = npad / 2, tot = kP * half_n;
-        for (int base = tid; base < tot; base += kBatch * kThreads) {
-            float2 v[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                int idx = base + u * kThreads;
-                int p = idx / half_n, r = idx - p * half_n;
-                v[u] = (idx < tot && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                int idx = base + u * kThreads;
-                if (idx < tot) {
-                    int p = idx / half_n, r = idx - p * half_n;
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    bf16_split(v[u].x, h0, l0);
-                    bf16_split(v[u].y, h1, l1);
-                    uint32_t off = b_off(p, 2 * r, lbo_b);
-                    *(uint32_t *)(B_hi + off) = pack2(h0, h1);
-                    *(uint32_t *)(B_lo + off) = pack2(l0, l1);
-                }
-            }
-        }
-        const int k = L.act_box[slot];
-        const double *ck = L.center + 3 * (size_t)k;
-        const int oct = (int)(L.key[k] & 7u);
-        for (int c0 = 0; c0 < rows; c0 += kM) {
-            const int row = c0 + tid;
-            const bool valid = row < rows;
-            float w[13];
-            cpx<float> f = {0.f, 0.f};
-            float2 *dest = nullptr;
-            if (valid) {
-                if (row < rows_t) {
-                    const int e = t0 + row;
-                    const int i = L.tl[e];
-                    if (L.tl_loc) {
-                        float4 t = L.tl_loc[e];
-                        float2 G = L.tl_fac[e];
-                        lagrange(3, pd.tsf, pd.itsf, t.x, w);
-                        lagrange(5, pd.taf, pd.itaf, t.y, w + 3);
-                        lagrange(5, pd.taf, pd.itaf, t.z, w + 8);
-                        f = {G.x, G.y};
-                    } else {
-                        double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]),
-                               vz = __dsub_rn(pd.zs[i], ck[2]);
-                        ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
-                        f = green_r<float>(pd.kappa, g.r);
-                    }
-                    dest = a.u + (size_t)i * nrhs;
-                } else {
-                    int e = L.ul[u0 + row - rows_t];
-                    int psl = e / kP, node = e % kP;
-                    int pcone = Lp->act_cone[psl];
-                    int trow = tab ? table_row(L.ubits, L.urank, pcone) : -1;
-                    if (trow >= 0) {
-                        const UpEntry<float, 13> &en = ((const UpEntry<float, 13> *)L.utab)[((size_t)trow * 8 + oct) * kP + node];
-#pragma unroll
-                        for (int m = 0; m < 13; ++m) w[m] = en.w[m];
-                        f = {en.fr, en.fi};
-                    } else {
-                        up_geometry<float, 3, 5>(pd, L, *Lp, pcone, node, oct, w, f);
-                    }
-                    dest = (float2 *)Lp->F + ((size_t)psl * kP + node) * nrhs;
-                }
-            }
-            // A row: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c; 16-byte stores of 8 k
-#pragma unroll
-            for (int kc = 0; kc < kK / 8; ++kc) {
-                uint32_t hv[4], lv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float x2[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        int p = kc * 8 + q * 2 + h;
-                        float x = 0.f;
-                        if (valid && p < kP) {
-                            int ia = p / 25, ib = (p / 5) % 5, ic = p % 5;
-                            x = w[ia] * w[3 + ib] * w[8 + ic];
-                        }
-                        x2[h] = x;
-                    }
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    bf16_split(x2[0], h0, l0);
-                    bf16_split(x2[1], h1, l1);
-                    hv[q] = pack2(h0, h1);
-                    lv[q] = pack2(l0, l1);
-                }
-                uint32_t off = a_off(tid, kc * 8);
-                *(uint4 *)(A_hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                *(uint4 *)(A_lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
-#pragma unroll
-                for (int kb = 0; kb < kK / 16; ++kb) {
-                    uint64_t dah = umma_desc(ah + kb * 256, 128, SBO_A);
-                    uint64_t dal = umma_desc(al + kb * 256, 128, SBO_A);
-                    uint64_t dbh = umma_desc(bh + kb * 2 * lbo_b, lbo_b, 128);
-                    uint64_t dbl = umma_desc(bl + kb * 2 * lbo_b, lbo_b, 128);
-                    uint32_t acc0 = kb > 0 ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(dah), "l"(dbh), "r"(idesc), "r"(acc0)
-                        : "memory");
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(dah), "l"(dbl), "r"(idesc), "r"(1u)
-                        : "memory");
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(dal), "l"(dbh), "r"(idesc), "r"(1u)
-                        : "memory");
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&mbar))
-                             : "memory");
-            }
-            uint32_t done = 0;
-            for (int it = 0; it < kWaitLimit && !done; ++it) {
-                asm volatile(
-                    "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
-                    : "=r"(done)
-                    : "r"(smem_u32(&mbar)), "r"(phase)
-                    : "memory");
-            }
-            // the decision must be the same for every thread of the CTA
-            if (__syncthreads_or(done ? 0 : 1)) {
-                if (tid == 0) atomicAdd(pd.err, 1);
-                failed = true;
-                break;
-            }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // epilogue, 32 accumulator columns (16 right-hand sides) per pass: thread tid
-            // writes row tid times its factor to the warp's stage rows; then the warp adds
-            // four 128-byte row segments per instruction (red.global.add.v4.f32, 16 bytes
-            // per lane), so that the additions are coalesced per row
-            float *srow = (float *)(stage + (size_t)tid * kStageStride);
-            const unsigned char *swarp = stage + (size_t)warp * 32 * kStageStride;
-            const unsigned long long dest_u = (unsigned long long)dest;
-            const int lane = tid & 31, lr = lane >> 3, lc = (lane & 7) * 4;
-            for (int cb = 0; cb < 2 * nrhs; cb += 32) {
-                uint32_t v[32];
-                uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int ncol = min(32, 2 * nrhs - cb);  // a multiple of 4: nrhs is even
-                __syncwarp();                             // the previous pass has read the stage
-                if (valid) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        if (j < ncol) {
-                            float r0 = __uint_as_float(v[j]), i0 = __uint_as_float(v[j + 1]);
-                            float r1 = __uint_as_float(v[j + 2]), i1 = __uint_as_float(v[j + 3]);
-                            *(float4 *)(srow + j) = make_float4(f.x * r0 - f.y * i0, f.x * i0 + f.y * r0,
-                                                                f.x * r1 - f.y * i1, f.x * i1 + f.y * r1);
-                        }
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int rr = 4 * q + lr;  // the warp's row read by this lane
-                    const unsigned long long d = __shfl_sync(0xffffffffu, dest_u, rr);
-                    if (d != 0ull && lc < ncol) {
-                        float4 x = *(const float4 *)(swarp + (size_t)rr * kStageStride + lc * 4);
-                        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(
-                                         (float *)d + cb + lc),
-                                     "f"(x.x), "f"(x.y), "f"(x.z), "f"(x.w)
-                                     : "memory");
-                    }
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        }
+    ConeJob cur;
+    cur.slot = -1;
+    cur.c0 = 0;
+    cur.rows = 0;
+    bool have = next_job(L, a, cur);
+    float w[13];
+    RowData rd = {nullptr, 0.f, 0.f};
+    if (have) rd = row_geometry(pd, L, Lp, a, cur, tab, tid, w);
+    while (have) {
+        // the previous job's MMAs have completed: B and A may be rewritten
+        if (cur.c0 == 0) load_cone_B(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid);
+        write_A_row(w, rd.dest != nullptr, tid, A_hi, A_lo);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            issue_cone_mma(tmem, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), lbo_b, idesc,
+                           smem_u32(&mbar));
+        }
+        // the next job's row while the tensor cores run this one
+        ConeJob nxt = cur;
+        const bool have_n = next_job(L, a, nxt);
+        float wn[13];
+        RowData rn = {nullptr, 0.f, 0.f};
+        if (have_n) rn = row_geometry(pd, L, Lp, a, nxt, tab, tid, wn);
+        uint32_t done = 0;
+        for (int it = 0; it < kWaitLimit && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(&mbar)), "r"(phase)
+                : "memory");
+        }
+        // the decision must be the same for every thread of the CTA
+        if (__syncthreads_or(done ? 0 : 1)) {
+            if (tid == 0) atomicAdd(pd.err, 1);
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        cone_epilogue(tmem, tid, nrhs, rd, stage);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        cur = nxt;
+        rd = rn;
+#pragma unroll
+        for (int m = 0; m < 13; ++m) w[m] = wn[m];
+        have = have_n;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
