@@ -212,26 +212,30 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
     }
 }
 
-// The cone's values as B (hi, lo): complex -> (re, im) columns 2r, 2r+1; batches of
-// kBatch independent loads per thread before any conversion
+// The cone's values as B (hi, lo): complex -> (re, im) columns 2r, 2r+1.  Lane l of a
+// warp converts (p, r) = (8 pb + l / 4, 4 rb + l % 4) of a tile (pb, rb), so that its
+// 32 four-byte stores fill one core matrix (no bank conflicts) and its loads read
+// eight 32-byte runs.  Batches of kBatch independent loads per thread before any
+// conversion; nt threads (a multiple of 32) take part, t is this thread's index.
 __device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrhs, int npad, uint32_t lbo_b,
-                                            unsigned char *B_hi, unsigned char *B_lo, int tid)
+                                            unsigned char *B_hi, unsigned char *B_lo, int t, int nt)
 {
     const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
-    const int half_n = npad / 2, tot = kP * half_n;
-    for (int base = tid; base < tot; base += kBatch * kThreads) {
+    const int ntr = npad / 8;               // r tiles of 4: npad / 2 columns pairs
+    const int tot = (kK / 8) * ntr * 32;    // (p tiles) x (r tiles) x 32 lanes
+    for (int base = t; base < tot; base += kBatch * nt) {
         float2 v[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int idx = base + u * kThreads;
-            const int p = idx / half_n, r = idx - p * half_n;
-            v[u] = (idx < tot && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
+            const int idx = base + u * nt, tile = idx >> 5, l = idx & 31;
+            const int p = (tile / ntr) * 8 + (l >> 2), r = (tile % ntr) * 4 + (l & 3);
+            v[u] = (idx < tot && p < kP && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
-            const int idx = base + u * kThreads;
-            if (idx < tot) {
-                const int p = idx / half_n, r = idx - p * half_n;
+            const int idx = base + u * nt, tile = idx >> 5, l = idx & 31;
+            const int p = (tile / ntr) * 8 + (l >> 2), r = (tile % ntr) * 4 + (l & 3);
+            if (idx < tot && p < kP) {
                 __nv_bfloat16 h0, l0, h1, l1;
                 bf16_split(v[u].x, h0, l0);
                 bf16_split(v[u].y, h1, l1);
@@ -272,54 +276,79 @@ __device__ __forceinline__ void issue_cone_mma(uint32_t tmem, uint32_t ah, uint3
                  : "memory");
 }
 
-// Epilogue, 32 accumulator columns (16 right-hand sides) per pass: thread tid writes
-// row tid times its factor to the warp's stage rows; then the warp adds four 128-byte
-// row segments per instruction (red.global.add.v4.f32, 16 bytes per lane), so that
-// the additions are coalesced per row.  Columns 2 nrhs is a multiple of 4 (nrhs even).
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(ta)
+        : "memory");
+}
+
+// One pass of 32 accumulator columns [c, c + 32): thread tid writes its row times the
+// row's factor to the warp's stage rows; then the warp reads four 128-byte row
+// segments per step (16 bytes per lane) and adds them to their destinations with
+// red.global.add.v4.f32, so that the additions are coalesced per row.  All stage
+// reads and pointer shuffles come before the reductions.
+__device__ __forceinline__ void epilogue_pass(const uint32_t (&v)[32], int c, int ncols, int lane, const RowData &rd,
+                                              float *srow, const unsigned char *swarp)
+{
+    const int lr = lane >> 3, lc = (lane & 7) * 4;
+    const int ncol = min(32, ncols - c);  // a multiple of 4: nrhs is even
+    const unsigned long long dest_u = (unsigned long long)rd.dest;
+    __syncwarp();  // the previous pass has read the stage
+    if (rd.dest) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            if (j < ncol) {
+                const float r0 = __uint_as_float(v[j]), i0 = __uint_as_float(v[j + 1]);
+                const float r1 = __uint_as_float(v[j + 2]), i1 = __uint_as_float(v[j + 3]);
+                *(float4 *)(srow + j) = make_float4(rd.fr * r0 - rd.fi * i0, rd.fr * i0 + rd.fi * r0,
+                                                    rd.fr * r1 - rd.fi * i1, rd.fr * i1 + rd.fi * r1);
+            }
+        }
+    }
+    __syncwarp();
+    float4 x[8];
+    unsigned long long d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int rr = 4 * q + lr;  // the warp's row read by this lane
+        d[q] = __shfl_sync(0xffffffffu, dest_u, rr);
+        x[q] = *(const float4 *)(swarp + (size_t)rr * kStageStride + lc * 4);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (d[q] != 0ull && lc < ncol)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"((float *)d[q] + c + lc), "f"(x[q].x),
+                         "f"(x[q].y), "f"(x[q].z), "f"(x[q].w)
+                         : "memory");
+    }
+}
+
+// Epilogue of one chunk: row tid of the accumulator times the row's factor, added to
+// the row's destination; 64 columns are read from tensor memory per wait.
 __device__ __forceinline__ void cone_epilogue(uint32_t tmem, int tid, int nrhs, const RowData &rd,
                                               unsigned char *stage)
 {
-    const int warp = tid >> 5, lane = tid & 31, lr = lane >> 3, lc = (lane & 7) * 4;
+    const int warp = tid >> 5, lane = tid & 31;
     float *srow = (float *)(stage + (size_t)tid * kStageStride);
     const unsigned char *swarp = stage + (size_t)warp * 32 * kStageStride;
-    const unsigned long long dest_u = (unsigned long long)rd.dest;
-    for (int cb = 0; cb < 2 * nrhs; cb += 32) {
-        uint32_t v[32];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(ta));
+    const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int ncols = 2 * nrhs;
+    for (int cb = 0; cb < ncols; cb += 64) {
+        uint32_t v0[32], v1[32];
+        const bool two = cb + 32 < ncols;
+        __syncwarp();  // tcgen05.ld / wait::ld are .sync.aligned: the warp must be converged
+        tmem_ld32(base + (uint32_t)cb, v0);
+        if (two) tmem_ld32(base + (uint32_t)(cb + 32), v1);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int ncol = min(32, 2 * nrhs - cb);
-        __syncwarp();  // the previous pass has read the stage
-        if (rd.dest) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                if (j < ncol) {
-                    const float r0 = __uint_as_float(v[j]), i0 = __uint_as_float(v[j + 1]);
-                    const float r1 = __uint_as_float(v[j + 2]), i1 = __uint_as_float(v[j + 3]);
-                    *(float4 *)(srow + j) = make_float4(rd.fr * r0 - rd.fi * i0, rd.fr * i0 + rd.fi * r0,
-                                                        rd.fr * r1 - rd.fi * i1, rd.fr * i1 + rd.fi * r1);
-                }
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int rr = 4 * q + lr;  // the warp's row read by this lane
-            const unsigned long long d = __shfl_sync(0xffffffffu, dest_u, rr);
-            if (d != 0ull && lc < ncol) {
-                const float4 x = *(const float4 *)(swarp + (size_t)rr * kStageStride + lc * 4);
-                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"((float *)d + cb + lc), "f"(x.x),
-                             "f"(x.y), "f"(x.z), "f"(x.w)
-                             : "memory");
-            }
-        }
+        epilogue_pass(v0, cb, ncols, lane, rd, srow, swarp);
+        if (two) epilogue_pass(v1, cb + 32, ncols, lane, rd, srow, swarp);
     }
 }
 
@@ -347,6 +376,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncwarp();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
                      "r"(a.tmem_cols)
@@ -378,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     if (have) rd = row_geometry(pd, L, Lp, a, cur, tab, tid, w);
     while (have) {
         // the previous job's MMAs have completed: B and A may be rewritten
-        if (cur.c0 == 0) load_cone_B(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid);
+        if (cur.c0 == 0) load_cone_B(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid, kThreads);
         write_A_row(w, rd.dest != nullptr, tid, A_hi, A_lo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -419,6 +449,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    __syncwarp();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
 }
