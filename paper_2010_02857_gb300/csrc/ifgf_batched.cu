@@ -91,40 +91,43 @@ struct ConeKernelArgs {
     int do_targets;   // cousin targets of level d -> u
     int do_upward;    // parent interpolation points (d > 3) -> F^{d-1}
     float2 *u;        // sorted fields [N][nrhs]
+    int *work;        // cone counter of this launch, zero at launch
 };
 
-// One CTA job: 128 rows (a chunk) of the evaluations that read relevant cone `slot`.
+// One CTA job: 128 rows (a chunk) of the evaluations that read relevant cone `slot`,
+// the CTA's cone number q.
 struct ConeJob {
-    int slot, c0, rows, rows_t, t0, u0;
+    int slot, c0, rows, rows_t, t0, u0, q;
 };
 
-// the CTA's next job: the next chunk of this cone, else the first chunk of the next
-// cone (stride gridDim.x) with rows; false past the last cone
-__device__ __forceinline__ bool next_job(const LevelDev &L, const ConeKernelArgs &a, ConeJob &j)
+// The CTA takes its cones one at a time from a level-wide counter, in slot order
+// (slots are box-major in Morton order), so that all CTAs work on neighbouring boxes
+// and the destinations of their reductions stay in L2.  sq[q % 2] holds the slot of
+// the CTA's cone q, fetched one cone ahead by thread 0 (take_cone).
+__device__ __forceinline__ bool next_job(const LevelDev &L, const ConeKernelArgs &a, const int *sq, ConeJob &j)
 {
     if (j.slot >= 0 && j.c0 + kM < j.rows) {
         j.c0 += kM;
         return true;
     }
-    const bool up = a.do_upward && a.d > 3;
-    for (int s = j.slot < 0 ? (int)blockIdx.x : j.slot + (int)gridDim.x; s < L.nact; s += gridDim.x) {
-        const int t0 = a.do_targets ? L.tl_start[s] : 0;
-        const int rt = a.do_targets ? L.tl_start[s + 1] - t0 : 0;
-        const int u0 = up ? L.ul_start[s] : 0;
-        const int ru = up ? L.ul_start[s + 1] - u0 : 0;
-        if (rt + ru > 0) {
-            j.slot = s;
-            j.c0 = 0;
-            j.rows = rt + ru;
-            j.rows_t = rt;
-            j.t0 = t0;
-            j.u0 = u0;
-            return true;
-        }
+    const int q = j.slot < 0 ? 0 : j.q + 1;
+    const int s = sq[q & 1];
+    if (s >= L.nact) {
+        j.slot = L.nact;
+        return false;
     }
-    j.slot = L.nact;
-    return false;
+    const bool up = a.do_upward && a.d > 3;
+    j.slot = s;
+    j.q = q;
+    j.c0 = 0;
+    j.t0 = a.do_targets ? L.tl_start[s] : 0;
+    j.rows_t = a.do_targets ? L.tl_start[s + 1] - j.t0 : 0;
+    j.u0 = up ? L.ul_start[s] : 0;
+    j.rows = j.rows_t + (up ? L.ul_start[s + 1] - j.u0 : 0);  // an empty cone is one empty chunk
+    return true;
 }
+
+__device__ __forceinline__ int take_cone(const ConeKernelArgs &a) { return atomicAdd(a.work, 1); }
 
 struct RowData {
     float2 *dest;   // destination row (nrhs complex values), nullptr past the job's rows
@@ -362,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tbase;
+    __shared__ int sq[2];  // slots of the CTA's cones q and q + 1 (entry q % 2)
     const int tid = threadIdx.x, warp = tid >> 5;
     const LevelDev &L = pd.lev[a.d];
     const int npad = a.npad, nrhs = a.nrhs;
@@ -375,6 +379,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sq[0] = take_cone(a);
+        sq[1] = take_cone(a);
     }
     __syncwarp();
     if (warp == 0) {
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     cur.slot = -1;
     cur.c0 = 0;
     cur.rows = 0;
-    bool have = next_job(L, a, cur);
+    bool have = next_job(L, a, sq, cur);
     float w[13];
     RowData rd = {nullptr, 0.f, 0.f};
     if (have) rd = row_geometry(pd, L, Lp, a, cur, tab, tid, w);
@@ -419,7 +425,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
         }
         // the next job's row while the tensor cores run this one
         ConeJob nxt = cur;
-        const bool have_n = next_job(L, a, nxt);
+        const bool have_n = next_job(L, a, sq, nxt);
+        // entering cone q: the entry of cone q - 1 takes cone q + 1 (read from the next
+        // iteration on, after the barriers below)
+        if (tid == 0 && have_n && nxt.c0 == 0) sq[(nxt.q + 1) & 1] = take_cone(a);
         float wn[13];
         RowData rn = {nullptr, 0.f, 0.f};
         if (have_n) rn = row_geometry(pd, L, Lp, a, nxt, tab, tid, wn);
@@ -643,6 +652,9 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
             a.do_targets = 1;
             a.do_upward = d > 3;
             a.u = us;
+            a.work = pd.sched + d;
+            e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+            if (e != cudaSuccess) return e;
             int grid = std::min(L.nact, 2 * 152);
             k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
             ++nl;

@@ -107,6 +107,7 @@ struct PlanDev {
     const dbl4 *leaf_off = nullptr;   // [N] x_j - centre of its leaf box, and its squared norm
     const int *perm = nullptr;
     int *err = nullptr;                                  // device invariant-failure counter
+    int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel
     LevelDev lev[IFGF_MAX_LEVELS + 1];
 };
 

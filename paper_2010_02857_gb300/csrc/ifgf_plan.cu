@@ -583,6 +583,8 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
     DALLOC(d_err, int, 1);
     CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     pd.err = d_err;
+    DALLOC(d_sched, int, IFGF_MAX_LEVELS + 1);
+    pd.sched = d_sched;
 
     // points to the device (AoS, caller order)
     Scratch pts;
