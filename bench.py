@@ -17,6 +17,7 @@ sample of targets, all host cores) on the same workload and metric.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -49,6 +50,14 @@ UPWARD_FLOPS_PER_EVAL = 372 + 8
 # i.e. 2 FMAs per clock per SM.
 FP64_FMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of
+# the same bench command (profiles/k_upward_sphere_32lambda_traffic.md), keyed by
+# (workload, precision).  A configuration without a capture of the current kernel
+# reports null.
+TRAFFIC_BYTES_PER_LAUNCH = {
+    ("sphere_32lambda", "fp64"): 50.89e9 / 5,
+}
 
 
 def _dist_env():
@@ -193,8 +202,12 @@ def main():
     ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched"],
                     help="override the workload's precision")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="override the workload's number of right-hand sides (same generator)")
     args = ap.parse_args()
     wl = wi.WORKLOADS[args.workload]
+    if args.nrhs is not None:
+        wl = dataclasses.replace(wl, nrhs=args.nrhs)
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -298,8 +311,10 @@ def main():
                     "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
                             f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
     achieved = flops / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
+    traffic = TRAFFIC_BYTES_PER_LAUNCH.get((wl.name, precision)) if nrhs == wi.WORKLOADS[wl.name].nrhs else None
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None})
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None})
 
     check = None
     if args.check:

@@ -266,6 +266,13 @@ WORKLOADS = {
                             leaf_ns=1, leaf_nc=2, nrhs=64, targets=2_048, seed=4, surface="cubes",
                             precision="batched",
                             description="three-cube union N=1572864, lambda=1, 64 RHS"),
+    # the three-cube union at 1/16 of the points with 6 levels and a quarter of the
+    # wavenumber: leaf boxes of the same size in wavelengths and points per leaf as the
+    # 8-level plan (profiling size for the tensor-core cone kernel)
+    "cubes_98k_64rhs": Workload("cubes_98k_64rhs", 98_304, 2.0 * math.pi / 4.0, 6,
+                                leaf_ns=1, leaf_nc=2, nrhs=64, targets=512, seed=4, surface="cubes",
+                                precision="batched",
+                                description="three-cube union N=98304, 64 RHS (profiling size)"),
     # unit sphere, diameter 256 wavelengths, D = 9, 8 RHS
     "sphere_256lambda": Workload("sphere_256lambda", 25_165_824, wavelengths_to_kappa(2.0, 256), 9,
                                  leaf_ns=3, leaf_nc=6, nrhs=8, targets=1_024, seed=5, surface="sphere",
