@@ -24,6 +24,10 @@
 
 #include "ifgf_device.cuh"
 
+// launch of the FP32 kernels blocked for 4 right-hand sides (ifgf_apply_f32_r4.cu)
+cudaError_t ifgf_launch_f32_r4(const PlanDev &pd, int nrhs, const void *in, void *out, int mode, int adjoint,
+                               cudaStream_t st, StageTimer &tm);
+
 namespace ifgf {
 
 constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
@@ -705,6 +709,11 @@ cudaError_t launch_orders(const PlanDev &pd, int nrhs, const void *in, void *out
         return adjoint ? launch_adjoint<T, 1, PS, PA>(pd, nrhs, in, out, mode, st, tm)
                        : launch_forward<T, 1, PS, PA>(pd, nrhs, in, out, mode, st, tm);
     }
+    // FP32 with 2..4 right-hand sides: kernels blocked for 4 (half the accumulator
+    // registers of the 8-wide blocking, so more warps per SM; instantiated in
+    // ifgf_apply_f32_r4.cu)
+    if constexpr (sizeof(T) == 4)
+        if (nrhs <= 4) return ifgf_launch_f32_r4(pd, nrhs, in, out, mode, adjoint, st, tm);
     constexpr int RB = sizeof(T) == 8 ? 4 : 8;
     return adjoint ? launch_adjoint<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm)
                    : launch_forward<T, RB, PS, PA>(pd, nrhs, in, out, mode, st, tm);
