@@ -131,9 +131,11 @@ template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, do
 // Analytic factor g(q, x_j) = (R/|q - x_j|) e^{i kappa (|q - x_j| - R)} (Eq. factored_f) for
 // an interpolation point q = x_k + R dir of a leaf cone and a source x_j = x_k + delta in
 // the same leaf box.  Double plans evaluate it as written.  Float plans use
-// |q - x_j| - R = (|delta|^2 - 2 R dir.delta) / (|q - x_j| + R): the numerator, where the
-// cancellation of the plain difference lives, is formed in FP64 from the stored FP64
-// offset; the denominator and the rest need only FP32 relative accuracy.
+// |q - x_j| - R = (|delta|^2 - 2 R dir.delta) / (|q - x_j| + R), all in FP32 from the
+// stored FP32 offset delta and |delta|^2: no difference of nearly equal numbers is
+// formed, so the absolute error of the numerator is about eps32 * 2 R |delta| and the
+// phase error about kappa |delta| eps32 (below 1e-6 rad for leaf boxes of a wavelength
+// at kappa = 800).
 template <typename T>
 __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const double *q, const double *dir, int j)
 {
@@ -144,15 +146,14 @@ __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const
         double a = R / r1;
         return {a * c, a * s};
     } else {
-        const dbl4 o = pd.leaf_off[j];
-        double num = fma(-2.0 * R, dir[0] * o.x + dir[1] * o.y + dir[2] * o.z, o.w);
-        float Rf = (float)R;
-        float r1 = sqrtf(fmaxf(Rf * Rf + (float)num, 0.f));
-        float den = r1 + Rf;
-        float ph = (float)(pd.kappa * num * (double)(1.0f / den));
+        const float4 o = pd.leaf_off[j];
+        const float Rf = (float)R, dx = (float)dir[0], dy = (float)dir[1], dz = (float)dir[2];
+        const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
+        const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
+        const float ph = (float)pd.kappa * num / (r1 + Rf);
         float c, s;
         sincosf(ph, &s, &c);
-        float a = Rf / r1;
+        const float a = Rf / r1;
         return {a * c, a * s};
     }
 }

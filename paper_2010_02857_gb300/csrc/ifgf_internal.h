@@ -32,10 +32,6 @@
 
 #define IFGF_MAX_LEVELS 20
 
-// four doubles, 32-byte aligned (point offset from its leaf centre and its squared norm)
-struct __align__(32) dbl4 {
-    double x, y, z, w;
-};
 #define IFGF_MAX_P 8
 
 struct LevelDev {
@@ -104,7 +100,7 @@ struct PlanDev {
     float tsf[IFGF_MAX_P] = {}, taf[IFGF_MAX_P] = {};   // the same in FP32, for FP32 weights
     float itsf[IFGF_MAX_P] = {}, itaf[IFGF_MAX_P] = {};
     const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
-    const dbl4 *leaf_off = nullptr;   // [N] x_j - centre of its leaf box, and its squared norm
+    const float4 *leaf_off = nullptr;  // [N] x_j - centre of its leaf box, and its squared norm (FP32)
     const int *perm = nullptr;
     int *err = nullptr;                                  // device invariant-failure counter
     int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel

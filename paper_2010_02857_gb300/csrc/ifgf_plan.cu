@@ -149,15 +149,16 @@ __global__ void k_level_boxes(const uint64_t *leafkey, const int *incl, int n, i
     if (i == n - 1) start[b + 1] = n;
 }
 
-// offset of every point from the centre of its leaf box, and its squared norm
-__global__ void k_leaf_offsets(PlanDev pd, dbl4 *off)
+// offset of every point from the centre of its leaf box, and its squared norm: formed
+// in FP64, stored in FP32 (for the FP32 leaf factor)
+__global__ void k_leaf_offsets(PlanDev pd, float4 *off)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
     const LevelDev &L = pd.lev[pd.D];
     const double *c = L.center + 3 * (size_t)L.pt_box[i];
     double dx = pd.xs[i] - c[0], dy = pd.ys[i] - c[1], dz = pd.zs[i] - c[2];
-    off[i] = dbl4{dx, dy, dz, dx * dx + dy * dy + dz * dz};
+    off[i] = make_float4((float)dx, (float)dy, (float)dz, (float)(dx * dx + dy * dy + dz * dz));
 }
 
 __global__ void k_parents(const int *start, int nbox, const int *pt_box_parent, int *parent)
@@ -690,7 +691,7 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         Lp.child_start = cstart;
     }
     {
-        DALLOC(off, dbl4, n);
+        DALLOC(off, float4, n);
         k_leaf_offsets<<<nblocks(n), kThreads, 0, st>>>(pd, off);
         CK(cudaGetLastError());
         pd.leaf_off = off;
