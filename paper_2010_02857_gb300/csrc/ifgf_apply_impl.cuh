@@ -128,6 +128,43 @@ template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, do
     return {a * c, a * s};
 }
 
+// Near-field distances of float plans without FP64 per pair.  A point's position
+// relative to the centre c_k of a leaf box k is formed once in FP64 and split into FP32
+// high and low parts; a source x_j of box k carries the same split of x_j - c_k (the
+// stored leaf offset and its remainder).  The difference of the high parts is exact
+// when the two points are close (Sterbenz), so r = |p - o_j| has FP32 relative
+// accuracy for every pair; the phase kappa r then carries an absolute error of about
+// kappa r * 6e-8.
+struct Rel32 {
+    float hx, hy, hz, lx, ly, lz;
+};
+
+__device__ __forceinline__ Rel32 rel32(double x, double y, double z, const double *c)
+{
+    const double px = x - c[0], py = y - c[1], pz = z - c[2];
+    Rel32 p;
+    p.hx = (float)px;
+    p.hy = (float)py;
+    p.hz = (float)pz;
+    p.lx = (float)(px - (double)p.hx);
+    p.ly = (float)(py - (double)p.hy);
+    p.lz = (float)(pz - (double)p.hz);
+    return p;
+}
+
+// e^{i kappa r} / (4 pi r) for r = |p - o_j| (FP32 only)
+__device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 &oh, const float4 &ol, float kf)
+{
+    const float dx = (p.hx - oh.x) + (p.lx - ol.x);
+    const float dy = (p.hy - oh.y) + (p.ly - ol.y);
+    const float dz = (p.hz - oh.z) + (p.lz - ol.z);
+    const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    float c, s;
+    sincosf(kf * r, &s, &c);
+    const float a = __fdividef((float)kInv4Pi, r);
+    return {a * c, a * s};
+}
+
 // Analytic factor g(q, x_j) = (R/|q - x_j|) e^{i kappa (|q - x_j| - R)} (Eq. factored_f) for
 // an interpolation point q = x_k + R dir of a leaf cone and a source x_j = x_k + delta in
 // the same leaf box.  Double plans evaluate it as written.  Float plans use
@@ -150,10 +187,12 @@ __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const
         const float Rf = (float)R, dx = (float)dir[0], dy = (float)dir[1], dz = (float)dir[2];
         const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
         const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
-        const float ph = (float)pd.kappa * num / (r1 + Rf);
+        // the quotients need FP32 relative accuracy only (r1 + R and r1 lie far inside
+        // the range where the fast division is accurate to 2 ulp)
+        const float ph = __fdividef((float)pd.kappa * num, r1 + Rf);
         float c, s;
         sincosf(ph, &s, &c);
-        const float a = Rf / r1;
+        const float a = __fdividef(Rf, r1);
         return {a * c, a * s};
     }
 }
@@ -380,10 +419,13 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
             for (int e = 0; e < 27; ++e) {
                 int k = LD.nbr[27 * (size_t)b + e];
                 if (k < 0) break;
+                Rel32 pk;
+                if constexpr (sizeof(T) == 4) pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
                 for (int j = LD.start[k]; j < LD.start[k + 1]; ++j) {
                     if (j == i) continue;
-                    double r1 = dist<T>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]);
-                    cpx<T> G = green_r<T>(pd.kappa, r1);
+                    cpx<T> G;
+                    if constexpr (sizeof(T) == 4) G = green_near32(pk, pd.leaf_off[j], pd.leaf_lo[j], (float)pd.kappa);
+                    else G = green_r<T>(pd.kappa, dist<T>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]));
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (R == 1 || r0 + r < nrhs) {
@@ -589,10 +631,13 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
             for (int e = 0; e < 27; ++e) {
                 int k = LD.nbr[27 * (size_t)b + e];
                 if (k < 0) break;
+                Rel32 pk;
+                if constexpr (sizeof(T) == 4) pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
                 for (int i = LD.start[k]; i < LD.start[k + 1]; ++i) {
                     if (i == j) continue;
-                    double r1 = dist<T>(pd.xs[i] - x, pd.ys[i] - y, pd.zs[i] - z);
-                    cpx<T> G = cconj(green_r<T>(pd.kappa, r1));
+                    cpx<T> G;
+                    if constexpr (sizeof(T) == 4) G = cconj(green_near32(pk, pd.leaf_off[i], pd.leaf_lo[i], (float)pd.kappa));
+                    else G = cconj(green_r<T>(pd.kappa, dist<T>(pd.xs[i] - x, pd.ys[i] - y, pd.zs[i] - z)));
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (R == 1 || r0 + r < nrhs) {

@@ -510,10 +510,11 @@ __global__ void __launch_bounds__(128) k_near_batched(PlanDev pd, int nrhs, cons
             int k = LD.nbr[27 * (size_t)b + e];
             if (k < 0) break;
             const int j1 = LD.start[k + 1];
+            const Rel32 pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
             for (int j0 = LD.start[k]; j0 < j1; j0 += 32) {
                 int j = j0 + lane;
                 cpx<float> G = {0.f, 0.f};
-                if (j < j1 && j != i) G = green_r<float>(pd.kappa, dist<float>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]));
+                if (j < j1 && j != i) G = green_near32(pk, pd.leaf_off[j], pd.leaf_lo[j], (float)pd.kappa);
                 int cnt = min(32, j1 - j0);
                 for (int t = 0; t < cnt; ++t) {
                     float gx = __shfl_sync(0xffffffffu, G.x, t), gy = __shfl_sync(0xffffffffu, G.y, t);

@@ -303,6 +303,34 @@ def test_mixed_precision_matches_fp64_oracle(pkg, torch_cuda, case):
     assert g.check() == 0
 
 
+def test_mixed_near_field_close_pairs(pkg, torch_cuda):
+    # Float plans form near-field distances in FP32 from split leaf offsets; the
+    # difference of the high parts is exact for close pairs, so pairs 1e-7 of a leaf
+    # box apart keep FP32 relative accuracy (a plain FP32 difference of the offsets
+    # would be off by tens of percent there).
+    torch = torch_cuda
+    wl, pts, _ = _make((3000, 3, 4, 2, 4))
+    H = (pts.max(0) - pts.min(0)).max() / 2 ** 3
+    rng = np.random.default_rng(5)
+    dirs = rng.normal(size=(3, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    extra = pts[[10, 500, 2000]] + 1e-7 * H * dirs
+    allp = np.ascontiguousarray(np.vstack([pts, extra]))
+    n = allp.shape[0]
+    sigma = wi.complex_normal(21, (1, n))
+    g = pkg.Plan(torch.from_numpy(allp).cuda(), wl.kappa, 4, 3, 5, 2, 4, precision="mixed")
+    o = oracle.Plan(allp, wl.kappa, 4, 3, 5, 2, 4)
+    un = g.apply_partial(torch.from_numpy(sigma.astype(np.complex64)).cuda(), 1).cpu().numpy()
+    ref = o.apply(sigma, mode=1)
+    assert rel(un, ref) < 2e-5
+    close = [10, 500, 2000, n - 3, n - 2, n - 1]
+    err = np.abs(un[0, close] - ref[0, close]) / np.abs(ref[0, close])
+    assert err.max() < 1e-5, err
+    w = g.apply_adjoint(torch.from_numpy(sigma.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(w, o.apply_adjoint(sigma)) < 2e-5
+    assert g.check() == 0
+
+
 def test_autograd_gradient_matches_finite_differences(pkg, torch_cuda):
     # L = ||A sigma||^2 is quadratic, so central differences are exact up to rounding
     torch = torch_cuda
