@@ -220,20 +220,31 @@ __device__ __forceinline__ ConeGeom geom_weights(const PlanDev &pd, const LevelD
 // Re-centring factor G(q, x_k) / G(q, x_j) = (r_j / r_k) e^{i kappa (r_k - r_j)} for the
 // interpolation point q = x_j + Rj dir, child centre x_k = x_j + delta, r_k = |q - x_k|.
 // r_k - r_j = (|delta|^2 - 2 Rj dir.delta) / (r_k + r_j) avoids the cancellation of
-// the plain difference.
+// the plain difference.  Float plans evaluate it in FP32: the absolute error of the
+// numerator is about eps32 * 2 Rj |delta|, so the phase error is about
+// kappa |delta| eps32 (2e-5 rad for the coarsest level of a 256-wavelength sphere).
 template <typename T>
 __device__ __forceinline__ cpx<T> recentre(double kappa, double Rj, const double *dir, double rk,
                                            double dx, double dy, double dz)
 {
-    double dd = dx * dx + dy * dy + dz * dz;
-    double yd = dir[0] * dx + dir[1] * dy + dir[2] * dz;
-    double diff = (dd - 2.0 * Rj * yd) / (rk + Rj);
-    T c, s;
-    expi(kappa * diff, c, s);
-    T a;
-    if constexpr (sizeof(T) == 8) a = Rj / rk;
-    else a = (float)Rj / (float)rk;
-    return {a * c, a * s};
+    if constexpr (sizeof(T) == 8) {
+        double dd = dx * dx + dy * dy + dz * dz;
+        double yd = dir[0] * dx + dir[1] * dy + dir[2] * dz;
+        double diff = (dd - 2.0 * Rj * yd) / (rk + Rj);
+        T c, s;
+        expi(kappa * diff, c, s);
+        T a = Rj / rk;
+        return {a * c, a * s};
+    } else {
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz, Rf = (float)Rj, rkf = (float)rk;
+        const float dd = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        const float yd = fmaf((float)dir[0], fx, fmaf((float)dir[1], fy, (float)dir[2] * fz));
+        const float diff = __fdividef(fmaf(-2.0f * Rf, yd, dd), rkf + Rf);
+        float c, s;
+        sincosf((float)kappa * diff, &s, &c);
+        const float a = __fdividef(Rf, rkf);
+        return {a * c, a * s};
+    }
 }
 
 // ---------------------------------------------------------------------------------
