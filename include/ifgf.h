@@ -86,7 +86,12 @@ typedef struct {
                        store at plan time each cousin-target evaluation's cone slot,
                        weights (local coordinates for IFGF_MIXED) and centred factor,
                        and the geometry of every upward evaluation of levels without an
-                       upward table; the evaluations then skip that geometry */
+                       upward table; the evaluations then skip that geometry;
+                       bit 6: adjoints of two-level plans build their upward transpose
+                       lists in ranges of at most 4096 evaluations (testing; the
+                       default range is 2^28).  Two-level plans build the adjoint's
+                       transpose lists level by level right before use, unless bit 0
+                       built them at plan time. */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels
@@ -110,7 +115,8 @@ typedef struct {
  *             (Sec. 4 uses (1, 2) at H_D ~ lambda / 4).
  *   stream    cudaStream_t used for the build; the call synchronises it before return.
  *   out       receives the plan (NULL on failure).
- * Errors: IFGF_EINVAL for bad arguments, IFGF_ENOMEM, IFGF_ECUDA.
+ * Errors: IFGF_EINVAL for bad arguments (including coinciding points), IFGF_ENOMEM,
+ * IFGF_ECUDA.
  */
 ifgf_status ifgf_plan_create(const double *points, int64_t n, double kappa, int levels,
                              int p_radial, int p_angular, const ifgf_options *opt,

@@ -177,7 +177,10 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         din = p->stage_in;
     }
     if (!out_dev) dout = p->stage_out;
-    if (adjoint && !p->adjoint_ready) {
+    // two-buffer plans build their adjoint's transpose lists per level just in time
+    // (resident lists for all levels would not fit beside the cone values)
+    const bool jit = adjoint && p->pingpong && !p->adjoint_ready;
+    if (adjoint && !p->adjoint_ready && !jit) {
         // first adjoint call: build the transpose lists (synchronises the stream)
         ifgf_status s = ifgf_build_adjoint_lists(p, st);
         if (s != IFGF_OK) return s;
@@ -194,6 +197,12 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         const int nc = std::min(p->rhs_chunk, nrhs - c0);
         const void *cin = (const char *)din + (size_t)c0 * p->n * eb;
         void *cout = (char *)dout + (size_t)c0 * p->n * eb;
+        if (jit) {
+            ifgf_status s = p->precision == IFGF_FP64 ? ifgf_run_adjoint_jit_f64(p, nc, cin, cout, mode, st)
+                                                      : ifgf_run_adjoint_jit_f32(p, nc, cin, cout, mode, st);
+            if (s != IFGF_OK) return s;
+            continue;
+        }
         if (p->precision == IFGF_FP64)
             e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
         else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nc % 2 == 0 && nc <= 64)

@@ -18,3 +18,8 @@ cudaError_t ifgf_build_evalcache_f32(const PlanDev &pd, int d, int which, cudaSt
 {
     return ifgf::build_evalcache<float>(pd, d, which, st);
 }
+
+ifgf_status ifgf_run_adjoint_jit_f32(ifgf_plan *p, int nrhs, const void *in, void *out, int mode, cudaStream_t st)
+{
+    return ifgf::run_adjoint_jit<float>(p, nrhs, in, out, mode, st);
+}

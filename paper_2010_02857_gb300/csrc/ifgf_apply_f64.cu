@@ -24,3 +24,8 @@ cudaError_t ifgf_build_evalcache_f64(const PlanDev &pd, int d, int which, cudaSt
 {
     return ifgf::build_evalcache<double>(pd, d, which, st);
 }
+
+ifgf_status ifgf_run_adjoint_jit_f64(ifgf_plan *p, int nrhs, const void *in, void *out, int mode, cudaStream_t st)
+{
+    return ifgf::run_adjoint_jit<double>(p, nrhs, in, out, mode, st);
+}

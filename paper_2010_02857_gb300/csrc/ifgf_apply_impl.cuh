@@ -515,8 +515,20 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
 // ---------------------------------------------------------------------------------
 constexpr int kAdjWarps = 4;
 
+// AdjLists: the transpose lists a launch reads (CSR over level-d slots, start[s - base]),
+// the slots [s0, s1) it covers, the passes it runs (bit 0 cousin targets, bit 1 parent
+// interpolation points) and whether it adds to the adjoint values instead of storing.
+struct AdjLists {
+    const int *tstart, *tlist;
+    int tbase;
+    const int *ustart, *ulist;
+    int ubase;
+    int s0, s1, passes, accumulate;
+};
+
 template <typename T, int R, int PS, int PA>
-__global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d, int nrhs, const void *vs, int mode)
+__global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d, int nrhs, const void *vs, int mode,
+                                                               AdjLists al)
 {
     constexpr int P = PS * PA * PA;
     constexpr int NW = PS + 2 * PA;
@@ -527,7 +539,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kAdjWarps + warp;
     const int nwarps = gridDim.x * kAdjWarps;
-    for (int slot = gw; slot < L.nact; slot += nwarps) {
+    for (int slot = al.s0 + gw; slot < al.s1; slot += nwarps) {
         const int k = L.act_box[slot];
         const double *ck = L.center + 3 * (size_t)k;
         for (int r0 = 0; r0 < nrhs; r0 += R) {
@@ -537,22 +549,24 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[h][r] = {T(0), T(0)};
             for (int pass = 0; pass < 2; ++pass) {
+                if (!((al.passes >> pass) & 1)) continue;
                 const int *lst;
                 int e_begin, e_end;
                 if (pass == 0) {
-                    lst = L.tl;
-                    e_begin = L.tl_start[slot];
-                    e_end = L.tl_start[slot + 1];
+                    lst = al.tlist;
+                    e_begin = al.tstart[slot - al.tbase];
+                    e_end = al.tstart[slot - al.tbase + 1];
                 } else {
                     if (d <= 3 || !(mode & 2)) break;
-                    lst = L.ul;
-                    e_begin = L.ul_start[slot];
-                    e_end = L.ul_start[slot + 1];
+                    lst = al.ulist;
+                    e_begin = al.ustart[slot - al.ubase];
+                    e_end = al.ustart[slot - al.ubase + 1];
                 }
                 for (int e0 = e_begin; e0 < e_end; e0 += 32) {
                     int e = e0 + lane;
                     if (e < e_end) {
-                        int item = lst[e];
+                        // a point index, or parent slot * P + node (can exceed 2^31 - 1)
+                        const unsigned item = (unsigned)lst[e];
                         int psl = 0, pnode = 0;
                         T w[NW];
                         cpx<T> f;
@@ -618,7 +632,16 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
                 if (p < P)
 #pragma unroll
                     for (int r = 0; r < R; ++r)
-                        if (R == 1 || r0 + r < nrhs) st<T>(L.Fadj, ((size_t)slot * P + p) * nrhs + r0 + r, acc[h][r]);
+                        if (R == 1 || r0 + r < nrhs) {
+                            const size_t o = ((size_t)slot * P + p) * nrhs + r0 + r;
+                            cpx<T> v = acc[h][r];
+                            if (al.accumulate) {
+                                const cpx<T> old = ld<T>(L.Fadj, o);
+                                v.x += old.x;
+                                v.y += old.y;
+                            }
+                            st<T>(L.Fadj, o, v);
+                        }
             }
         }
     }
@@ -748,7 +771,9 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
             int nact = pd.lev[d].nact;
             if (nact == 0) continue;
             int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
-            k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode);
+            const LevelDev &L = pd.lev[d];
+            const AdjLists al = {L.tl_start, L.tl, 0, L.ul_start, L.ul, 0, 0, nact, 3, 0};
+            k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
             ++nl;
         }
         tm.mark(STAGE_ADJ_LEVEL, nl, st);
@@ -756,6 +781,80 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
     k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, mode);
     tm.mark(STAGE_ADJ_EVAL, 1, st);
     return cudaGetLastError();
+}
+
+// Adjoint of a two-buffer plan with transpose lists built just in time: per level d =
+// 3..D, the cousin-target lists of the level (one launch over all slots, storing), then
+// the upward lists in ranges of parent boxes of at most max_entries evaluations (one
+// launch per range over the child slots of that range, adding).  The child slots of a
+// range of parent boxes are contiguous, and every child slot takes all of its upward
+// entries from one range, so each slot's sum has a fixed order.
+template <typename T, int R, int PS, int PA>
+ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws, int mode, cudaStream_t st,
+                               int64_t max_entries)
+{
+    const PlanDev &pd = p->dev;
+    JitLists tl, ul;
+    ifgf_status s = IFGF_OK;
+    if (mode & 2) {
+        for (int d = 3; d <= pd.D && s == IFGF_OK; ++d) {
+            const int nact = pd.lev[d].nact;
+            if (nact == 0) continue;
+            const int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+            s = ifgf_jit_targets(p, d, &tl, st);
+            if (s != IFGF_OK) break;
+            {
+                const AdjLists al = {tl.start, tl.list, 0, nullptr, nullptr, 0, 0, nact, 1, 0};
+                k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+                if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; break; }
+            }
+            if (d > 3) {
+                std::vector<int> bounds;
+                s = ifgf_jit_chunks(p, d, max_entries, &bounds);
+                for (size_t c = 0; c + 1 < bounds.size() && s == IFGF_OK; ++c) {
+                    s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, st);
+                    if (s != IFGF_OK || ul.s1 == ul.s0) continue;
+                    const int nb = (int)std::min<int64_t>((ul.s1 - ul.s0 + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+                    const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1};
+                    k_adj_level<T, R, PS, PA><<<nb, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+                    if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; }
+                    // the lists are freed (and rebuilt) only after the launch has read them
+                    if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
+                }
+            }
+            if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
+        }
+    }
+    ifgf_jit_release(&tl);
+    ifgf_jit_release(&ul);
+    if (s != IFGF_OK) return s;
+    k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, mode);
+    if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint launch"; return IFGF_ECUDA; }
+    return IFGF_OK;
+}
+
+// permute, just-in-time adjoint, un-permute (FP64 or FP32 plans, one right-hand-side chunk)
+template <typename T>
+ifgf_status run_adjoint_jit(ifgf_plan *p, int nrhs, const void *in_user, void *out_user, int mode, cudaStream_t st)
+{
+    const PlanDev &pd = p->dev;
+    const int64_t tot = (int64_t)pd.n * nrhs;
+    const int64_t max_entries = (p->flags & 64) ? 4096 : ((int64_t)1 << 28);
+    k_permute_in<T><<<grid_for(tot, 256), 256, 0, st>>>(in_user, p->sig_sorted, pd.perm, pd.n, nrhs);
+    constexpr int RB = sizeof(T) == 8 ? 4 : 8;
+    ifgf_status s;
+    if (pd.Ps == 3 && pd.Pang == 5)
+        s = nrhs == 1 ? launch_adjoint_jit<T, 1, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries)
+                      : launch_adjoint_jit<T, RB, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
+    else if (pd.Ps == 4 && pd.Pang == 7)
+        s = nrhs == 1 ? launch_adjoint_jit<T, 1, 4, 7>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries)
+                      : launch_adjoint_jit<T, RB, 4, 7>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
+    else
+        return IFGF_EINVAL;
+    if (s != IFGF_OK) return s;
+    k_permute_out<T><<<grid_for(tot, 256), 256, 0, st>>>(p->u_sorted, out_user, pd.perm, pd.n, nrhs);
+    if (cudaGetLastError() != cudaSuccess) { p->last_error = "permute launch"; return IFGF_ECUDA; }
+    return IFGF_OK;
 }
 
 template <typename T, int PS, int PA>

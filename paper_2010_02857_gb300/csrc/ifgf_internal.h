@@ -196,8 +196,29 @@ struct TEntry32 {
     float gr, gi;
 };
 
+// Transpose lists built just in time for one level, for the adjoint of plans whose
+// lists do not stay resident (two-buffer plans): CSR over the level-d slots [s0, s1)
+// (start[s - s0] .. start[s - s0 + 1] index list).  Target lists hold point indices;
+// upward lists hold parent slot * P + node, read as unsigned.
+struct JitLists {
+    int s0 = 0, s1 = 0;
+    int *start = nullptr;
+    int *list = nullptr;
+    void *mem = nullptr;   // owns start and list
+};
+
 // plan.cu
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
+// cousin-target transpose lists of level d (all slots)
+ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, cudaStream_t st);
+// upward transpose lists of level d for the parent boxes [b0, b1) of level d-1
+ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, cudaStream_t st);
+void ifgf_jit_release(JitLists *l);
+// apply_f64.cu / apply_f32.cu: the adjoint with just-in-time lists (one RHS chunk)
+ifgf_status ifgf_run_adjoint_jit_f64(ifgf_plan *p, int nrhs, const void *in, void *out, int mode, cudaStream_t st);
+ifgf_status ifgf_run_adjoint_jit_f32(ifgf_plan *p, int nrhs, const void *in, void *out, int mode, cudaStream_t st);
+// parent-box ranges of level d-1 whose upward lists hold at most max_entries each
+ifgf_status ifgf_jit_chunks(ifgf_plan *p, int d, int64_t max_entries, std::vector<int> *bounds);
 ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st);
 ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p);
 cudaError_t ifgf_cache_target_geometry(const PlanDev &pd, int d, float4 *loc, float2 *fac, int64_t m, cudaStream_t st);

@@ -164,6 +164,23 @@ __global__ void k_leaf_offsets(PlanDev pd, float4 *off, float4 *lo)
     lo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
 }
 
+// Points must be pairwise distinct (Eq. field1 sums over m != l; the method's
+// factorisation divides by |x_l - x_m|).  Equal points share their Morton key and hence
+// their leaf box, so each point is compared with the later points of its leaf.
+__global__ void k_duplicates(PlanDev pd, int *found)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pd.n) return;
+    const LevelDev &L = pd.lev[pd.D];
+    const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
+    const int j1 = L.start[L.pt_box[i] + 1];
+    for (int j = i + 1; j < j1; ++j)
+        if (pd.xs[j] == x && pd.ys[j] == y && pd.zs[j] == z) {
+            atomicExch(found, 1);
+            return;
+        }
+}
+
 __global__ void k_parents(const int *start, int nbox, const int *pt_box_parent, int *parent)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -468,6 +485,42 @@ __global__ void k_emit_ulist(PlanDev pd, int d, const int *off, int *keys, int *
     }
 }
 
+// Upward evaluations of level d whose parent slots are [q0, q1), for just-in-time
+// lists: cnt[q - q0] = entries of parent slot q
+__global__ void k_parent_slot_count_range(PlanDev pd, int d, int q0, int q1, int *cnt)
+{
+    const LevelDev &Lp = pd.lev[d - 1];
+    int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    int j = Lp.act_box[q];
+    cnt[q - q0] = (Lp.child_start[j + 1] - Lp.child_start[j]) * pd.P;
+}
+
+// (child slot - s0, parent slot * P + node) pairs of those evaluations; the second
+// member is stored as the bits of an unsigned value (it can exceed 2^31 - 1)
+__global__ void k_emit_ulist_range(PlanDev pd, int d, int q0, int q1, int s0, const int *off, int *keys,
+                                   int *vals)
+{
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int64_t t = (int64_t)q0 * pd.P + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)q1 * pd.P) return;
+    const int slot = (int)(t / pd.P), node = (int)(t % pd.P);
+    const int j = Lp.act_box[slot];
+    const int nch = Lp.child_start[j + 1] - Lp.child_start[j];
+    const double hh = L.H * 0.5;
+    int o = off[slot - q0] + node * nch;
+    for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k, ++o) {
+        double v[3];
+        node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
+        ConeGeom g = cone_of(L, v[0], v[1], v[2]);
+        int sl = cone_slot(L, k, g.cone);
+        if (sl < 0) { atomicAdd(pd.err, 1); sl = s0; }
+        keys[o] = sl - s0;
+        vals[o] = (int)(unsigned)t;
+    }
+}
+
 // CSR starts from sorted keys: start[s] = first position with key >= s
 __global__ void k_csr_from_sorted(const int *keys, int64_t m, int nslot, int *start)
 {
@@ -681,6 +734,17 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         k_neighbours<<<nblocks(nbox), kThreads, 0, st>>>(key, nbox, 1 << (d - 1), nbr);
         CK(cudaGetLastError());
         L.nbr = nbr;
+    }
+    {
+        CK(cudaMemsetAsync(flag.ptr, 0, sizeof(int), st));
+        k_duplicates<<<nblocks(n), kThreads, 0, st>>>(pd, (int *)flag.ptr);
+        CK(cudaGetLastError());
+        int dup = 0;
+        CK(cudaMemcpy(&dup, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (dup) {
+            p->last_error = "duplicate points (the points must be pairwise distinct)";
+            return IFGF_EINVAL;
+        }
     }
     for (int d = 2; d <= D; ++d) {
         LevelDev &L = pd.lev[d];
@@ -1051,15 +1115,10 @@ ifgf_status ifgf_alloc_adjoint_values(ifgf_plan *p)
             if (!L.Fadj) { p->last_error = "adjoint value buffer"; return IFGF_ENOMEM; }
         }
     } else {
-        // the adjoint needs levels d-1 and d at a time, like the forward step
-        size_t even = 0, odd = 0;
-        for (int d = 3; d <= p->D; ++d) {
-            size_t b = (size_t)p->dev.lev[d].nact * p->P * p->rhs_chunk * eb;
-            if (d & 1) odd = std::max(odd, b); else even = std::max(even, b);
-        }
-        void *bufs[2] = {ifgf_dalloc(p, even), ifgf_dalloc(p, odd)};
-        if (!bufs[0] || !bufs[1]) { p->last_error = "adjoint value buffers"; return IFGF_ENOMEM; }
-        for (int d = 3; d <= p->D; ++d) p->dev.lev[d].Fadj = bufs[d & 1];
+        // the adjoint needs levels d-1 and d at a time, like the forward step, and a plan
+        // runs one evaluation at a time on its stream: the adjoint reuses the forward's
+        // two alternating buffers
+        for (int d = 3; d <= p->D; ++d) p->dev.lev[d].Fadj = p->dev.lev[d].F;
     }
     p->adjoint_values_ready = true;
     return IFGF_OK;
@@ -1130,4 +1189,143 @@ ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
     if (herr) { p->last_error = "adjoint lists: a cone lookup missed"; return IFGF_EINTERNAL; }
     p->adjoint_ready = true;
     return IFGF_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Just-in-time transpose lists (adjoint of two-buffer plans).  The resident lists of
+// ifgf_build_adjoint_lists cost 4 bytes per cousin and per upward evaluation for all
+// levels at once (about 190 GB for the 256-wavelength sphere); these are built for one
+// level, and the upward ones for a range of parent boxes, right before use.
+// ---------------------------------------------------------------------------------
+namespace {
+
+// stable sort of (key, value) pairs by key into list, and CSR starts over nslot keys
+ifgf_status sort_into_csr(ifgf_plan *p, int *keys, int *vals, int64_t m, int nslot, int *start, int *list,
+                          cudaStream_t st)
+{
+    Scratch kb;
+    if (!kb.alloc((size_t)m * 4)) { p->last_error = "adjoint list sort"; return IFGF_ENOMEM; }
+    int end_bit = 1;
+    while (end_bit < 31 && (1 << end_bit) <= nslot) ++end_bit;
+    size_t bytes = 0;
+    CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
+    Scratch tmp;
+    if (!tmp.alloc(bytes)) { p->last_error = "adjoint list sort temp"; return IFGF_ENOMEM; }
+    CK(cub::DeviceRadixSort::SortPairs(tmp.ptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
+    k_csr_from_sorted<<<nblocks(nslot + 1), kThreads, 0, st>>>((int *)kb.ptr, m, nslot, start);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return IFGF_OK;
+}
+
+// one allocation for start [nslot + 1] and list [m]
+ifgf_status jit_alloc(ifgf_plan *p, JitLists *out, int nslot, int64_t m)
+{
+    const size_t sb = ((size_t)(nslot + 1) * 4 + 255) / 256 * 256;
+    if (cudaMalloc(&out->mem, sb + (size_t)m * 4 + 16) != cudaSuccess) {
+        out->mem = nullptr;
+        p->last_error = "just-in-time adjoint lists";
+        return IFGF_ENOMEM;
+    }
+    out->start = (int *)out->mem;
+    out->list = (int *)((char *)out->mem + sb);
+    return IFGF_OK;
+}
+
+}  // namespace
+
+void ifgf_jit_release(JitLists *l)
+{
+    if (l->mem) cudaFree(l->mem);
+    *l = JitLists();
+}
+
+ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, cudaStream_t st)
+{
+    ifgf_jit_release(out);
+    PlanDev &pd = p->dev;
+    const LevelDev &L = pd.lev[d];
+    const int n = (int)p->n;
+    Scratch cnt, off;
+    if (!cnt.alloc((size_t)(n + 1) * 4) || !off.alloc((size_t)(n + 1) * 4)) return IFGF_ENOMEM;
+    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(n + 1) * 4, st));
+    k_point_cousin_count<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+    CK(cudaGetLastError());
+    ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, n + 1, st);
+    if (s != IFGF_OK) return s;
+    int m = 0;
+    CK(cudaMemcpy(&m, (int *)off.ptr + n, sizeof(int), cudaMemcpyDeviceToHost));
+    Scratch keys, vals;
+    if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+    k_emit_tlist<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)off.ptr, (int *)keys.ptr, (int *)vals.ptr);
+    CK(cudaGetLastError());
+    s = jit_alloc(p, out, L.nact, m);
+    if (s != IFGF_OK) return s;
+    out->s0 = 0;
+    out->s1 = L.nact;
+    return sort_into_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, out->start, out->list, st);
+}
+
+ifgf_status ifgf_jit_chunks(ifgf_plan *p, int d, int64_t max_entries, std::vector<int> *bounds)
+{
+    const LevelDev &Lp = p->dev.lev[d - 1];
+    const int nb = Lp.nbox;
+    std::vector<int> as(nb + 1), cs(nb + 1);
+    CK(cudaMemcpy(as.data(), Lp.act_start, (size_t)(nb + 1) * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cs.data(), Lp.child_start, (size_t)(nb + 1) * 4, cudaMemcpyDeviceToHost));
+    bounds->assign(1, 0);
+    int64_t acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t e = (int64_t)(as[b + 1] - as[b]) * p->P * (cs[b + 1] - cs[b]);
+        if (e > INT32_MAX) { p->last_error = "a parent box with more than 2^31 upward evaluations"; return IFGF_EINVAL; }
+        if (acc > 0 && acc + e > max_entries) {
+            bounds->push_back(b);
+            acc = 0;
+        }
+        acc += e;
+    }
+    bounds->push_back(nb);
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, cudaStream_t st)
+{
+    ifgf_jit_release(out);
+    PlanDev &pd = p->dev;
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    int q[2], cb[2], sl[2];
+    CK(cudaMemcpy(&q[0], Lp.act_start + b0, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&q[1], Lp.act_start + b1, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&cb[0], Lp.child_start + b0, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&cb[1], Lp.child_start + b1, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&sl[0], L.act_start + cb[0], 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&sl[1], L.act_start + cb[1], 4, cudaMemcpyDeviceToHost));
+    const int nq = q[1] - q[0], ns = sl[1] - sl[0];
+    Scratch cnt, off;
+    if (!cnt.alloc((size_t)(nq + 1) * 4) || !off.alloc((size_t)(nq + 1) * 4)) return IFGF_ENOMEM;
+    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nq + 1) * 4, st));
+    if (nq > 0) k_parent_slot_count_range<<<nblocks(nq), kThreads, 0, st>>>(pd, d, q[0], q[1], (int *)cnt.ptr);
+    CK(cudaGetLastError());
+    ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, nq + 1, st);
+    if (s != IFGF_OK) return s;
+    int m = 0;
+    CK(cudaMemcpy(&m, (int *)off.ptr + nq, sizeof(int), cudaMemcpyDeviceToHost));
+    Scratch keys, vals;
+    if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+    const int64_t nt = (int64_t)nq * pd.P;
+    if (nt > 0)
+        k_emit_ulist_range<<<nblocks(nt), kThreads, 0, st>>>(pd, d, q[0], q[1], sl[0], (int *)off.ptr,
+                                                             (int *)keys.ptr, (int *)vals.ptr);
+    CK(cudaGetLastError());
+    s = jit_alloc(p, out, ns, m);
+    if (s != IFGF_OK) return s;
+    out->s0 = sl[0];
+    out->s1 = sl[1];
+    if (m == 0) {
+        CK(cudaMemsetAsync(out->start, 0, (size_t)(ns + 1) * 4, st));
+        CK(cudaStreamSynchronize(st));
+        return IFGF_OK;
+    }
+    return sort_into_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, ns, out->start, out->list, st);
 }

@@ -256,6 +256,29 @@ def test_two_level_buffers_and_rhs_chunks_match(pkg, torch_cuda, precision, tol)
     assert a.check() == 0 and b.check() == 0 and c.check() == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_adjoint_with_just_in_time_lists(pkg, torch_cuda, precision, tol):
+    # two-level plans build the adjoint's transpose lists level by level right before
+    # use; flags bit 6 cuts the upward lists into ranges of at most 4096 evaluations,
+    # so every level runs as many ranges; bit 4: 2 right-hand sides per pass
+    torch = torch_cuda
+    wl, pts, _ = _make((3500, 4, 5, 1, 2))
+    nrhs = 3
+    v = wi.complex_normal(71, (nrhs, wl.n))
+    s = wi.complex_normal(72, (nrhs, wl.n))
+    o = oracle.Plan(pts, wl.kappa, 5, 3, 5, 1, 2)
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision=precision,
+                 flags=8 | 16 | 64)
+    assert g.stats()["pingpong"] == 1
+    w = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert rel(w, o.apply_adjoint(v)) < tol
+    # the adjoint identity <v, A s> = <A^H v, s> with the same plan's forward
+    u = g.apply(torch.from_numpy(s).cuda()).cpu().numpy()
+    lhs, rhs = np.vdot(v, u), np.vdot(w, s)
+    assert abs(lhs - rhs) / abs(lhs) < (1e-12 if precision == "fp64" else 1e-5)
+    assert g.check() == 0
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-6)])
 def test_evaluation_caches_match_on_the_fly_geometry(pkg, torch_cuda, precision, tol):
     # plan-time caches of cousin-target and untabled-upward geometry (default) vs none
@@ -329,6 +352,21 @@ def test_mixed_near_field_close_pairs(pkg, torch_cuda):
     w = g.apply_adjoint(torch.from_numpy(sigma.astype(np.complex64)).cuda()).cpu().numpy()
     assert rel(w, o.apply_adjoint(sigma)) < 2e-5
     assert g.check() == 0
+
+
+def test_duplicate_points_rejected(pkg, torch_cuda):
+    # the points must be pairwise distinct: an exact duplicate is an invalid argument,
+    # a point 1e-13 away from another is accepted
+    torch = torch_cuda
+    wl, pts, _ = _make((3000, 3, 4, 2, 4))
+    dup = np.ascontiguousarray(np.vstack([pts, pts[17:18]]))
+    with pytest.raises(pkg.IFGFError) as ei:
+        pkg.Plan(torch.from_numpy(dup).cuda(), wl.kappa, 4, 3, 5, 2, 4)
+    assert "duplicate" in str(ei.value)
+    near = dup.copy()
+    near[-1, 0] += 1e-13
+    g = pkg.Plan(torch.from_numpy(near).cuda(), wl.kappa, 4, 3, 5, 2, 4)
+    assert g.stats()["n"] == near.shape[0]
 
 
 def test_autograd_gradient_matches_finite_differences(pkg, torch_cuda):
