@@ -91,13 +91,24 @@ typedef struct {
                        lists in ranges of at most 4096 evaluations (testing; the
                        default range is 2^28).  Two-level plans build the adjoint's
                        transpose lists level by level right before use, unless bit 0
-                       built them at plan time. */
+                       built them at plan time;
+                       bit 7: host-side waits never see the device finish, so they
+                       end with IFGF_ETIMEOUT (testing; the limit is timeout_s, or
+                       0.05 s when that is 0);
+                       bit 8: the tensor-core cone kernel of IFGF_BATCHED_BF16 plans
+                       issues no MMA, so its bounded waits for them run out (after a
+                       shortened limit) and the device error counter records it
+                       (testing; see ifgf_plan_check). */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels
                        (d and d-1) and applies right-hand sides in chunks that fit; the
                        per-level values returned by ifgf_plan_get_values are then those
                        of the last two levels written */
+    double timeout_s;   /* limit of the host-side waits of an evaluation (calls with host
+                       buffers wait for their result; profiling waits for its events):
+                       past it the call returns IFGF_ETIMEOUT and the queued work
+                       completes on its own; 0 = no limit */
 } ifgf_options;
 
 /*

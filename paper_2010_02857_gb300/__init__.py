@@ -49,7 +49,8 @@ class IFGFError(RuntimeError):
 
 class ifgf_options(ctypes.Structure):
     _fields_ = [("leaf_ns", ctypes.c_int), ("leaf_nc", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("value_budget_bytes", ctypes.c_longlong)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("value_budget_bytes", ctypes.c_longlong),
+                ("timeout_s", ctypes.c_double)]
 
 
 _lib = None
@@ -123,7 +124,7 @@ def _stream(x=None):
 
 def plan_create(points, kappa: float, levels: int, p_radial: int = 3, p_angular: int = 5,
                 leaf_ns: int = 0, leaf_nc: int = 0, max_nrhs: int = 1, precision="fp64",
-                flags: int = 0, value_budget_bytes: int = 0, stream=None):
+                flags: int = 0, value_budget_bytes: int = 0, timeout_s: float = 0.0, stream=None):
     """ifgf_plan_create; points: [N,3] float64 (numpy or torch, host or device)."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
@@ -134,7 +135,7 @@ def plan_create(points, kappa: float, levels: int, p_radial: int = 3, p_angular:
         points = points.contiguous()
         n = points.shape[0]
     opt = ifgf_options(int(leaf_ns), int(leaf_nc), int(max_nrhs), int(precision), int(flags),
-                       int(value_budget_bytes))
+                       int(value_budget_bytes), float(timeout_s))
     h = ctypes.c_void_p()
     st = stream if stream is not None else _stream(points)
     _check(lib().ifgf_plan_create(_ptr(points), n, float(kappa), int(levels), int(p_radial),
@@ -176,14 +177,14 @@ class Plan:
     """An IFGF plan on the current CUDA device."""
 
     def __init__(self, points, kappa, levels, p_radial=3, p_angular=5, leaf_ns=0, leaf_nc=0,
-                 max_nrhs=1, precision="fp64", flags=0, value_budget_bytes=0):
+                 max_nrhs=1, precision="fp64", flags=0, value_budget_bytes=0, timeout_s=0.0):
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n = int(points.shape[0])
         self.levels = int(levels)
         self.max_nrhs = int(max_nrhs)
         self.P = p_radial * p_angular * p_angular
         self.handle = plan_create(points, kappa, levels, p_radial, p_angular, leaf_ns, leaf_nc,
-                                  max_nrhs, self.precision, flags, value_budget_bytes)
+                                  max_nrhs, self.precision, flags, value_budget_bytes, timeout_s)
 
     @property
     def complex_dtype(self):

@@ -1,10 +1,12 @@
 // C ABI of the IFGF library: argument checks, plan lifetime, host/device pointer
 // handling and introspection.  All numerical work is in ifgf_plan.cu and the
 // ifgf_apply_*.cu kernels.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ifgf_device.cuh"
@@ -73,9 +75,10 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         g_create_error = "IFGF_BATCHED_BF16 plans support (P_s, P_ang) = (3, 5)";
         return IFGF_EINVAL;
     }
-    ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0};
+    ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0, 0.0};
     if (opt) o = *opt;
     if (o.value_budget_bytes < 0) { g_create_error = "value_budget_bytes must be >= 0"; return IFGF_EINVAL; }
+    if (!(o.timeout_s >= 0.0)) { g_create_error = "timeout_s must be >= 0"; return IFGF_EINVAL; }
     if (o.max_nrhs <= 0) o.max_nrhs = 1;
     if (o.max_nrhs > 1024) { g_create_error = "max_nrhs must be <= 1024"; return IFGF_EINVAL; }
     if (o.precision != IFGF_FP64 && o.precision != IFGF_MIXED && o.precision != IFGF_BATCHED_BF16) {
@@ -97,6 +100,8 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     p->precision = o.precision;
     p->max_nrhs = o.max_nrhs;
     p->flags = o.flags;
+    p->dev.flags = o.flags;
+    p->timeout_s = o.timeout_s;
     p->value_budget = (size_t)o.value_budget_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     p->build_stream = st;
@@ -142,6 +147,47 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     }
     *out = p;
     return IFGF_OK;
+}
+
+// Host-side wait for the work queued on st, bounded by the plan's timeout_s: past it
+// the call reports IFGF_ETIMEOUT and leaves the queued work to complete on its own.
+// Flags bit 7 (testing) makes the device look unfinished.
+static ifgf_status wait_stream(ifgf_plan *p, cudaStream_t st)
+{
+    const bool fake = (p->flags & 128) != 0;
+    if (p->timeout_s <= 0.0 && !fake) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            p->last_error = std::string("stream synchronisation failed: ") + cudaGetErrorString(e);
+            return IFGF_ECUDA;
+        }
+        return IFGF_OK;
+    }
+    const double limit = p->timeout_s > 0.0 ? p->timeout_s : 0.05;
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess) {
+        p->last_error = "event creation failed";
+        return IFGF_ECUDA;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    ifgf_status s = IFGF_OK;
+    for (;;) {
+        const cudaError_t q = fake ? cudaErrorNotReady : cudaEventQuery(ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+            p->last_error = std::string("device error while waiting: ") + cudaGetErrorString(q);
+            s = IFGF_ECUDA;
+            break;
+        }
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit) {
+            p->last_error = "timed out waiting for the device";
+            s = IFGF_ETIMEOUT;
+            break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(ev);
+    return s;
 }
 
 ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, int mode, int adjoint,
@@ -216,10 +262,8 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
     }
     if (p->timer.on && p->timer.n > 1) {
         // profiling mode: wait for this call and attribute the time between marks
-        if (cudaEventSynchronize(p->timer.ev[p->timer.n - 1]) != cudaSuccess) {
-            p->last_error = "event synchronisation failed";
-            return IFGF_ECUDA;
-        }
+        const ifgf_status ws = wait_stream(p, st);
+        if (ws != IFGF_OK) return ws;
         for (int i = 1; i < p->timer.n; ++i) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, p->timer.ev[i - 1], p->timer.ev[i]);
@@ -238,13 +282,7 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
             return IFGF_ECUDA;
         }
     }
-    if (!in_dev || !out_dev) {
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            p->last_error = std::string("stream synchronisation failed: ") + cudaGetErrorString(e);
-            return IFGF_ECUDA;
-        }
-    }
+    if (!in_dev || !out_dev) return wait_stream(p, st);
     return IFGF_OK;
 }
 

@@ -105,6 +105,7 @@ struct PlanDev {
     const int *perm = nullptr;
     int *err = nullptr;                                  // device invariant-failure counter
     int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel
+    int flags = 0;         // the plan's option flags (test switches read by kernels)
     LevelDev lev[IFGF_MAX_LEVELS + 1];
 };
 
@@ -146,6 +147,7 @@ struct ifgf_plan {
     int precision = IFGF_FP64;
     int max_nrhs = 1;
     int flags = 0;
+    double timeout_s = 0;      // host-side wait limit of an evaluation (0: none)
     size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
     bool pingpong = false;     // two alternating level buffers instead of one per level
     size_t cache_bytes = 0;    // evaluation caches (0: none)

@@ -52,9 +52,31 @@ def test_invalid_arguments_rejected_before_any_device_work(libifgf):
         pkg.plan_create(pts, 1.0, 4)
     assert e.value.status == 1
     pts = np.random.default_rng(0).normal(size=(10, 3))
-    for kw in [dict(levels=2), dict(levels=21), dict(kappa=-1.0), dict(p_radial=2, p_angular=2)]:
+    for kw in [dict(levels=2), dict(levels=21), dict(kappa=-1.0), dict(p_radial=2, p_angular=2),
+               dict(timeout_s=-1.0)]:
         args = dict(kappa=1.0, levels=4)
         args.update(kw)
         with pytest.raises(pkg.IFGFError) as e:
             pkg.plan_create(pts, args.pop("kappa"), args.pop("levels"), **args)
         assert e.value.status == 1
+
+
+def test_options_struct_layout_matches_header(tmp_path):
+    # the ctypes mirror of ifgf_options must have the C layout of include/ifgf.h
+    import shutil
+    import subprocess
+    import paper_2010_02857_gb300 as pkg
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    fields = [f[0] for f in pkg.ifgf_options._fields_]
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ifgf.h\"\nint main(void) {\n"
+                   "  printf(\"%zu\", sizeof(ifgf_options));\n"
+                   + "".join(f'  printf(" %zu", offsetof(ifgf_options, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(pkg.ifgf_options)] + [getattr(pkg.ifgf_options, f).offset for f in fields]
+    assert got == want

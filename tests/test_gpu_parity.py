@@ -369,6 +369,44 @@ def test_duplicate_points_rejected(pkg, torch_cuda):
     assert g.stats()["n"] == near.shape[0]
 
 
+def test_host_wait_timeout_is_reported(pkg, torch_cuda):
+    # flags bit 7: the host-side wait never sees the device finish (a fake of the event
+    # query), so an evaluation with host buffers returns IFGF_ETIMEOUT after timeout_s;
+    # the queued work completes on its own and the device stays usable
+    torch = torch_cuda
+    wl, pts, sigma = _make((3000, 3, 4, 2, 4))
+    dpts = torch.from_numpy(pts).cuda()
+    g = pkg.Plan(dpts, wl.kappa, 4, 3, 5, 2, 4, flags=128, timeout_s=0.05)
+    with pytest.raises(pkg.IFGFError) as ei:
+        g.apply(sigma)  # numpy in and out: the call waits for its result
+    assert ei.value.status == 4
+    torch.cuda.synchronize()
+    h = pkg.Plan(dpts, wl.kappa, 4, 3, 5, 2, 4, timeout_s=30.0)
+    u = h.apply(sigma)  # a bounded wait that succeeds
+    u = u if isinstance(u, np.ndarray) else u.cpu().numpy()
+    ref = h.apply(torch.from_numpy(sigma).cuda()).cpu().numpy()
+    assert np.array_equal(u, ref)
+    assert g.check() == 0 and h.check() == 0
+
+
+def test_device_wait_limit_reports_error(pkg, torch_cuda):
+    # flags bit 8: the tensor-core cone kernel issues no MMA, so each CTA's bounded wait
+    # for its MMAs runs out (shortened limit); the kernel counts it in the device error
+    # counter, frees its tensor memory and returns, and the device stays usable
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    nrhs = 4
+    s = torch.from_numpy(wi.complex_normal(73, (nrhs, wl.n))).cuda()
+    dpts = torch.from_numpy(pts).cuda()
+    bad = pkg.Plan(dpts, wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched", flags=256)
+    bad.apply(s)
+    assert bad.check() > 0
+    good = pkg.Plan(dpts, wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched")
+    m = pkg.Plan(dpts, wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="mixed")
+    assert rel(good.apply(s).cpu().numpy(), m.apply(s).cpu().numpy()) < 2e-4
+    assert good.check() == 0 and m.check() == 0
+
+
 def test_autograd_gradient_matches_finite_differences(pkg, torch_cuda):
     # L = ||A sigma||^2 is quadratic, so central differences are exact up to rounding
     torch = torch_cuda
