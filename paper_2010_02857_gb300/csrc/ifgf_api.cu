@@ -61,6 +61,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
                                         int p_radial, int p_angular, const ifgf_options *opt,
                                         void *stream, ifgf_plan **out)
 {
+    NvtxRange range("ifgf_plan_create");
     if (out) *out = nullptr;
     g_create_error.clear();
     if (!points || !out) { g_create_error = "NULL argument"; return IFGF_EINVAL; }
@@ -193,6 +194,7 @@ static ifgf_status wait_stream(ifgf_plan *p, cudaStream_t st)
 ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, int mode, int adjoint,
                            cudaStream_t st)
 {
+    NvtxRange range(adjoint ? "ifgf_apply_adjoint" : "ifgf_apply");
     if (!p || !in || !out) return IFGF_EINVAL;
     if (nrhs < 1 || nrhs > p->max_nrhs) {
         p->last_error = "nrhs must be in [1, max_nrhs]";

@@ -720,19 +720,26 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
         if (mode & 2) {
             const LevelDev &L = pd.lev[pd.D];
             int64_t nt = (int64_t)L.nact * P;
-            if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
+            {
+                NvtxRange range("leaf", pd.D);
+                if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
+            }
             tm.mark(STAGE_LEAF, nt > 0, st);
             int nl = 0;
             for (int d = pd.D; d >= 4; --d) {
                 int64_t np = (int64_t)pd.lev[d - 1].nact * P;
                 if (np == 0) continue;
+                NvtxRange range("upward", d);
                 if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
                 else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
                 ++nl;
             }
             tm.mark(STAGE_UPWARD, nl, st);
         }
-        k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode, pd.D, 3, 0);
+        {
+            NvtxRange range("near and targets");
+            k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode, pd.D, 3, 0);
+        }
         tm.mark(STAGE_EVAL, 1, st);
         return cudaGetLastError();
     }
@@ -746,6 +753,7 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
         if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
         tm.mark(STAGE_LEAF, nt > 0, st);
         for (int d = pd.D; d >= 3; --d) {
+            NvtxRange range("targets and upward", d);
             k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, 2, d, d, 1);
             tm.mark(STAGE_EVAL, 1, st);
             if (d > 3) {
@@ -771,6 +779,7 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
             int nact = pd.lev[d].nact;
             if (nact == 0) continue;
             int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+            NvtxRange range("adjoint level", d);
             const LevelDev &L = pd.lev[d];
             const AdjLists al = {L.tl_start, L.tl, 0, L.ul_start, L.ul, 0, 0, nact, 3, 0};
             k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
@@ -801,6 +810,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
             const int nact = pd.lev[d].nact;
             if (nact == 0) continue;
             const int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+            NvtxRange range("adjoint level (lists built here)", d);
             s = ifgf_jit_targets(p, d, &tl, st);
             if (s != IFGF_OK) break;
             {

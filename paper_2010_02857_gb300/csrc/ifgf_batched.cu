@@ -647,6 +647,7 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
                 if (e != cudaSuccess) return e;
             }
             if (L.nact == 0) continue;
+            NvtxRange range("tensor-core cones", d);
             ConeKernelArgs a;
             a.d = d;
             a.nrhs = nrhs;

@@ -24,7 +24,10 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <cstdio>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include <cuda_runtime.h>
 
@@ -130,6 +133,22 @@ struct StageTimer {
         launches[n] = nlaunch;
         ++n;
     }
+};
+
+// NVTX range for profilers (nsys timelines, ncu --nvtx-include): the plan build, each
+// evaluation, and each stage and level of its launches.  Header-only NVTX: a no-op
+// unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    NvtxRange(const char *stage, int level)
+    {
+        char buf[48];
+        snprintf(buf, sizeof buf, "%s d=%d", stage, level);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 struct LevelHost {
