@@ -173,6 +173,19 @@ __device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 
 // formed, so the absolute error of the numerator is about eps32 * 2 R |delta| and the
 // phase error about kappa |delta| eps32 (below 1e-6 rad for leaf boxes of a wavelength
 // at kappa = 800).
+// FP32 leaf factor from the node's FP32 constants (R, dir, kappa) and the source's
+// stored offset o = (delta, |delta|^2)
+__device__ __forceinline__ cpx<float> leaf_factor32(float Rf, float dx, float dy, float dz, float kf, const float4 &o)
+{
+    const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
+    const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
+    const float ph = __fdividef(kf * num, r1 + Rf);
+    float c, s;
+    sincosf(ph, &s, &c);
+    const float a = __fdividef(Rf, r1);
+    return {a * c, a * s};
+}
+
 template <typename T>
 __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const double *q, const double *dir, int j)
 {
@@ -183,17 +196,9 @@ __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const
         double a = R / r1;
         return {a * c, a * s};
     } else {
-        const float4 o = pd.leaf_off[j];
-        const float Rf = (float)R, dx = (float)dir[0], dy = (float)dir[1], dz = (float)dir[2];
-        const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
-        const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
         // the quotients need FP32 relative accuracy only (r1 + R and r1 lie far inside
         // the range where the fast division is accurate to 2 ulp)
-        const float ph = __fdividef((float)pd.kappa * num, r1 + Rf);
-        float c, s;
-        sincosf(ph, &s, &c);
-        const float a = __fdividef(Rf, r1);
-        return {a * c, a * s};
+        return leaf_factor32((float)R, (float)dir[0], (float)dir[1], (float)dir[2], (float)pd.kappa, pd.leaf_off[j]);
     }
 }
 

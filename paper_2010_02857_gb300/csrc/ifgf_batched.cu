@@ -553,6 +553,9 @@ __global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, cons
     const double *c = L.center + 3 * (size_t)b;
     double q[3], dir[3];
     const double R0 = node_pos(L, 3, 5, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
+    // the node's FP32 constants, converted once per warp
+    const float Rf = (float)R0, dxf = (float)dir[0], dyf = (float)dir[1], dzf = (float)dir[2];
+    const float kf = (float)pd.kappa;
     cpx<float> acc[RPL];
 #pragma unroll
     for (int t = 0; t < RPL; ++t) acc[t] = {0.f, 0.f};
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, cons
         int j = j0 + lane;
         float gx = 0.f, gy = 0.f;
         if (j < j1) {
-            cpx<float> g = leaf_factor<float>(pd, R0, q, dir, j);
+            const cpx<float> g = leaf_factor32(Rf, dxf, dyf, dzf, kf, pd.leaf_off[j]);
             gx = g.x;
             gy = g.y;
         }
