@@ -117,6 +117,29 @@ template <typename T> __device__ __forceinline__ double dist(double dx, double d
     }
 }
 
+// 1/sqrt(r2) in FP64 without an FP64 square root or division: the FP32 estimate
+// (relative error about 2^-23) and two Newton steps, each of which squares the
+// relative error, so the result is within a few ulp.  Outside the FP32 range of r2 the
+// plain FP64 operations are used.
+__device__ __forceinline__ double rsqrt64(double r2)
+{
+    if (!(r2 > 1e-30 && r2 < 1e30)) return 1.0 / sqrt(r2);
+    double y = (double)rsqrtf((float)r2);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    y = y * fma(-0.5 * r2, y * y, 1.5);
+    return y;
+}
+
+// e^{i kappa r} / (4 pi r) in FP64 from r^2
+__device__ __forceinline__ cpx<double> green_r2_64(double kappa, double r2)
+{
+    const double y = rsqrt64(r2);
+    double c, s;
+    expi(kappa * (r2 * y), c, s);
+    const double a = kInv4Pi * y;
+    return {a * c, a * s};
+}
+
 // e^{i kappa r} / (4 pi r)
 template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, double r)
 {
@@ -190,10 +213,12 @@ template <typename T>
 __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const double *q, const double *dir, int j)
 {
     if constexpr (sizeof(T) == 8) {
-        double r1 = dist<T>(q[0] - pd.xs[j], q[1] - pd.ys[j], q[2] - pd.zs[j]);
+        const double dx = q[0] - pd.xs[j], dy = q[1] - pd.ys[j], dz = q[2] - pd.zs[j];
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double y = rsqrt64(r2);
         double c, s;
-        expi(pd.kappa * (r1 - R), c, s);
-        double a = R / r1;
+        expi(pd.kappa * (r2 * y - R), c, s);
+        const double a = R * y;
         return {a * c, a * s};
     } else {
         // the quotients need FP32 relative accuracy only (r1 + R and r1 lie far inside
@@ -441,7 +466,10 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
                     if (j == i) continue;
                     cpx<T> G;
                     if constexpr (sizeof(T) == 4) G = green_near32(pk, pd.leaf_off[j], pd.leaf_lo[j], (float)pd.kappa);
-                    else G = green_r<T>(pd.kappa, dist<T>(x - pd.xs[j], y - pd.ys[j], z - pd.zs[j]));
+                    else {
+                        const double dx = x - pd.xs[j], dy = y - pd.ys[j], dz = z - pd.zs[j];
+                        G = green_r2_64(pd.kappa, dx * dx + dy * dy + dz * dz);
+                    }
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (R == 1 || r0 + r < nrhs) {
@@ -676,7 +704,10 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
                     if (i == j) continue;
                     cpx<T> G;
                     if constexpr (sizeof(T) == 4) G = cconj(green_near32(pk, pd.leaf_off[i], pd.leaf_lo[i], (float)pd.kappa));
-                    else G = cconj(green_r<T>(pd.kappa, dist<T>(pd.xs[i] - x, pd.ys[i] - y, pd.zs[i] - z)));
+                    else {
+                        const double dx = pd.xs[i] - x, dy = pd.ys[i] - y, dz = pd.zs[i] - z;
+                        G = cconj(green_r2_64(pd.kappa, dx * dx + dy * dy + dz * dz));
+                    }
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (R == 1 || r0 + r < nrhs) {
