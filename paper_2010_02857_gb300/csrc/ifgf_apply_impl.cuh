@@ -11,15 +11,17 @@
 //   k_upward  F_j^{d-1} at the parent cones' interpolation points from the children's
 //             interpolants, re-centred by G(x, x_k^d) / G(x, x_j^{d-1}): one thread
 //             per (parent cone, point), looping over the children.
-//   k_eval    per target: level-D direct sums over neighbouring boxes (skipping the
-//             self term) plus, for d = D..3, interpolation from every cousin box's
-//             cone times G(x, x_k^d).
+//   k_near_staged  per leaf box (one block): level-D direct sums over the neighbouring
+//             boxes (skipping the self term), the sources staged through shared
+//             memory with cp.async; also the adjoint's conjugated sums.
+//   k_eval    per target: for d = D..3, interpolation from every cousin box's cone
+//             times G(x, x_k^d), added to the near field.
 // Adjoint (w = A^H v), same data, transposed:
 //   k_adj_level  per relevant cone slot of level d (one warp per slot): conjugated
 //             contributions of the cousin targets that read the slot and of the
-//             parent interpolation points that read it (lists built at plan time).
-//   k_adj_eval   per source: conjugated direct sums plus conj(g) of its leaf's cone
-//             values.
+//             parent interpolation points that read it (transpose lists).
+//   k_adj_eval   per source: conj(g) of its leaf's cone values, added to the
+//             conjugated near field.
 #pragma once
 
 #include "ifgf_device.cuh"
@@ -442,6 +444,170 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
 // ---------------------------------------------------------------------------------
 // Targets: near field + interpolation from every cousin box of every level
 // ---------------------------------------------------------------------------------
+// Near field (Algorithm 1's direct evaluations at level D) with the sources staged
+// through shared memory.  A block holds one work item of the plan's near tile list: up to
+// kNearTargets consecutive targets of one leaf box.  The sources of the box's neighbours
+// (at most 27 ranges, each contiguous in Morton order) form one list of ns entries, which
+// the block copies in tiles of kNearTile into shared memory: FP64 plans copy positions
+// and densities with cp.async; float plans convert each source once to its offset from
+// the box centre split into FP32 high and low parts (see Rel32), so that the difference
+// of two close points loses nothing.  The 128 threads form q = 128 / nt groups over the
+// nt targets: group g sums, for each target, the tile entries g, g + q, ...  Small leaf
+// boxes (a few points, the common case) therefore keep every lane busy, and a large box
+// spreads over several blocks.  The groups' partial sums are added in group order.  The
+// self term is skipped by index; conj = 1 gives the adjoint's conjugated sums.  The order
+// of every sum is fixed by the plan, so results repeat bitwise.
+constexpr int kNearTile = 128;
+constexpr int kNearThreads = 128;
+static_assert(kNearThreads >= kNearTargets, "every target of a work item needs a thread");
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nrhs, const void *in, void *out,
+                                                              int conj)
+{
+    // positions: FP64 plans x, y, z [kNearTile] doubles; float plans the split offsets
+    // (high, low) [kNearTile] float4 each
+    __shared__ __align__(16) unsigned char spos[kNearTile * 32];
+    __shared__ __align__(16) cpx<T> ssig[kNearTile * R];
+    __shared__ __align__(16) cpx<T> spart[kNearThreads * R];
+    __shared__ int sidx[kNearTile];
+    __shared__ int sbeg[27], spre[28];
+    double *sx = (double *)spos, *sy = sx + kNearTile, *sz = sy + kNearTile;
+    float4 *soh = (float4 *)spos, *sol = soh + kNearTile;
+    const LevelDev &LD = pd.lev[pd.D];
+    const int tid = threadIdx.x;
+    const int2 item = pd.near_tile[blockIdx.x];
+    const int b = item.x, t0 = item.y;
+    const int nt = min(kNearTargets, LD.start[b + 1] - t0);  // 1 .. kNearTargets
+    if (tid < 32) {
+        // neighbour ranges and their exclusive prefix (neighbour lists end at the first -1)
+        int cnt = 0, beg = 0;
+        if (tid < 27) {
+            const int k = LD.nbr[27 * (size_t)b + tid];
+            if (k >= 0) {
+                beg = LD.start[k];
+                cnt = LD.start[k + 1] - beg;
+            }
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (tid >= o) inc += v;
+        }
+        if (tid < 27) {
+            sbeg[tid] = beg;
+            spre[tid + 1] = inc;
+        }
+        if (tid == 0) spre[0] = 0;
+    }
+    __syncthreads();
+    const int ns = spre[27];
+    const int q = kNearThreads / nt;
+    const int tt = tid % nt, grp = tid / nt;
+    const bool tv = grp < q;
+    const int i = t0 + tt;
+    const double *cb = LD.center + 3 * (size_t)b;
+    const float kf = (float)pd.kappa;
+    double x = 0, y = 0, z = 0;
+    if (tv) {
+        x = pd.xs[i];
+        y = pd.ys[i];
+        z = pd.zs[i];
+    }
+    Rel32 pt;
+    if constexpr (sizeof(T) == 4) pt = rel32(x, y, z, cb);
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        const int rv = min(R, nrhs - r0);
+        cpx<T> acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
+        for (int g0 = 0; g0 < ns; g0 += kNearTile) {
+            const int cnt = min(kNearTile, ns - g0);
+            for (int s = tid; s < cnt; s += kNearThreads) {
+                const int g = g0 + s;
+                int e = 0;  // the neighbour range holding g: spre[e] <= g < spre[e + 1]
+#pragma unroll
+                for (int w = 16; w >= 1; w >>= 1)
+                    if (e + w < 28 && spre[e + w] <= g) e += w;
+                const int j = sbeg[e] + (g - spre[e]);
+                sidx[s] = j;
+                if constexpr (sizeof(T) == 8) {
+                    cp_async8(sx + s, pd.xs + j);
+                    cp_async8(sy + s, pd.ys + j);
+                    cp_async8(sz + s, pd.zs + j);
+                } else {
+                    const Rel32 ps = rel32(pd.xs[j], pd.ys[j], pd.zs[j], cb);
+                    soh[s] = make_float4(ps.hx, ps.hy, ps.hz, 0.f);
+                    sol[s] = make_float4(ps.lx, ps.ly, ps.lz, 0.f);
+                }
+                for (int r = 0; r < rv; ++r) {
+                    const cpx<T> *src = (const cpx<T> *)in + (size_t)j * nrhs + r0 + r;
+                    if constexpr (sizeof(T) == 8) cp_async16(ssig + s * R + r, src);
+                    else cp_async8(ssig + s * R + r, src);
+                }
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            if (tv) {
+                for (int s = grp; s < cnt; s += q) {
+                    if (sidx[s] == i) continue;
+                    cpx<T> G;
+                    if constexpr (sizeof(T) == 8) {
+                        const double dx = x - sx[s], dy = y - sy[s], dz = z - sz[s];
+                        G = green_r2_64(pd.kappa, dx * dx + dy * dy + dz * dz);
+                    } else {
+                        G = green_near32(pt, soh[s], sol[s], kf);
+                    }
+                    if (conj) G = cconj(G);
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r < rv) {
+                            const cpx<T> m = cmul(G, ssig[s * R + r]);
+                            acc[r].x += m.x;
+                            acc[r].y += m.y;
+                        }
+                }
+            }
+            __syncthreads();  // the tile is read before the next copy overwrites it
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) spart[tid * R + r] = acc[r];
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (R == 1 || r < rv) {
+                    cpx<T> v = spart[tt * R + r];
+                    for (int g = 1; g < q; ++g) {
+                        const cpx<T> o = spart[(g * nt + tt) * R + r];
+                        v.x += o.x;
+                        v.y += o.y;
+                    }
+                    st<T>(out, (size_t)i * nrhs + r0 + r, v);
+                }
+        }
+        __syncthreads();  // the partial sums are read before the next chunk writes them
+    }
+}
+
 template <typename T, int R, int PS, int PA>
 __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *sig, void *us, int mode, int d_hi,
                                               int d_lo, int accumulate)
@@ -455,31 +621,6 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
         cpx<T> acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
-        if (mode & 1) {
-            int b = LD.pt_box[i];
-            for (int e = 0; e < 27; ++e) {
-                int k = LD.nbr[27 * (size_t)b + e];
-                if (k < 0) break;
-                Rel32 pk;
-                if constexpr (sizeof(T) == 4) pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
-                for (int j = LD.start[k]; j < LD.start[k + 1]; ++j) {
-                    if (j == i) continue;
-                    cpx<T> G;
-                    if constexpr (sizeof(T) == 4) G = green_near32(pk, pd.leaf_off[j], pd.leaf_lo[j], (float)pd.kappa);
-                    else {
-                        const double dx = x - pd.xs[j], dy = y - pd.ys[j], dz = z - pd.zs[j];
-                        G = green_r2_64(pd.kappa, dx * dx + dy * dy + dz * dz);
-                    }
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (R == 1 || r0 + r < nrhs) {
-                            cpx<T> m = cmul(G, ld<T>(sig, (size_t)j * nrhs + r0 + r));
-                            acc[r].x += m.x;
-                            acc[r].y += m.y;
-                        }
-                }
-            }
-        }
         if (mode & 2) {
             for (int d = d_hi; d >= d_lo; --d) {
                 const LevelDev &L = pd.lev[d];
@@ -680,9 +821,11 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
     }
 }
 
-// Adjoint per source: conjugated neighbour sums + conj(g(q, x')) times the leaf cones' adjoint values.
+// Adjoint per source: conj(g(q, x')) times the leaf cones' adjoint values, stored or added
+// to the conjugated near field (accumulate).
 template <typename T, int R, int PS, int PA>
-__global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const void *vs, void *ws, int mode)
+__global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const void *vs, void *ws, int mode,
+                                                  int accumulate)
 {
     constexpr int P = PS * PA * PA;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,30 +837,6 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
         cpx<T> acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
-        if (mode & 1) {
-            for (int e = 0; e < 27; ++e) {
-                int k = LD.nbr[27 * (size_t)b + e];
-                if (k < 0) break;
-                Rel32 pk;
-                if constexpr (sizeof(T) == 4) pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
-                for (int i = LD.start[k]; i < LD.start[k + 1]; ++i) {
-                    if (i == j) continue;
-                    cpx<T> G;
-                    if constexpr (sizeof(T) == 4) G = cconj(green_near32(pk, pd.leaf_off[i], pd.leaf_lo[i], (float)pd.kappa));
-                    else {
-                        const double dx = pd.xs[i] - x, dy = pd.ys[i] - y, dz = pd.zs[i] - z;
-                        G = cconj(green_r2_64(pd.kappa, dx * dx + dy * dy + dz * dz));
-                    }
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (R == 1 || r0 + r < nrhs) {
-                            cpx<T> m = cmul(G, ld<T>(vs, (size_t)i * nrhs + r0 + r));
-                            acc[r].x += m.x;
-                            acc[r].y += m.y;
-                        }
-                }
-            }
-        }
         if (mode & 2) {
             const double *c = LD.center + 3 * (size_t)b;
             for (int slot = LD.act_start[b]; slot < LD.act_start[b + 1]; ++slot) {
@@ -738,7 +857,15 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (R == 1 || r0 + r < nrhs) st<T>(ws, (size_t)j * nrhs + r0 + r, acc[r]);
+            if (R == 1 || r0 + r < nrhs) {
+                cpx<T> v = acc[r];
+                if (accumulate) {
+                    const cpx<T> old = ld<T>(ws, (size_t)j * nrhs + r0 + r);
+                    v.x += old.x;
+                    v.y += old.y;
+                }
+                st<T>(ws, (size_t)j * nrhs + r0 + r, v);
+            }
     }
 }
 
@@ -773,15 +900,22 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
             tm.mark(STAGE_UPWARD, nl, st);
         }
         {
-            NvtxRange range("near and targets");
-            k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode, pd.D, 3, 0);
+            NvtxRange range("near field and targets");
+            if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, sig, us, 0);
+            if (mode & 2)
+                k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, 2, pd.D, 3, mode & 1);
         }
-        tm.mark(STAGE_EVAL, 1, st);
+        tm.mark(STAGE_EVAL, 1 + ((mode & 3) == 3), st);
         return cudaGetLastError();
     }
     // two alternating level buffers: each level's targets are evaluated before the
     // upward step overwrites the buffer of level d-1's parent
-    k_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, sig, us, mode & 1, pd.D, 3, 0);
+    if (mode & 1) {
+        NvtxRange range("near field");
+        k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, sig, us, 0);
+    } else {
+        cudaMemsetAsync(us, 0, (size_t)pd.n * nrhs * sizeof(cpx<T>), st);
+    }
     tm.mark(STAGE_EVAL, 1, st);
     if (mode & 2) {
         const LevelDev &L = pd.lev[pd.D];
@@ -823,8 +957,9 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
         }
         tm.mark(STAGE_ADJ_LEVEL, nl, st);
     }
-    k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, mode);
-    tm.mark(STAGE_ADJ_EVAL, 1, st);
+    if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
+    if (mode & 2) k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1);
+    tm.mark(STAGE_ADJ_EVAL, 1 + ((mode & 3) == 3), st);
     return cudaGetLastError();
 }
 
@@ -874,7 +1009,8 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
     ifgf_jit_release(&tl);
     ifgf_jit_release(&ul);
     if (s != IFGF_OK) return s;
-    k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, mode);
+    if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
+    if (mode & 2) k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1);
     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint launch"; return IFGF_ECUDA; }
     return IFGF_OK;
 }

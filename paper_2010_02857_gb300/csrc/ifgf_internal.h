@@ -94,6 +94,8 @@ struct LevelDev {
     const void *ucache = nullptr;
 };
 
+constexpr int kNearTargets = 32;  // targets per near-field block
+
 struct PlanDev {
     int n = 0, D = 0, Ps = 0, Pang = 0, P = 0;
     int pingpong = 0;   // level buffers alternate: target evaluation runs level by level
@@ -106,6 +108,10 @@ struct PlanDev {
     const float4 *leaf_off = nullptr;  // [N] x_j - centre of its leaf box, and its squared norm (FP32)
     const float4 *leaf_lo = nullptr;   // [N] the rounding remainder of that offset (x, y, z), FP32
     const int *perm = nullptr;
+    // near-field work items: (leaf box, first target) for each run of at most
+    // kNearTargets consecutive targets of a level-D box
+    const int2 *near_tile = nullptr;
+    int n_near_tile = 0;
     int *err = nullptr;                                  // device invariant-failure counter
     int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel
     int flags = 0;         // the plan's option flags (test switches read by kernels)

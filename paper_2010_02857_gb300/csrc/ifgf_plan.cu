@@ -164,6 +164,22 @@ __global__ void k_leaf_offsets(PlanDev pd, float4 *off, float4 *lo)
     lo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
 }
 
+// Near-field work items: the targets of each leaf box in runs of kNearTargets.
+__global__ void k_near_tile_count(const int *start, int nbox, int *cnt)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbox) return;
+    cnt[b] = b < nbox ? (start[b + 1] - start[b] + kNearTargets - 1) / kNearTargets : 0;
+}
+
+__global__ void k_near_tile_emit(const int *start, int nbox, const int *tstart, int2 *tile)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    for (int t = tstart[b]; t < tstart[b + 1]; ++t)
+        tile[t] = make_int2(b, start[b] + (t - tstart[b]) * kNearTargets);
+}
+
 // Points must be pairwise distinct (Eq. field1 sums over m != l; the method's
 // factorisation divides by |x_l - x_m|).  Equal points share their Morton key and hence
 // their leaf box, so each point is compared with the later points of its leaf.
@@ -764,6 +780,22 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaGetLastError());
         pd.leaf_off = off;
         pd.leaf_lo = lo;
+    }
+    {
+        const LevelDev &L = pd.lev[D];
+        Scratch cnt, tstart;
+        if (!cnt.alloc((size_t)(L.nbox + 1) * 4) || !tstart.alloc((size_t)(L.nbox + 1) * 4)) return IFGF_ENOMEM;
+        k_near_tile_count<<<nblocks(L.nbox + 1), kThreads, 0, st>>>(L.start, L.nbox, (int *)cnt.ptr);
+        CK(cudaGetLastError());
+        ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)tstart.ptr, L.nbox + 1, st);
+        if (s != IFGF_OK) return s;
+        int ntile = 0;
+        CK(cudaMemcpy(&ntile, (int *)tstart.ptr + L.nbox, sizeof(int), cudaMemcpyDeviceToHost));
+        DALLOC(tile, int2, ntile);
+        k_near_tile_emit<<<nblocks(L.nbox), kThreads, 0, st>>>(L.start, L.nbox, (int *)tstart.ptr, tile);
+        CK(cudaGetLastError());
+        pd.near_tile = tile;
+        pd.n_near_tile = ntile;
     }
     // cousins of levels 3..D
     for (int d = 3; d <= D; ++d) {

@@ -107,6 +107,29 @@ def test_fp64_apply_matches_oracle_and_direct(pkg, torch_cuda, case):
     assert g.check() == 0
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_order_4_7_matches_oracle(pkg, torch_cuda, precision, tol):
+    # (P_s, P_ang) = (4, 7): 196 interpolation points per cone, 18 Lagrange weights
+    torch = torch_cuda
+    wl, pts, sigma = _make((3000, 3, 4, 2, 4))
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 4, 4, 7, 2, 4, precision=precision)
+    o = oracle.Plan(pts, wl.kappa, 4, 4, 7, 2, 4)
+    s = torch.from_numpy(sigma).cuda()
+    if precision == "fp64":
+        o.apply(sigma, mode=2)
+        g.apply_partial(s, 2)
+        for d in range(3, 5):
+            assert maxrel(g.values(d), o.F(d)) < tol, d
+    u = g.apply(s).cpu().numpy()
+    uo = o.apply(sigma)
+    assert rel(u, uo) < tol
+    assert rel(u, oracle.direct(pts, wl.kappa, sigma)) < 1e-3
+    v = wi.complex_normal(33, (1, wl.n))
+    w = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert rel(w, o.apply_adjoint(v)) < tol
+    assert g.check() == 0
+
+
 @pytest.mark.parametrize("case", CASES[:3])
 def test_fp64_adjoint_matches_oracle(pkg, torch_cuda, case):
     torch = torch_cuda
