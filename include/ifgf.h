@@ -246,6 +246,23 @@ ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors);
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on);
 
 /*
+ * CUDA-graph replay of evaluations.  With on != 0, the launches of an evaluation
+ * (ifgf_apply, ifgf_apply_adjoint, ifgf_apply_partial) are captured into a CUDA graph
+ * the first time the plan evaluates with a given input buffer, output buffer, nrhs,
+ * mode and direction, and that graph is replayed on the caller's stream by later such
+ * calls (host-pointer calls use the plan's own device staging buffers, so they share
+ * one graph per nrhs, mode and direction).  A replay runs the same kernels in the same
+ * order as the plain launches, so the results are the same.  The graph keeps the
+ * buffer addresses, not their contents.  At most 8 graphs are kept (the least recently
+ * used is dropped); on = 0 frees them.  With profiling on (ifgf_plan_set_profiling),
+ * separate graphs are captured that record the stage events themselves, so per-stage
+ * times stay available.  Graphs are not used for the adjoint of two-buffer plans, whose
+ * transpose lists are built between launches.  Off by default.  Errors: IFGF_EINVAL
+ * for a NULL plan; a capture that fails makes the evaluation return IFGF_ECUDA.
+ */
+ifgf_status ifgf_plan_set_graphs(ifgf_plan *plan, int on);
+
+/*
  * Totals since profiling was turned on: ms[s] milliseconds and launches[s] kernel
  * launches of stage s, calls = profiled calls; count >= 7.  Stages: 0 density
  * permutation, 1 leaf analytic factors, 2 upward interpolation (all levels),

@@ -36,7 +36,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_p
            "ifgf_plan_destroy", "ifgf_plan_level_info", "ifgf_plan_get_perm", "ifgf_plan_get_boxes",
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
            "ifgf_plan_geometry",
-           "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_timings",
+           "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_timings",
            "ifgf_last_error"]
 STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
 
@@ -81,6 +81,7 @@ def lib():
         L.ifgf_plan_stats.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
         L.ifgf_plan_check.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
         L.ifgf_plan_set_profiling.argtypes = [P, i]
+        L.ifgf_plan_set_graphs.argtypes = [P, i]
         L.ifgf_plan_timings.argtypes = [P, P, P, P, i]
         L.ifgf_last_error.argtypes = [P]
         L.ifgf_last_error.restype = ctypes.c_char_p
@@ -301,6 +302,10 @@ class Plan:
 
     def set_profiling(self, on: bool):
         _check(lib().ifgf_plan_set_profiling(self.handle, int(bool(on))), self.handle)
+
+    def set_graphs(self, on: bool):
+        """Capture each evaluation into a CUDA graph on first use and replay it after."""
+        _check(lib().ifgf_plan_set_graphs(self.handle, int(bool(on))), self.handle)
 
     def timings(self) -> dict:
         ms = np.zeros(len(STAGES))

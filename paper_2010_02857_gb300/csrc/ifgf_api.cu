@@ -20,6 +20,7 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
 
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
+cudaError_t ifgf_batched_prepare();
 
 static thread_local std::string g_create_error;
 
@@ -33,8 +34,18 @@ static bool is_device_pointer(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Drops the plan's captured evaluations (their kernels hold a copy of the plan's device
+// description, which is stale once it changes).
+static void graphs_clear(ifgf_plan *p)
+{
+    for (auto &g : p->graphs) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+}
+
 static void free_plan(ifgf_plan *p)
 {
+    graphs_clear(p);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     for (int i = 0; i < StageTimer::kMax; ++i)
         if (p->timer.ev[i]) cudaEventDestroy(p->timer.ev[i]);
     for (void *ptr : p->allocs) cudaFree(ptr);
@@ -139,6 +150,11 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     ifgf_status s = ifgf_build_plan(p, points, st);
     // batched plans group evaluations by source cone with the transpose lists
     if (s == IFGF_OK && ((o.flags & 1) || o.precision == IFGF_BATCHED_BF16)) s = ifgf_build_adjoint_lists(p, st);
+    if (s == IFGF_OK && o.precision == IFGF_BATCHED_BF16 && ifgf_batched_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        p->last_error = "shared-memory limit of the tensor-core kernel";
+        s = IFGF_ECUDA;
+    }
     if (s != IFGF_OK) {
         g_create_error = p->last_error;
         cudaStreamSynchronize(st);
@@ -191,6 +207,99 @@ static ifgf_status wait_stream(ifgf_plan *p, cudaStream_t st)
     return s;
 }
 
+// Queues the launches of one evaluation on st (device buffers in the caller's order):
+// right-hand sides in chunks of at most rhs_chunk, a chunk being a contiguous block of
+// rows of the [nrhs][N] arrays.  Launches only: no host synchronisation, so that the
+// sequence can be captured into a CUDA graph.
+static cudaError_t launch_evaluation(ifgf_plan *p, const void *din, void *dout, int nrhs, int mode, int adjoint,
+                                     cudaStream_t st)
+{
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    cudaError_t e = cudaSuccess;
+    for (int c0 = 0; c0 < nrhs && e == cudaSuccess; c0 += p->rhs_chunk) {
+        const int nc = std::min(p->rhs_chunk, nrhs - c0);
+        const void *cin = (const char *)din + (size_t)c0 * p->n * eb;
+        void *cout = (char *)dout + (size_t)c0 * p->n * eb;
+        if (p->precision == IFGF_FP64)
+            e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+        else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nc % 2 == 0 && nc <= 64)
+            e = ifgf_run_batched(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
+        else
+            e = ifgf_run_typed_f32(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+    }
+    return e;
+}
+
+// Replays the captured graph of this evaluation on st, capturing it first if needed (on
+// the plan's own capture stream: capture does not run anything, and the caller's stream
+// may be the legacy default stream, which cannot be captured).  At most kMaxGraphs are
+// kept; the least recently used is dropped.
+static ifgf_status replay_graph(ifgf_plan *p, const void *din, void *dout, int nrhs, int mode, int adjoint,
+                                cudaStream_t st)
+{
+    const bool timed = p->timer.on;
+    ifgf_plan::GraphEntry *g = nullptr;
+    for (auto &x : p->graphs)
+        if (x.in == din && x.out == dout && x.nrhs == nrhs && x.mode == mode && x.adjoint == adjoint &&
+            x.timed == timed)
+            g = &x;
+    if (!g) {
+        if (!p->capture_stream && cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            p->last_error = "capture stream creation failed";
+            return IFGF_ECUDA;
+        }
+        if (cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            p->last_error = "graph capture could not start";
+            return IFGF_ECUDA;
+        }
+        p->timer.n = 0;
+        p->timer.external = true;
+        const cudaError_t le = launch_evaluation(p, din, dout, nrhs, mode, adjoint, p->capture_stream);
+        p->timer.external = false;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(p->capture_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie =
+            (le == cudaSuccess && ce == cudaSuccess) ? cudaGraphInstantiate(&exec, graph, 0) : cudaErrorUnknown;
+        if (graph) cudaGraphDestroy(graph);
+        if (le != cudaSuccess || ce != cudaSuccess || ie != cudaSuccess) {
+            cudaGetLastError();
+            p->last_error = std::string("graph capture failed: ") +
+                            cudaGetErrorString(le != cudaSuccess ? le : ce != cudaSuccess ? ce : ie);
+            return IFGF_ECUDA;
+        }
+        if ((int)p->graphs.size() >= ifgf_plan::kMaxGraphs) {
+            size_t lru = 0;
+            for (size_t i = 1; i < p->graphs.size(); ++i)
+                if (p->graphs[i].used < p->graphs[lru].used) lru = i;
+            cudaGraphExecDestroy(p->graphs[lru].exec);
+            p->graphs.erase(p->graphs.begin() + lru);
+        }
+        ifgf_plan::GraphEntry ne{din, dout, nrhs, mode, adjoint, timed, exec, 0, p->timer.n, {}, {}};
+        ne.tstage.assign(p->timer.stage, p->timer.stage + p->timer.n);
+        ne.tlaunch.assign(p->timer.launches, p->timer.launches + p->timer.n);
+        p->graphs.push_back(std::move(ne));
+        g = &p->graphs.back();
+        ++p->graph_captures;
+    }
+    g->used = ++p->graph_clock;
+    // the marks this replay records, for the caller's attribution of stage times
+    p->timer.n = g->tn;
+    for (int i = 0; i < g->tn; ++i) {
+        p->timer.stage[i] = g->tstage[i];
+        p->timer.launches[i] = g->tlaunch[i];
+    }
+    if (cudaGraphLaunch(g->exec, st) != cudaSuccess) {
+        cudaGetLastError();
+        p->last_error = "graph launch failed";
+        return IFGF_ECUDA;
+    }
+    ++p->graph_replays;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, int mode, int adjoint,
                            cudaStream_t st)
 {
@@ -232,31 +341,31 @@ ifgf_status ifgf_run_apply(ifgf_plan *p, const void *in, void *out, int nrhs, in
         // first adjoint call: build the transpose lists (synchronises the stream)
         ifgf_status s = ifgf_build_adjoint_lists(p, st);
         if (s != IFGF_OK) return s;
+        graphs_clear(p);
     }
     if (adjoint && !p->adjoint_values_ready) {
         ifgf_status s = ifgf_alloc_adjoint_values(p);
         if (s != IFGF_OK) return s;
+        graphs_clear(p);
     }
     p->timer.n = 0;
     cudaError_t e = cudaSuccess;
-    // right-hand sides in chunks of at most rhs_chunk: a chunk is a contiguous block
-    // of rows of the caller's [nrhs][N] arrays
-    for (int c0 = 0; c0 < nrhs && e == cudaSuccess; c0 += p->rhs_chunk) {
-        const int nc = std::min(p->rhs_chunk, nrhs - c0);
-        const void *cin = (const char *)din + (size_t)c0 * p->n * eb;
-        void *cout = (char *)dout + (size_t)c0 * p->n * eb;
-        if (jit) {
+    if (jit) {
+        // right-hand sides in chunks of at most rhs_chunk (contiguous rows of the
+        // caller's [nrhs][N] arrays); the lists are built and freed between launches
+        for (int c0 = 0; c0 < nrhs; c0 += p->rhs_chunk) {
+            const int nc = std::min(p->rhs_chunk, nrhs - c0);
+            const void *cin = (const char *)din + (size_t)c0 * p->n * eb;
+            void *cout = (char *)dout + (size_t)c0 * p->n * eb;
             ifgf_status s = p->precision == IFGF_FP64 ? ifgf_run_adjoint_jit_f64(p, nc, cin, cout, mode, st)
                                                       : ifgf_run_adjoint_jit_f32(p, nc, cin, cout, mode, st);
             if (s != IFGF_OK) return s;
-            continue;
         }
-        if (p->precision == IFGF_FP64)
-            e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
-        else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nc % 2 == 0 && nc <= 64)
-            e = ifgf_run_batched(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
-        else
-            e = ifgf_run_typed_f32(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
+    } else if (p->use_graphs) {
+        ifgf_status s = replay_graph(p, din, dout, nrhs, mode, adjoint, st);
+        if (s != IFGF_OK) return s;
+    } else {
+        e = launch_evaluation(p, din, dout, nrhs, mode, adjoint, st);
     }
     if (e != cudaSuccess) {
         p->last_error = std::string("kernel launch failed: ") + cudaGetErrorString(e);
@@ -413,10 +522,12 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
     snprintf(tmp, sizeof tmp,
              "\"n\": %lld, \"levels\": %d, \"P\": %d, \"kappa\": %.17g, \"precision\": %d, \"max_nrhs\": %d, "
              "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, "
-             "\"pingpong\": %d, \"rhs_chunk\": %d, \"cache_bytes\": %zu, \"level\": [",
+             "\"pingpong\": %d, \"rhs_chunk\": %d, \"cache_bytes\": %zu, \"graphs\": %d, "
+             "\"graph_captures\": %lld, \"graph_replays\": %lld, \"level\": [",
              (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
              (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes,
-             plan->pingpong ? 1 : 0, plan->rhs_chunk, plan->cache_bytes);
+             plan->pingpong ? 1 : 0, plan->rhs_chunk, plan->cache_bytes, (int)plan->graphs.size(),
+             (long long)plan->graph_captures, (long long)plan->graph_replays);
     s += tmp;
     for (int d = 1; d <= plan->D; ++d) {
         const LevelHost &h = plan->lh[d];
@@ -503,6 +614,14 @@ extern "C" ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on)
         plan->stage_launches[s] = 0;
     }
     plan->stage_calls = 0;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_set_graphs(ifgf_plan *plan, int on)
+{
+    if (!plan) return IFGF_EINVAL;
+    plan->use_graphs = on != 0;
+    if (!on) graphs_clear(plan);
     return IFGF_OK;
 }
 

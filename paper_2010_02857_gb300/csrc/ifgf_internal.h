@@ -131,10 +131,12 @@ struct StageTimer {
     cudaEvent_t ev[kMax] = {};
     int stage[kMax] = {};
     int launches[kMax] = {};
+    bool external = false;  // capturing a CUDA graph: the records become event-record nodes
     void mark(int s, int nlaunch, cudaStream_t st)
     {
         if (!on || n >= kMax) return;
-        cudaEventRecord(ev[n], st);
+        if (external) cudaEventRecordWithFlags(ev[n], st, cudaEventRecordExternal);
+        else cudaEventRecord(ev[n], st);
         stage[n] = s;
         launches[n] = nlaunch;
         ++n;
@@ -198,6 +200,27 @@ struct ifgf_plan {
     double stage_ms[STAGE_COUNT] = {};
     int64_t stage_launches[STAGE_COUNT] = {};
     int64_t stage_calls = 0;
+    // CUDA graphs of evaluations (ifgf_plan_set_graphs): the launches of one evaluation
+    // for fixed device buffers, right-hand-side count, mode and direction, captured on
+    // capture_stream at the first such call and replayed on the caller's stream after.
+    // A graph captured with profiling on records the stage timer's events itself; it
+    // keeps the stage and launch count of each mark for the attribution after a replay.
+    struct GraphEntry {
+        const void *in;
+        void *out;
+        int nrhs, mode, adjoint;
+        bool timed;
+        cudaGraphExec_t exec;
+        uint64_t used;
+        int tn;
+        std::vector<int> tstage, tlaunch;
+    };
+    static constexpr int kMaxGraphs = 8;
+    bool use_graphs = false;
+    std::vector<GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
+    uint64_t graph_clock = 0;
+    int64_t graph_captures = 0, graph_replays = 0;
 };
 
 // complex element size of the plan's data type

@@ -334,6 +334,69 @@ def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     assert np.array_equal(g.apply_adjoint(sigma), w1)
 
 
+@pytest.mark.parametrize("precision,nrhs,flags", [("fp64", 1, 0), ("mixed", 3, 0), ("batched", 4, 0),
+                                                   ("fp64", 2, 8 | 16)])
+def test_graph_replay_matches_plain_launches(pkg, torch_cuda, precision, nrhs, flags):
+    # a captured evaluation replays the same kernels in the same order: bitwise equal
+    # results on the deterministic paths, and new buffer contents are picked up
+    torch = torch_cuda
+    wl, pts, _ = _make((3000, 4, 5, 1, 2))
+    sig = wi.complex_normal(90 + nrhs, (2, nrhs, wl.n))
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision=precision,
+                 flags=flags)
+    s = torch.from_numpy(sig[0]).cuda().to(g.complex_dtype)
+    plain = [g.apply(s).cpu().numpy(), g.apply_adjoint(s).cpu().numpy()]
+    s2 = torch.from_numpy(sig[1]).cuda().to(g.complex_dtype)
+    plain2 = g.apply(s2).cpu().numpy()
+    g.set_graphs(True)
+    u = torch.empty_like(s)
+    w = torch.empty_like(s)
+    got = []
+    for _ in range(3):
+        g.apply(s, out=u)
+        g.apply_adjoint(s, out=w)
+        got.append((u.cpu().numpy(), w.cpu().numpy()))
+    s.copy_(s2)
+    g.apply(s, out=u)
+    got2 = u.cpu().numpy()
+    # host buffers go through the plan's staging buffers: one more graph
+    uh = g.apply(sig[1].astype(g.numpy_dtype))
+    st = g.stats()
+    pingpong_adjoint = bool(flags & 8)   # adjoint lists built between launches: not captured
+    assert st["graph_captures"] == (2 if pingpong_adjoint else 3)
+    assert st["graph_replays"] == (5 if pingpong_adjoint else 8)
+    exact = precision != "batched"
+    for uu, ww in got:
+        if exact:
+            assert np.array_equal(uu, plain[0])
+            assert np.array_equal(ww, plain[1])
+        else:
+            assert rel(uu, plain[0]) < 1e-5
+            assert rel(ww, plain[1]) < 1e-5
+    if exact:
+        assert np.array_equal(got2, plain2)
+        assert np.array_equal(uh, plain2)
+    else:
+        assert rel(got2, plain2) < 1e-5
+        assert rel(uh, plain2) < 1e-5
+    # with profiling on, the graph records the stage events: stage times add up to
+    # the call and the result does not change
+    g.set_profiling(True)
+    for _ in range(2):
+        g.apply(s, out=u)
+    tm = g.timings()
+    g.set_profiling(False)
+    assert tm["calls"] == 2
+    assert sum(v["ms"] for v in tm["stages"].values()) > 0
+    assert tm["stages"]["upward"]["launches"] > 0
+    if exact:
+        assert np.array_equal(u.cpu().numpy(), plain2)
+    assert g.stats()["graph_captures"] == (3 if pingpong_adjoint else 4)
+    g.set_graphs(False)
+    assert g.stats()["graphs"] == 0
+    assert g.check() == 0
+
+
 @pytest.mark.parametrize("case", CASES[:3])
 def test_mixed_precision_matches_fp64_oracle(pkg, torch_cuda, case):
     torch = torch_cuda
