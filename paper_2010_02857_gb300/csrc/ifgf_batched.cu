@@ -615,6 +615,15 @@ static size_t cone_mma_smem(int npad)
     return (size_t)2 * kM * kK * 2 + (size_t)2 * kK * npad * 2 + (size_t)kM * kStageStride;
 }
 
+// Raises k_cone_mma's dynamic shared-memory limit to what 64 right-hand sides (128
+// columns) need.  Called once per batched plan, so that evaluations queue only
+// stream-ordered work (and can be captured into CUDA graphs).
+cudaError_t ifgf_batched_prepare()
+{
+    using namespace ifgf::batched;
+    return cudaFuncSetAttribute(k_cone_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cone_mma_smem(128));
+}
+
 // Forward apply of a batched plan (device pointers to Morton-ordered buffers).
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm)
@@ -638,9 +647,7 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
         const int npad = ((2 * nrhs + 15) / 16) * 16;
         int tcols = 32;
         while (tcols < npad) tcols *= 2;
-        const size_t smem = cone_mma_smem(npad);
-        e = cudaFuncSetAttribute(k_cone_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        const size_t smem = cone_mma_smem(npad);  // within the limit ifgf_batched_prepare set
         int nl = 0;
         for (int d = pd.D; d >= 3; --d) {
             const LevelDev &L = pd.lev[d];
