@@ -25,9 +25,10 @@
 // summation order (and the last bits of the result) varies from run to run on this
 // path.
 //
-// The level-D direct sums (near field) and the leaf analytic factors are computed on
-// CUDA cores by warp-cooperative kernels: lanes own right-hand sides, and each
-// Green-function or analytic-factor value is computed once per pair and broadcast.
+// The level-D direct sums (near field) and the leaf analytic factors run on CUDA cores:
+// the near field by warps whose lanes own right-hand sides, each Green-function value
+// computed once per pair and broadcast; the leaf factors by blocks that stage a chunk
+// of sources' densities and factors in shared memory and contract them from there.
 #include <cuda_bf16.h>
 
 #include "ifgf_apply_impl.cuh"
@@ -540,53 +541,90 @@ __global__ void __launch_bounds__(128) k_near_batched(PlanDev pd, int nrhs, cons
     }
 }
 
-// Leaf analytic factors, one warp per (relevant leaf cone, interpolation point).
-template <int RPL>
-__global__ void __launch_bounds__(128) k_leaf_batched(PlanDev pd, int nrhs, const float2 *sig)
+// Leaf analytic factors (Eq. factored_f at the interpolation points of every relevant
+// leaf cone, summed over the sources of the cone's box), one block per relevant leaf
+// cone.  Per chunk of kLeafKT sources of the box, the densities [kLeafKT][nrhs] are
+// copied into shared memory with cp.async and the factors g(q_n, x_j) of the 75 nodes
+// are computed once into shared memory (FP32, from the node's FP32 constants and the
+// source's stored offset).  The contraction F[n][r] = sum_j g(q_n, x_j) sigma_j[r] then
+// runs from shared memory: thread (tx, ty) holds nodes ty + 8 i (i < 10) and right-hand
+// sides tx + 16 k (k < RPT) in registers, so that each pair of shared-memory loads feeds
+// 4 RPT x 10 FMAs.  Every output is one thread's sum over the sources in order.
+constexpr int kLeafKT = 32;
+constexpr int kLeafNodeGroups = 8;                             // ty
+constexpr int kLeafNodesPerThread = (kP + kLeafNodeGroups - 1) / kLeafNodeGroups;  // 10
+
+template <int RPT>
+__global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const float2 *sig)
 {
+    __shared__ float4 snode[kP];                      // R and dir of each node (FP32)
+    __shared__ float4 soff[kLeafKT];                  // the chunk's source offsets (delta, |delta|^2)
+    __shared__ float2 sg[kP][kLeafKT + 1];            // g(q_n, x_j); padded against bank conflicts
+    __shared__ __align__(16) float2 ssig[kLeafKT * 16 * RPT];
     const LevelDev &L = pd.lev[pd.D];
-    const int lane = threadIdx.x & 31;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= (int64_t)L.nact * kP) return;
-    const int slot = (int)(w / kP), node = (int)(w % kP);
+    const int slot = blockIdx.x;
     const int b = L.act_box[slot];
-    const double *c = L.center + 3 * (size_t)b;
-    double q[3], dir[3];
-    const double R0 = node_pos(L, 3, 5, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
-    // the node's FP32 constants, converted once per warp
-    const float Rf = (float)R0, dxf = (float)dir[0], dyf = (float)dir[1], dzf = (float)dir[2];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float kf = (float)pd.kappa;
-    cpx<float> acc[RPL];
+    if (tid < kP) {
+        const double *c = L.center + 3 * (size_t)b;
+        double q[3], dir[3];
+        const double R0 = node_pos(L, 3, 5, L.act_cone[slot], tid, c[0], c[1], c[2], q, dir);
+        snode[tid] = make_float4((float)R0, (float)dir[0], (float)dir[1], (float)dir[2]);
+    }
+    float2 acc[kLeafNodesPerThread][RPT];
 #pragma unroll
-    for (int t = 0; t < RPL; ++t) acc[t] = {0.f, 0.f};
-    const int j1 = L.start[b + 1];
-    for (int j0 = L.start[b]; j0 < j1; j0 += 32) {
-        int j = j0 + lane;
-        float gx = 0.f, gy = 0.f;
-        if (j < j1) {
-            const cpx<float> g = leaf_factor32(Rf, dxf, dyf, dzf, kf, pd.leaf_off[j]);
-            gx = g.x;
-            gy = g.y;
+    for (int i = 0; i < kLeafNodesPerThread; ++i)
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) acc[i][k] = make_float2(0.f, 0.f);
+    const int j0 = L.start[b], j1 = L.start[b + 1];
+    for (int jb = j0; jb < j1; jb += kLeafKT) {
+        const int cnt = min(kLeafKT, j1 - jb);
+        __syncthreads();  // the previous chunk is consumed (and the node constants are written)
+        // nrhs is even: a chunk's rows are cnt * nrhs / 2 aligned 16-byte pieces
+        const int pieces = cnt * nrhs / 2;
+        for (int q = tid; q < pieces; q += blockDim.x) cp_async16(ssig + 2 * q, sig + (size_t)jb * nrhs + 2 * q);
+        if (tid < cnt) soff[tid] = pd.leaf_off[jb + tid];
+        cp_async_wait_all();
+        __syncthreads();
+        for (int e = tid; e < kP * cnt; e += blockDim.x) {
+            const int n = e / cnt, t = e - n * cnt;
+            const float4 nd = snode[n];
+            const cpx<float> g = leaf_factor32(nd.x, nd.y, nd.z, nd.w, kf, soff[t]);
+            sg[n][t] = make_float2(g.x, g.y);
         }
-        int cnt = min(32, j1 - j0);
+        __syncthreads();
         for (int t = 0; t < cnt; ++t) {
-            float ax = __shfl_sync(0xffffffffu, gx, t), ay = __shfl_sync(0xffffffffu, gy, t);
+            float2 s[RPT];
 #pragma unroll
-            for (int u = 0; u < RPL; ++u) {
-                int r = lane + 32 * u;
-                if (r < nrhs) {
-                    float2 s = sig[(size_t)(j0 + t) * nrhs + r];
-                    acc[u].x += ax * s.x - ay * s.y;
-                    acc[u].y += ax * s.y + ay * s.x;
+            for (int k = 0; k < RPT; ++k) {
+                const int r = tx + 16 * k;
+                s[k] = r < nrhs ? ssig[t * nrhs + r] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < kLeafNodesPerThread; ++i) {
+                const int n = ty + kLeafNodeGroups * i;
+                if (n < kP) {
+                    const float2 g = sg[n][t];
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        acc[i][k].x += g.x * s[k].x - g.y * s[k].y;
+                        acc[i][k].y += g.x * s[k].y + g.y * s[k].x;
+                    }
                 }
             }
         }
     }
-    float2 *F = (float2 *)L.F + ((size_t)slot * kP + node) * nrhs;
+    float2 *F = (float2 *)L.F + (size_t)slot * kP * nrhs;
 #pragma unroll
-    for (int u = 0; u < RPL; ++u) {
-        int r = lane + 32 * u;
-        if (r < nrhs) F[r] = make_float2(acc[u].x, acc[u].y);
+    for (int i = 0; i < kLeafNodesPerThread; ++i) {
+        const int n = ty + kLeafNodeGroups * i;
+        if (n >= kP) continue;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = tx + 16 * k;
+            if (r < nrhs) F[(size_t)n * nrhs + r] = acc[i][k];
+        }
     }
 }
 
@@ -595,9 +633,13 @@ cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, flo
                              StageTimer &tm)
 {
     if (mode & 2) {
-        int64_t warps = (int64_t)pd.lev[pd.D].nact * kP;
-        if (warps > 0) k_leaf_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig);
-        tm.mark(STAGE_LEAF, warps > 0, st);
+        const int nact = pd.lev[pd.D].nact;
+        if (nact > 0) {
+            if (nrhs <= 16) k_leaf_tiled<1><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+            else if (nrhs <= 32) k_leaf_tiled<2><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+            else k_leaf_tiled<4><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+        }
+        tm.mark(STAGE_LEAF, nact > 0, st);
     }
     int64_t warps = pd.n;
     k_near_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
