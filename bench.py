@@ -235,6 +235,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # batched plans: the tile shapes come from the autotuner, timed on this plan
+    tiles = None
+    if precision == "batched" and wl.nrhs % 2 == 0 and wl.nrhs <= 64:
+        t0 = time.perf_counter()
+        tiles = plan.autotune(wl.nrhs)
+        tiles["tune_s"] = time.perf_counter() - t0
     # every evaluation below replays a CUDA graph of the apply's launches; the graphs
     # (with and without the stage events) are captured during the warm-up
     plan.set_graphs(True)
@@ -340,7 +346,7 @@ def main():
                            "leaf_cones": [wl.leaf_ns, wl.leaf_nc], "precision": precision,
                            "l2": "flushed between steps (256 MB write)", "launch": "CUDA graph replay",
                            "parallelism": f"replicas x{world}"},
-                "t_plan_ms": t_plan * 1e3,
+                "t_plan_ms": t_plan * 1e3, "tiles": tiles,
                 "stage_ms": {k: v["ms"] / calls for k, v in st.items() if v["launches"]},
                 "e2e": {"value": world * n * n * nrhs / e2e_s, "unit": UNIT,
                         "h2d_bytes_per_step": n * nrhs * eb, "d2h_bytes_per_step": n * nrhs * eb,

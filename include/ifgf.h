@@ -246,6 +246,35 @@ ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors);
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on);
 
 /*
+ * Autotuner of the batched tensor-core path (IFGF_BATCHED_BF16 plans).  On this plan's
+ * relevant cones with nrhs right-hand sides (even, 2..min(64, max_nrhs)) it times:
+ *   - each register-tile shape of the leaf analytic-factor kernel, written as threads
+ *     along the right-hand sides x thread groups along the 75 nodes of a cone:
+ *     0 = 16 x 8 (the default), 1 = 32 x 4, 2 = 8 x 16;
+ *   - each grid of the persistent tensor-core cone kernel: 1 or 2 CTAs per SM (2 is
+ *     the default);
+ * reps runs of each after one warm-up run, and keeps the fastest of each for the
+ * plan's later evaluations.  ms (NULL or [5]) receives the candidates' mean times in
+ * milliseconds in the order above (the 3 leaf shapes, then 1 and 2 CTAs per SM);
+ * choice (NULL or [2]) receives {leaf shape, CTAs per SM}.  The shapes change how the
+ * work is split, not the result (the cone kernel's reductions vary in order from run to
+ * run whatever the shape).  The runs use the plan's own buffers (densities zeroed),
+ * never the caller's; captured CUDA graphs of the plan are dropped.  Synchronises the
+ * stream.  Errors: IFGF_EINVAL for another precision, an odd or out-of-range nrhs or
+ * reps < 1; IFGF_ECUDA for a failed launch.
+ */
+ifgf_status ifgf_plan_autotune(ifgf_plan *plan, int nrhs, int reps, double *ms, int *choice, void *stream);
+
+/*
+ * Sets the batched path's tile shapes directly (for instance to reuse what
+ * ifgf_plan_autotune chose for an earlier plan of the same geometry): leaf_shape in
+ * 0..2 as listed above, cone_ctas_per_sm 1 or 2.  Drops the plan's captured CUDA
+ * graphs.  Plans of other precisions keep the setting and ignore it.  Errors:
+ * IFGF_EINVAL for values out of range.
+ */
+ifgf_status ifgf_plan_set_tiles(ifgf_plan *plan, int leaf_shape, int cone_ctas_per_sm);
+
+/*
  * CUDA-graph replay of evaluations.  With on != 0, the launches of an evaluation
  * (ifgf_apply, ifgf_apply_adjoint, ifgf_apply_partial) are captured into a CUDA graph
  * the first time the plan evaluates with a given input buffer, output buffer, nrhs,

@@ -36,7 +36,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_p
            "ifgf_plan_destroy", "ifgf_plan_level_info", "ifgf_plan_get_perm", "ifgf_plan_get_boxes",
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
            "ifgf_plan_geometry",
-           "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_timings",
+           "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_autotune", "ifgf_plan_set_tiles", "ifgf_plan_timings",
            "ifgf_last_error"]
 STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
 
@@ -82,6 +82,8 @@ def lib():
         L.ifgf_plan_check.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
         L.ifgf_plan_set_profiling.argtypes = [P, i]
         L.ifgf_plan_set_graphs.argtypes = [P, i]
+        L.ifgf_plan_autotune.argtypes = [P, i, i, P, P, P]
+        L.ifgf_plan_set_tiles.argtypes = [P, i, i]
         L.ifgf_plan_timings.argtypes = [P, P, P, P, i]
         L.ifgf_last_error.argtypes = [P]
         L.ifgf_last_error.restype = ctypes.c_char_p
@@ -302,6 +304,19 @@ class Plan:
 
     def set_profiling(self, on: bool):
         _check(lib().ifgf_plan_set_profiling(self.handle, int(bool(on))), self.handle)
+
+    def autotune(self, nrhs: int, reps: int = 3) -> dict:
+        """Time the batched path's tile shapes on this plan and keep the fastest."""
+        ms = np.zeros(5)
+        choice = np.zeros(2, dtype=np.int32)
+        _check(lib().ifgf_plan_autotune(self.handle, int(nrhs), int(reps), _ptr(ms), _ptr(choice), _stream()),
+               self.handle)
+        return {"leaf_shape": ["16x8", "32x4", "8x16"][int(choice[0])], "cone_ctas_per_sm": int(choice[1]),
+                "leaf_ms": [float(x) for x in ms[:3]], "cone_ms": [float(x) for x in ms[3:]]}
+
+    def set_tiles(self, leaf_shape: int, cone_ctas_per_sm: int):
+        """Set the batched path's tile shapes (leaf shape 0..2, 1 or 2 CTAs per SM)."""
+        _check(lib().ifgf_plan_set_tiles(self.handle, int(leaf_shape), int(cone_ctas_per_sm)), self.handle)
 
     def set_graphs(self, on: bool):
         """Capture each evaluation into a CUDA graph on first use and replay it after."""

@@ -21,6 +21,8 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
 cudaError_t ifgf_batched_prepare();
+cudaError_t ifgf_batched_autotune(PlanDev &pd, int nrhs, const void *sig, void *us, cudaStream_t st, int reps,
+                                  float *ms);
 
 static thread_local std::string g_create_error;
 
@@ -523,11 +525,13 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
              "\"n\": %lld, \"levels\": %d, \"P\": %d, \"kappa\": %.17g, \"precision\": %d, \"max_nrhs\": %d, "
              "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, "
              "\"pingpong\": %d, \"rhs_chunk\": %d, \"cache_bytes\": %zu, \"graphs\": %d, "
-             "\"graph_captures\": %lld, \"graph_replays\": %lld, \"level\": [",
+             "\"graph_captures\": %lld, \"graph_replays\": %lld, \"tune_leaf\": %d, \"tune_cone_ctas\": %d, "
+             "\"level\": [",
              (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
              (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes,
              plan->pingpong ? 1 : 0, plan->rhs_chunk, plan->cache_bytes, (int)plan->graphs.size(),
-             (long long)plan->graph_captures, (long long)plan->graph_replays);
+             (long long)plan->graph_captures, (long long)plan->graph_replays, plan->dev.tune_leaf,
+             plan->dev.tune_cone_ctas);
     s += tmp;
     for (int d = 1; d <= plan->D; ++d) {
         const LevelHost &h = plan->lh[d];
@@ -614,6 +618,51 @@ extern "C" ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on)
         plan->stage_launches[s] = 0;
     }
     plan->stage_calls = 0;
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_autotune(ifgf_plan *plan, int nrhs, int reps, double *ms, int *choice,
+                                          void *stream)
+{
+    if (!plan) return IFGF_EINVAL;
+    if (plan->precision != IFGF_BATCHED_BF16 || nrhs < 2 || nrhs > 64 || nrhs % 2 || nrhs > plan->max_nrhs ||
+        reps < 1) {
+        plan->last_error = "autotune: batched plan, even nrhs in [2, min(64, max_nrhs)] and reps >= 1";
+        return IFGF_EINVAL;
+    }
+    NvtxRange range("ifgf_plan_autotune");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(plan->sig_sorted, 0, (size_t)plan->n * nrhs * 8, st) != cudaSuccess) {
+        cudaGetLastError();
+        plan->last_error = "autotune: clearing the density buffer";
+        return IFGF_ECUDA;
+    }
+    float t[5] = {0, 0, 0, 0, 0};
+    const cudaError_t e = ifgf_batched_autotune(plan->dev, nrhs, plan->sig_sorted, plan->u_sorted, st, reps, t);
+    if (e != cudaSuccess) {
+        plan->last_error = std::string("autotune: ") + cudaGetErrorString(e);
+        return IFGF_ECUDA;
+    }
+    graphs_clear(plan);  // captured evaluations hold the previous tile shapes
+    if (ms)
+        for (int i = 0; i < 5; ++i) ms[i] = t[i];
+    if (choice) {
+        choice[0] = plan->dev.tune_leaf;
+        choice[1] = plan->dev.tune_cone_ctas;
+    }
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_set_tiles(ifgf_plan *plan, int leaf_shape, int cone_ctas_per_sm)
+{
+    if (!plan) return IFGF_EINVAL;
+    if (leaf_shape < 0 || leaf_shape > 2 || cone_ctas_per_sm < 1 || cone_ctas_per_sm > 2) {
+        plan->last_error = "tiles: leaf shape in [0, 2], CTAs per SM in [1, 2]";
+        return IFGF_EINVAL;
+    }
+    plan->dev.tune_leaf = leaf_shape;
+    plan->dev.tune_cone_ctas = cone_ctas_per_sm;
+    graphs_clear(plan);
     return IFGF_OK;
 }
 

@@ -547,24 +547,27 @@ __global__ void __launch_bounds__(128) k_near_batched(PlanDev pd, int nrhs, cons
 // copied into shared memory with cp.async and the factors g(q_n, x_j) of the 75 nodes
 // are computed once into shared memory (FP32, from the node's FP32 constants and the
 // source's stored offset).  The contraction F[n][r] = sum_j g(q_n, x_j) sigma_j[r] then
-// runs from shared memory: thread (tx, ty) holds nodes ty + 8 i (i < 10) and right-hand
-// sides tx + 16 k (k < RPT) in registers, so that each pair of shared-memory loads feeds
-// 4 RPT x 10 FMAs.  Every output is one thread's sum over the sources in order.
+// runs from shared memory on register tiles: the 128 threads are TX along the
+// right-hand sides times NG = 128 / TX along the nodes; thread (tx, ty) holds nodes
+// ty + NG i and right-hand sides tx + TX k (k < RPT).  TX is the tile shape the
+// autotuner chooses (8, 16 or 32).  Every output is one thread's sum over the sources
+// in order, so the result does not depend on the shape.
 constexpr int kLeafKT = 32;
-constexpr int kLeafNodeGroups = 8;                             // ty
-constexpr int kLeafNodesPerThread = (kP + kLeafNodeGroups - 1) / kLeafNodeGroups;  // 10
+constexpr int kLeafShapes = 3;  // TX = 16, 32, 8 (launch_leaf)
 
-template <int RPT>
+template <int TX, int RPT>
 __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const float2 *sig)
 {
-    __shared__ float4 snode[kP];                      // R and dir of each node (FP32)
-    __shared__ float4 soff[kLeafKT];                  // the chunk's source offsets (delta, |delta|^2)
-    __shared__ float2 sg[kP][kLeafKT + 1];            // g(q_n, x_j); padded against bank conflicts
-    __shared__ __align__(16) float2 ssig[kLeafKT * 16 * RPT];
+    constexpr int NG = 128 / TX;
+    constexpr int NPT = (kP + NG - 1) / NG;  // nodes per thread
+    __shared__ float4 snode[kP];              // R and dir of each node (FP32)
+    __shared__ float4 soff[kLeafKT];          // the chunk's source offsets (delta, |delta|^2)
+    __shared__ float2 sg[kP][kLeafKT + 1];    // g(q_n, x_j); padded against bank conflicts
+    __shared__ __align__(16) float2 ssig[kLeafKT * TX * RPT];
     const LevelDev &L = pd.lev[pd.D];
     const int slot = blockIdx.x;
     const int b = L.act_box[slot];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const float kf = (float)pd.kappa;
     if (tid < kP) {
         const double *c = L.center + 3 * (size_t)b;
@@ -572,9 +575,9 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
         const double R0 = node_pos(L, 3, 5, L.act_cone[slot], tid, c[0], c[1], c[2], q, dir);
         snode[tid] = make_float4((float)R0, (float)dir[0], (float)dir[1], (float)dir[2]);
     }
-    float2 acc[kLeafNodesPerThread][RPT];
+    float2 acc[NPT][RPT];
 #pragma unroll
-    for (int i = 0; i < kLeafNodesPerThread; ++i)
+    for (int i = 0; i < NPT; ++i)
 #pragma unroll
         for (int k = 0; k < RPT; ++k) acc[i][k] = make_float2(0.f, 0.f);
     const int j0 = L.start[b], j1 = L.start[b + 1];
@@ -598,12 +601,12 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
             float2 s[RPT];
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                const int r = tx + 16 * k;
+                const int r = tx + TX * k;
                 s[k] = r < nrhs ? ssig[t * nrhs + r] : make_float2(0.f, 0.f);
             }
 #pragma unroll
-            for (int i = 0; i < kLeafNodesPerThread; ++i) {
-                const int n = ty + kLeafNodeGroups * i;
+            for (int i = 0; i < NPT; ++i) {
+                const int n = ty + NG * i;
                 if (n < kP) {
                     const float2 g = sg[n][t];
 #pragma unroll
@@ -617,15 +620,42 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
     }
     float2 *F = (float2 *)L.F + (size_t)slot * kP * nrhs;
 #pragma unroll
-    for (int i = 0; i < kLeafNodesPerThread; ++i) {
-        const int n = ty + kLeafNodeGroups * i;
+    for (int i = 0; i < NPT; ++i) {
+        const int n = ty + NG * i;
         if (n >= kP) continue;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            const int r = tx + 16 * k;
+            const int r = tx + TX * k;
             if (r < nrhs) F[(size_t)n * nrhs + r] = acc[i][k];
         }
     }
+}
+
+// right-hand sides per thread: the fewest of 1, 2, 4, 8 with TX * RPT >= nrhs (nrhs <= 64)
+template <int TX>
+void launch_leaf_shape(const PlanDev &pd, int nrhs, const float2 *sig, int nact, cudaStream_t st)
+{
+    const int rpt = (nrhs + TX - 1) / TX;
+    if (rpt <= 1) {
+        k_leaf_tiled<TX, 1><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+    } else if (rpt <= 2) {
+        k_leaf_tiled<TX, 2><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+    } else {
+        if constexpr (TX <= 16) {
+            if (rpt <= 4) k_leaf_tiled<TX, 4><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+            else if constexpr (TX <= 8) k_leaf_tiled<TX, 8><<<nact, 128, 0, st>>>(pd, nrhs, sig);
+        }
+    }
+}
+
+// leaf factors of all relevant leaf cones with tile shape `shape` (an index of kLeafTX)
+inline void launch_leaf(const PlanDev &pd, int nrhs, const float2 *sig, int shape, cudaStream_t st)
+{
+    const int nact = pd.lev[pd.D].nact;
+    if (nact == 0) return;
+    if (shape == 1) launch_leaf_shape<32>(pd, nrhs, sig, nact, st);
+    else if (shape == 2) launch_leaf_shape<8>(pd, nrhs, sig, nact, st);
+    else launch_leaf_shape<16>(pd, nrhs, sig, nact, st);
 }
 
 template <int RPL>
@@ -633,13 +663,8 @@ cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, flo
                              StageTimer &tm)
 {
     if (mode & 2) {
-        const int nact = pd.lev[pd.D].nact;
-        if (nact > 0) {
-            if (nrhs <= 16) k_leaf_tiled<1><<<nact, 128, 0, st>>>(pd, nrhs, sig);
-            else if (nrhs <= 32) k_leaf_tiled<2><<<nact, 128, 0, st>>>(pd, nrhs, sig);
-            else k_leaf_tiled<4><<<nact, 128, 0, st>>>(pd, nrhs, sig);
-        }
-        tm.mark(STAGE_LEAF, nact > 0, st);
+        launch_leaf(pd, nrhs, sig, pd.tune_leaf, st);
+        tm.mark(STAGE_LEAF, pd.lev[pd.D].nact > 0, st);
     }
     int64_t warps = pd.n;
     k_near_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
@@ -666,6 +691,101 @@ cudaError_t ifgf_batched_prepare()
     return cudaFuncSetAttribute(k_cone_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cone_mma_smem(128));
 }
 
+// The tensor-core cone kernels of levels D..3 (targets of every level, parent
+// interpolation points above level 3), ctas persistent CTAs per SM.
+static cudaError_t launch_cones(const PlanDev &pd, int nrhs, float2 *us, int ctas, cudaStream_t st, int *launches)
+{
+    using namespace ifgf;
+    using namespace ifgf::batched;
+    const int npad = ((2 * nrhs + 15) / 16) * 16;
+    int tcols = 32;
+    while (tcols < npad) tcols *= 2;
+    const size_t smem = cone_mma_smem(npad);  // within the limit ifgf_batched_prepare set
+    for (int d = pd.D; d >= 3; --d) {
+        const LevelDev &L = pd.lev[d];
+        if (d > 3) {
+            const LevelDev &Lp = pd.lev[d - 1];
+            const cudaError_t e = cudaMemsetAsync(Lp.F, 0, (size_t)Lp.nact * kP * nrhs * sizeof(float2), st);
+            if (e != cudaSuccess) return e;
+        }
+        if (L.nact == 0) continue;
+        NvtxRange range("tensor-core cones", d);
+        ConeKernelArgs a;
+        a.d = d;
+        a.nrhs = nrhs;
+        a.npad = npad;
+        a.tmem_cols = tcols;
+        a.do_targets = 1;
+        a.do_upward = d > 3;
+        a.u = us;
+        a.work = pd.sched + d;
+        a.skip_mma = (pd.flags & 256) ? 1 : 0;
+        a.wait_limit = a.skip_mma ? (1 << 10) : kWaitLimit;
+        const cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(L.nact, (ctas == 1 ? 1 : 2) * 152);
+        k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
+        ++*launches;
+    }
+    return cudaGetLastError();
+}
+
+// Autotuner of the batched path for nrhs right-hand sides (even, <= 64): times each
+// leaf tile shape and each cone-kernel grid (1 or 2 persistent CTAs per SM) on this
+// plan's relevant cones, over reps runs after one warm-up run, and keeps the fastest
+// of each in pd.  The runs read sig (Morton-ordered densities, [N][nrhs]) and write the
+// plan's cone values and us (scratch).  ms[] receives the mean time of every
+// candidate: leaf shapes 0..2, then cone grids of 1 and 2 CTAs per SM.  Synchronises
+// the stream.
+cudaError_t ifgf_batched_autotune(PlanDev &pd, int nrhs, const void *sig, void *us, cudaStream_t st, int reps,
+                                  float *ms)
+{
+    using namespace ifgf;
+    using namespace ifgf::batched;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cudaGetLastError();
+    }
+    cudaError_t err = cudaSuccess;
+    auto timed = [&](auto &&run) -> float {
+        run();  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r) run();
+        cudaEventRecord(e1, st);
+        float t = 0.f;
+        const cudaError_t s = cudaEventSynchronize(e1);
+        if (s != cudaSuccess || (err = cudaGetLastError()) != cudaSuccess) {
+            if (err == cudaSuccess) err = s;
+            return 0.f;
+        }
+        cudaEventElapsedTime(&t, e0, e1);
+        return t / reps;
+    };
+    int best = 0;
+    for (int s = 0; s < kLeafShapes && err == cudaSuccess; ++s) {
+        ms[s] = timed([&] { launch_leaf(pd, nrhs, (const float2 *)sig, s, st); });
+        if (ms[s] < ms[best]) best = s;
+    }
+    int best_ctas = 2;
+    for (int c = 1; c <= 2 && err == cudaSuccess; ++c) {
+        int nl = 0;
+        ms[kLeafShapes + c - 1] = timed([&] {
+            const cudaError_t le = launch_cones(pd, nrhs, (float2 *)us, c, st, &nl);
+            if (le != cudaSuccess && err == cudaSuccess) err = le;
+        });
+    }
+    if (err == cudaSuccess) {
+        best_ctas = ms[kLeafShapes] < ms[kLeafShapes + 1] ? 1 : 2;
+        pd.tune_leaf = best;
+        pd.tune_cone_ctas = best_ctas;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err;
+}
+
 // Forward apply of a batched plan (device pointers to Morton-ordered buffers).
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm)
@@ -686,39 +806,9 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
     else e = launch_cuda_core<4>(pd, nrhs, sig, us, mode, st, tm);
     if (e != cudaSuccess) return e;
     if (mode & 2) {
-        const int npad = ((2 * nrhs + 15) / 16) * 16;
-        int tcols = 32;
-        while (tcols < npad) tcols *= 2;
-        const size_t smem = cone_mma_smem(npad);  // within the limit ifgf_batched_prepare set
         int nl = 0;
-        for (int d = pd.D; d >= 3; --d) {
-            const LevelDev &L = pd.lev[d];
-            if (d > 3) {
-                const LevelDev &Lp = pd.lev[d - 1];
-                e = cudaMemsetAsync(Lp.F, 0, (size_t)Lp.nact * kP * nrhs * sizeof(float2), st);
-                if (e != cudaSuccess) return e;
-            }
-            if (L.nact == 0) continue;
-            NvtxRange range("tensor-core cones", d);
-            ConeKernelArgs a;
-            a.d = d;
-            a.nrhs = nrhs;
-            a.npad = npad;
-            a.tmem_cols = tcols;
-            a.do_targets = 1;
-            a.do_upward = d > 3;
-            a.u = us;
-            a.work = pd.sched + d;
-            a.skip_mma = (pd.flags & 256) ? 1 : 0;
-            a.wait_limit = a.skip_mma ? (1 << 10) : kWaitLimit;
-            e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
-            if (e != cudaSuccess) return e;
-            int grid = std::min(L.nact, 2 * 152);
-            k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
-            ++nl;
-        }
+        e = launch_cones(pd, nrhs, us, pd.tune_cone_ctas, st, &nl);
         tm.mark(STAGE_UPWARD, nl, st);
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     k_permute_out<float><<<grid_for(tot, 256), 256, 0, st>>>(out_sorted, out_user, pd.perm, n, nrhs);

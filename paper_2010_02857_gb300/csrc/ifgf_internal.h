@@ -115,6 +115,11 @@ struct PlanDev {
     int *err = nullptr;                                  // device invariant-failure counter
     int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel
     int flags = 0;         // the plan's option flags (test switches read by kernels)
+    // batched path tile shapes (set by the autotuner, ifgf_plan_autotune): the leaf
+    // kernel's register tile (0: 16 RHS threads x 8 node groups, 1: 32 x 4, 2: 8 x 16)
+    // and the tensor-core cone kernel's persistent CTAs per SM (1 or 2)
+    int tune_leaf = 0;
+    int tune_cone_ctas = 2;
     LevelDev lev[IFGF_MAX_LEVELS + 1];
 };
 

@@ -334,6 +334,42 @@ def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     assert np.array_equal(g.apply_adjoint(sigma), w1)
 
 
+@pytest.mark.parametrize("nrhs", [2, 24, 64])
+def test_autotuned_tile_shapes_give_the_same_result(pkg, torch_cuda, nrhs):
+    # every leaf tile shape sums each output over the sources in the same order, and the
+    # cone grid only changes which CTA takes which cone: same leaf values, same field
+    # up to the run-to-run order of the cone kernel's FP32 reductions
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    sig = wi.complex_normal(110 + nrhs, (nrhs, wl.n))
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched")
+    s = torch.from_numpy(sig).cuda().to(torch.complex64)
+    u0 = b.apply(s).cpu().numpy()
+    leaf0 = b.values(5, nrhs)
+    for shape in range(3):
+        for ctas in (1, 2):
+            b.set_tiles(shape, ctas)
+            u = b.apply(s).cpu().numpy()
+            assert rel(u, u0) < 1e-5, (shape, ctas, rel(u, u0))
+            lv = b.values(5, nrhs)
+            assert rel(lv, leaf0) < 1e-6, (shape, rel(lv, leaf0))
+    tune = b.autotune(nrhs, reps=2)
+    assert tune["leaf_shape"] in ("16x8", "32x4", "8x16") and tune["cone_ctas_per_sm"] in (1, 2)
+    assert all(t > 0 for t in tune["leaf_ms"] + tune["cone_ms"])
+    st = b.stats()
+    assert ["16x8", "32x4", "8x16"][st["tune_leaf"]] == tune["leaf_shape"]
+    assert st["tune_cone_ctas"] == tune["cone_ctas_per_sm"]
+    # the tuner's runs use the plan's own buffers: the caller's field is unchanged
+    assert rel(b.apply(s).cpu().numpy(), u0) < 1e-5
+    ex = oracle.direct(pts, wl.kappa, sig[:1])
+    assert rel(b.apply(s).cpu().numpy()[:1], ex) < 1e-3
+    with pytest.raises(pkg.IFGFError):
+        b.autotune(3)
+    with pytest.raises(pkg.IFGFError):
+        b.set_tiles(3, 1)
+    assert b.check() == 0
+
+
 @pytest.mark.parametrize("precision,nrhs,flags", [("fp64", 1, 0), ("mixed", 3, 0), ("batched", 4, 0),
                                                    ("fp64", 2, 8 | 16)])
 def test_graph_replay_matches_plain_launches(pkg, torch_cuda, precision, nrhs, flags):
