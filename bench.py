@@ -44,6 +44,11 @@ UNIT = "interactions/s"
 # Lagrange weights, factor) is box-independent and tabulated per level where that
 # pays, so it is not counted.
 UPWARD_FLOPS_PER_EVAL = 372 + 8
+# Adjoint: every cousin or upward evaluation, transposed, is a rank-1 update of the 75
+# values of its cone's adjoint by the Lagrange weight product times the conjugated factor
+# times the reader's value: 75 real-by-complex multiply-adds (300 flops) plus the complex
+# product of factor and value (8 flops) per RHS.
+ADJOINT_FLOPS_PER_EVAL = 300 + 8
 
 # FP64 FMA throughput per SM per clock on GB300: the nominal 1.25 TFLOP/s at the
 # 2070 MHz maximum SM clock over 152 SMs is 1.25e12 / (2 * 152 * 2.07e9) = 1.99,
@@ -145,34 +150,36 @@ def run_reference(args, wl: wi.Workload):
     if rank != 0:
         return
     oracle.build()
+    direct = oracle.direct if args.op == "apply" else oracle.direct_adjoint
     pts = wl.points()
     sig = wl.densities()
     tg = wl.target_indices()
     m = min(len(tg), max(8, int(args.ref_targets)))
     tg = tg[:m]
-    oracle.direct(pts, wl.kappa, sig, tg[:4])  # warm the library
+    direct(pts, wl.kappa, sig, tg[:4])  # warm the library
     times = []
     for _ in range(args.warmup):
-        oracle.direct(pts, wl.kappa, sig, tg)
+        direct(pts, wl.kappa, sig, tg)
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.direct(pts, wl.kappa, sig, tg)
+        direct(pts, wl.kappa, sig, tg)
         times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
     value = m * wl.n * wl.nrhs / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "n": wl.n, "nrhs": wl.nrhs, "kappa": wl.kappa},
+            "config": {"workload": wl.name, "op": args.op, "n": wl.n, "nrhs": wl.nrhs, "kappa": wl.kappa},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"FP64 direct sum of Eq. (field1) at {m} sampled targets x {wl.n} sources"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def cpu_baseline(wl: wi.Workload, seconds: float = 12.0) -> dict:
+def cpu_baseline(wl: wi.Workload, op: str = "apply", seconds: float = 12.0) -> dict:
     import oracle
     oracle.build()
+    direct = oracle.direct if op == "apply" else oracle.direct_adjoint
     pts = wl.points()
     sig = wl.densities()
     tg = wl.target_indices()
@@ -180,14 +187,15 @@ def cpu_baseline(wl: wi.Workload, seconds: float = 12.0) -> dict:
     t = 0.0
     while True:
         t0 = time.perf_counter()
-        oracle.direct(pts, wl.kappa, sig, tg[:m])
+        direct(pts, wl.kappa, sig, tg[:m])
         t = time.perf_counter() - t0
         if t > seconds / 4 or m >= len(tg):
             break
         m = min(len(tg), int(m * max(2.0, seconds / 4 / max(t, 1e-3))))
     value = m * wl.n * wl.nrhs / t
     return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 direct sum of Eq. (field1) at {m} sampled targets x {wl.n} sources, {t:.1f} s"}
+            "sample": f"FP64 direct sum of Eq. (field1){'' if op == 'apply' else ', conjugate transpose,'} "
+                      f"at {m} sampled targets x {wl.n} sources, {t:.1f} s"}
 
 
 def main():
@@ -204,6 +212,8 @@ def main():
                     help="override the workload's precision")
     ap.add_argument("--nrhs", type=int, default=None,
                     help="override the workload's number of right-hand sides (same generator)")
+    ap.add_argument("--op", default="apply", choices=["apply", "adjoint"],
+                    help="time ifgf_apply (default) or ifgf_apply_adjoint")
     args = ap.parse_args()
     wl = wi.WORKLOADS[args.workload]
     if args.nrhs is not None:
@@ -235,6 +245,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # the operation timed: the forward apply or its adjoint (same plan, same buffers)
+    evaluate = plan.apply if args.op == "apply" else plan.apply_adjoint
     # batched plans: the tile shapes come from the autotuner, timed on this plan
     tiles = None
     if precision == "batched" and wl.nrhs % 2 == 0 and wl.nrhs <= 64:
@@ -246,7 +258,7 @@ def main():
     plan.set_graphs(True)
     plan.set_profiling(True)
     for _ in range(max(3, args.warmup)):
-        plan.apply(sig, out=u)
+        evaluate(sig, out=u)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -259,7 +271,7 @@ def main():
     for k in range(args.steps):
         flush.fill_(float(k))  # L2 flush between steps (256 MB > 129 MB L2)
         ev[k][0].record(stream)
-        plan.apply(sig, out=u)
+        evaluate(sig, out=u)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -272,11 +284,11 @@ def main():
     sig_h = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
     sig_h.copy_(torch.from_numpy(sig_np))
     u_h = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
-    plan.apply(sig_h, out=u_h)  # captures the graph of the host-pointer calls
+    evaluate(sig_h, out=u_h)  # captures the graph of the host-pointer calls
     e2e_times = []
     for _ in range(max(2, min(args.steps, 5))):
         t0 = time.perf_counter()
-        plan.apply(sig_h, out=u_h)  # host pointers: H2D, apply, D2H, synchronise
+        evaluate(sig_h, out=u_h)  # host pointers: H2D, evaluation, D2H, synchronise
         e2e_times.append(time.perf_counter() - t0)
     clk = clocks.stop()
 
@@ -298,7 +310,21 @@ def main():
     up_evals = sum(lv["upward_evals"] for lv in stats["level"])
     cousin_evals = sum(lv["cousin_evals"] for lv in stats["level"])
     f_mhz = clk.get("sm_mhz") or 2070.0
-    if precision == "batched":
+    if args.op == "adjoint":
+        # k_adj_level: the transposed cousin-target and upward evaluations of every level
+        ad_ms = st["adj_level"]["ms"] / calls
+        ad_launches = st["adj_level"]["launches"] / calls
+        flops = (up_evals + cousin_evals) * ADJOINT_FLOPS_PER_EVAL * nrhs
+        if precision == "fp64":
+            peak, psrc = fp64_peak_tflops(clk.get("sm_mhz"))
+        else:
+            peak = 2 * 128 * NUM_SMS * f_mhz * 1e6 / 1e12
+            psrc = f"derived FP32: 128 FMA/clk/SM x {NUM_SMS} SMs x {f_mhz:.0f} MHz"
+        roofline = {"bound": "alu", "kernel": "k_adj_level", "peak_source": psrc,
+                    "work": f"{up_evals + cousin_evals} transposed evaluations x {ADJOINT_FLOPS_PER_EVAL} flops "
+                            f"per RHS, {ad_launches:.0f} launches, {ad_ms:.3f} ms"}
+        up_ms = ad_ms
+    elif precision == "batched":
         # tcgen05 cone kernels: every cousin and upward evaluation is one GEMM row of
         # 75 weights x 2 nrhs real columns (useful flops; the BF16 hi/lo split and
         # the padding of K to 80 are not counted)
@@ -322,7 +348,8 @@ def main():
                     "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
                             f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
     achieved = flops / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
-    traffic = TRAFFIC_BYTES_PER_LAUNCH.get((wl.name, precision)) if nrhs == wi.WORKLOADS[wl.name].nrhs else None
+    traffic = (TRAFFIC_BYTES_PER_LAUNCH.get((wl.name, precision))
+               if nrhs == wi.WORKLOADS[wl.name].nrhs and args.op == "apply" else None)
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None})
@@ -331,7 +358,10 @@ def main():
     if args.check:
         import oracle
         tg = wl.target_indices()[:512]
-        ex = oracle.direct(wl.points(), wl.kappa, wl.densities(), tg)
+        if args.op == "apply":
+            ex = oracle.direct(wl.points(), wl.kappa, wl.densities(), tg)
+        else:
+            ex = oracle.direct_adjoint(wl.points(), wl.kappa, wl.densities(), tg)
         got = u.cpu().numpy()[:, tg]
         check = float(np.linalg.norm(got - ex) / np.linalg.norm(ex))
 
@@ -341,7 +371,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "mixed": "f32+f64", "batched": "bf16x3+f32+f64"}[precision],
                 "data": "synthetic",
-                "config": {"workload": wl.name, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
+                "config": {"workload": wl.name, "op": args.op, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
                            "p_radial": wl.p_radial, "p_angular": wl.p_angular,
                            "leaf_cones": [wl.leaf_ns, wl.leaf_nc], "precision": precision,
                            "l2": "flushed between steps (256 MB write)", "launch": "CUDA graph replay",
@@ -357,7 +387,7 @@ def main():
         if check is not None:
             line["rel_err_sampled"] = check
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"] = cpu_baseline(wl, args.op)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

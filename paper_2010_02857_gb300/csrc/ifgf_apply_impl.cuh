@@ -821,6 +821,157 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
     }
 }
 
+// One right-hand side: the same sums, sum-factorised.  The contribution of a reader
+// with weights w (Lagrange weights of its local coordinates), factor f and value v to
+// node (a, b, c) of the slot is w_c t_ab with t_ab = w_a w_b conj(f) v.  Each lane forms
+// the PS PA values t_ab of the reader it loads; the warp then adds w_c t_ab at the nodes
+// of two readers at a time (2P node slots over the lanes, 150 of 160 for P = 75): two
+// FMAs per node and reader instead of a weight product and two FMAs on 75 of 96 slots.
+// A node's sum over the even readers of each batch of 32 and its sum over the odd ones
+// are added at the end, so the order of every sum is fixed.
+constexpr int kAdj1Warps = 2;
+
+template <typename T, int PS, int PA>
+__global__ void __launch_bounds__(32 * kAdj1Warps) k_adj_level1(PlanDev pd, int d, const void *vs, int mode,
+                                                                 AdjLists al)
+{
+    constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
+    constexpr int NAB = PS * PA;
+    constexpr int NS = (2 * P + 31) / 32;  // node slots per lane (two readers)
+    constexpr int NPL = (P + 31) / 32;     // nodes per lane
+    static_assert(2 * P <= 32 * NAB, "the partial sums reuse the t_ab buffer");
+    __shared__ cpx<T> stab[kAdj1Warps][32][NAB];
+    __shared__ T swc[kAdj1Warps][32][PA];
+    const LevelDev &L = pd.lev[d];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kAdj1Warps + warp;
+    const int nwarps = gridDim.x * kAdj1Warps;
+    for (int slot = al.s0 + gw; slot < al.s1; slot += nwarps) {
+        const int k = L.act_box[slot];
+        const double *ck = L.center + 3 * (size_t)k;
+        cpx<T> acc[NS];
+#pragma unroll
+        for (int h = 0; h < NS; ++h) acc[h] = {T(0), T(0)};
+        for (int pass = 0; pass < 2; ++pass) {
+            if (!((al.passes >> pass) & 1)) continue;
+            const int *lst;
+            int e_begin, e_end;
+            if (pass == 0) {
+                lst = al.tlist;
+                e_begin = al.tstart[slot - al.tbase];
+                e_end = al.tstart[slot - al.tbase + 1];
+            } else {
+                if (d <= 3 || !(mode & 2)) break;
+                lst = al.ulist;
+                e_begin = al.ustart[slot - al.ubase];
+                e_end = al.ustart[slot - al.ubase + 1];
+            }
+            for (int e0 = e_begin; e0 < e_end; e0 += 32) {
+                const int e = e0 + lane;
+                if (e < e_end) {
+                    // a point index, or parent slot * P + node (can exceed 2^31 - 1)
+                    const unsigned item = (unsigned)lst[e];
+                    T w[NW];
+                    cpx<T> f, v;
+                    if (pass == 0) {
+                        double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
+                               vz = __dsub_rn(pd.zs[item], ck[2]);
+                        ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
+                        f = cconj(green_r<T>(pd.kappa, g.r));
+                        v = ld<T>(vs, (size_t)item);
+                    } else {
+                        const LevelDev &Lp = pd.lev[d - 1];
+                        const int psl = item / P, pnode = item % P;
+                        const int oct = (int)(L.key[k] & 7u);
+                        const int pcone = Lp.act_cone[psl];
+                        const int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
+                        if (row >= 0) {
+                            const UpEntry<T, NW> &en =
+                                ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
+#pragma unroll
+                            for (int m = 0; m < NW; ++m) w[m] = en.w[m];
+                            f = cconj(cpx<T>{en.fr, en.fi});
+                        } else {
+                            cpx<T> ff;
+                            up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
+                            f = cconj(ff);
+                        }
+                        v = ld<T>(Lp.Fadj, (size_t)psl * P + pnode);
+                    }
+                    const cpx<T> z = cmul(f, v);
+#pragma unroll
+                    for (int a = 0; a < PS; ++a)
+#pragma unroll
+                        for (int b = 0; b < PA; ++b) {
+                            const T wab = w[a] * w[PS + b];
+                            stab[warp][lane][a * PA + b] = {wab * z.x, wab * z.y};
+                        }
+#pragma unroll
+                    for (int c = 0; c < PA; ++c) swc[warp][lane][c] = w[PS + PA + c];
+                }
+                __syncwarp();
+                const int cnt = min(32, e_end - e0);
+                for (int m = 0; m < cnt; m += 2) {
+#pragma unroll
+                    for (int h = 0; h < NS; ++h) {
+                        const int s = lane + 32 * h;
+                        const int eo = s >= P ? 1 : 0;
+                        const int pn = s - eo * P;
+                        if (s < 2 * P && m + eo < cnt) {
+                            const cpx<T> t = stab[warp][m + eo][pn / PA];
+                            const T wc = swc[warp][m + eo][pn % PA];
+                            acc[h].x += wc * t.x;
+                            acc[h].y += wc * t.y;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // node p: the even readers' sum (slot p) plus the odd readers' sum (slot p + P)
+        cpx<T> *part = &stab[warp][0][0];
+#pragma unroll
+        for (int h = 0; h < NS; ++h) {
+            const int s = lane + 32 * h;
+            if (s < 2 * P) part[s] = acc[h];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < NPL; ++h) {
+            const int pn = lane + 32 * h;
+            if (pn < P) {
+                cpx<T> v = {part[pn].x + part[pn + P].x, part[pn].y + part[pn + P].y};
+                const size_t o = (size_t)slot * P + pn;
+                if (al.accumulate) {
+                    const cpx<T> old = ld<T>(L.Fadj, o);
+                    v.x += old.x;
+                    v.y += old.y;
+                }
+                st<T>(L.Fadj, o, v);
+            }
+        }
+        __syncwarp();  // the partial sums are read before the next slot's readers overwrite them
+    }
+}
+
+// Launch of the adjoint level kernel for slots [al.s0, al.s1): the sum-factorised
+// single-RHS kernel for one right-hand side, else the R-blocked one.
+template <typename T, int R, int PS, int PA>
+inline void launch_adj_level(const PlanDev &pd, int d, int nrhs, const void *vs, int mode, const AdjLists &al,
+                             cudaStream_t st)
+{
+    const int64_t ns = al.s1 - al.s0;
+    if (ns <= 0) return;
+    if constexpr (R == 1) {
+        const int blocks = (int)std::min<int64_t>((ns + kAdj1Warps - 1) / kAdj1Warps, 152 * 128);
+        k_adj_level1<T, PS, PA><<<blocks, 32 * kAdj1Warps, 0, st>>>(pd, d, vs, mode, al);
+    } else {
+        const int blocks = (int)std::min<int64_t>((ns + kAdjWarps - 1) / kAdjWarps, 152 * 64);
+        k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+    }
+}
+
 // Adjoint per source: conj(g(q, x')) times the leaf cones' adjoint values, stored or added
 // to the conjugated near field (accumulate).
 template <typename T, int R, int PS, int PA>
@@ -948,11 +1099,10 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
         for (int d = 3; d <= pd.D; ++d) {
             int nact = pd.lev[d].nact;
             if (nact == 0) continue;
-            int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
             NvtxRange range("adjoint level", d);
             const LevelDev &L = pd.lev[d];
             const AdjLists al = {L.tl_start, L.tl, 0, L.ul_start, L.ul, 0, 0, nact, 3, 0};
-            k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+            launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
             ++nl;
         }
         tm.mark(STAGE_ADJ_LEVEL, nl, st);
@@ -980,13 +1130,12 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
         for (int d = 3; d <= pd.D && s == IFGF_OK; ++d) {
             const int nact = pd.lev[d].nact;
             if (nact == 0) continue;
-            const int blocks = (int)std::min<int64_t>((nact + kAdjWarps - 1) / kAdjWarps, 152 * 64);
             NvtxRange range("adjoint level (lists built here)", d);
             s = ifgf_jit_targets(p, d, &tl, st);
             if (s != IFGF_OK) break;
             {
                 const AdjLists al = {tl.start, tl.list, 0, nullptr, nullptr, 0, 0, nact, 1, 0};
-                k_adj_level<T, R, PS, PA><<<blocks, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+                launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                 if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; break; }
             }
             if (d > 3) {
@@ -995,9 +1144,8 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                 for (size_t c = 0; c + 1 < bounds.size() && s == IFGF_OK; ++c) {
                     s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, st);
                     if (s != IFGF_OK || ul.s1 == ul.s0) continue;
-                    const int nb = (int)std::min<int64_t>((ul.s1 - ul.s0 + kAdjWarps - 1) / kAdjWarps, 152 * 64);
                     const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1};
-                    k_adj_level<T, R, PS, PA><<<nb, 32 * kAdjWarps, 0, st>>>(pd, d, nrhs, vs, mode, al);
+                    launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; }
                     // the lists are freed (and rebuilt) only after the launch has read them
                     if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
