@@ -698,7 +698,70 @@ struct AdjLists {
     const int *ustart, *ulist;
     int ubase;
     int s0, s1, passes, accumulate;
+    const int *tcache_idx;  // per entry of tlist, its index in the level's target cache (or null)
 };
+
+// Weights and conjugated factor of one reader of a level-d cone slot of box k (centre ck):
+// pass 0 a cousin target (item = point index, e its list position), pass 1 a parent
+// interpolation point (item = parent slot * P + node).  Cached geometry is used where
+// the plan holds it: the target cache through the list's cache index, the upward table,
+// or the upward cache of an untabled level (indexed by parent slot, node and the child's
+// position among the parent box's children); otherwise it is computed here.
+template <typename T, int PS, int PA>
+__device__ __forceinline__ void adj_reader(const PlanDev &pd, const LevelDev &L, int d, int k, const double *ck,
+                                           int pass, unsigned item, int e, const AdjLists &al, T *w, cpx<T> &f)
+{
+    constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
+    if (pass == 0) {
+        if constexpr (NW <= 13) {
+            if (al.tcache_idx && L.tcache) {
+                const size_t o = (size_t)al.tcache_idx[e];
+                if constexpr (sizeof(T) == 8) {
+                    const TEntry64 &en = ((const TEntry64 *)L.tcache)[o];
+#pragma unroll
+                    for (int m = 0; m < NW; ++m) w[m] = en.w[m];
+                    f = cconj(cpx<T>{en.gr, en.gi});
+                } else {
+                    const TEntry32 en = ((const TEntry32 *)L.tcache)[o];
+                    lagrange(PS, pd.tsf, pd.itsf, en.t[0], w);
+                    lagrange(PA, pd.taf, pd.itaf, en.t[1], w + PS);
+                    lagrange(PA, pd.taf, pd.itaf, en.t[2], w + PS + PA);
+                    f = cconj(cpx<T>{en.gr, en.gi});
+                }
+                return;
+            }
+        }
+        const double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
+                     vz = __dsub_rn(pd.zs[item], ck[2]);
+        ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
+        f = cconj(green_r<T>(pd.kappa, g.r));
+        return;
+    }
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int psl = item / P, pnode = item % P;
+    const int oct = (int)(L.key[k] & 7u);
+    const int pcone = Lp.act_cone[psl];
+    const int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
+    if (row >= 0) {
+        const UpEntry<T, NW> &en = ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) w[m] = en.w[m];
+        f = cconj(cpx<T>{en.fr, en.fi});
+    } else if (L.ucache) {
+        const int j = Lp.act_box[psl];
+        const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
+        const UpEntry<T, NW> &en =
+            ((const UpEntry<T, NW> *)L.ucache)[(size_t)L.uoff[psl] + (size_t)pnode * nch + (k - k0)];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) w[m] = en.w[m];
+        f = cconj(cpx<T>{en.fr, en.fi});
+    } else {
+        cpx<T> ff;
+        up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
+        f = cconj(ff);
+    }
+}
 
 template <typename T, int R, int PS, int PA>
 __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d, int nrhs, const void *vs, int mode,
@@ -741,33 +804,10 @@ __global__ void __launch_bounds__(32 * kAdjWarps) k_adj_level(PlanDev pd, int d,
                     if (e < e_end) {
                         // a point index, or parent slot * P + node (can exceed 2^31 - 1)
                         const unsigned item = (unsigned)lst[e];
-                        int psl = 0, pnode = 0;
+                        const int psl = (int)(item / P), pnode = (int)(item % P);  // pass 1
                         T w[NW];
                         cpx<T> f;
-                        if (pass == 0) {
-                            double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
-                                   vz = __dsub_rn(pd.zs[item], ck[2]);
-                            ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
-                            f = cconj(green_r<T>(pd.kappa, g.r));
-                        } else {
-                            const LevelDev &Lp = pd.lev[d - 1];
-                            psl = item / P;
-                            pnode = item % P;
-                            const int oct = (int)(L.key[k] & 7u);
-                            const int pcone = Lp.act_cone[psl];
-                            int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
-                            if (row >= 0) {
-                                const UpEntry<T, NW> &en =
-                                    ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
-#pragma unroll
-                                for (int m = 0; m < NW; ++m) w[m] = en.w[m];
-                                f = cconj(cpx<T>{en.fr, en.fi});
-                            } else {
-                                cpx<T> ff;
-                                up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
-                                f = cconj(ff);
-                            }
-                        }
+                        adj_reader<T, PS, PA>(pd, L, d, k, ck, pass, item, e, al, w, f);
 #pragma unroll
                         for (int m = 0; m < NW; ++m) sw[warp][lane][m] = w[m];
 #pragma unroll
@@ -873,32 +913,9 @@ __global__ void __launch_bounds__(32 * kAdj1Warps) k_adj_level1(PlanDev pd, int 
                     // a point index, or parent slot * P + node (can exceed 2^31 - 1)
                     const unsigned item = (unsigned)lst[e];
                     T w[NW];
-                    cpx<T> f, v;
-                    if (pass == 0) {
-                        double vx = __dsub_rn(pd.xs[item], ck[0]), vy = __dsub_rn(pd.ys[item], ck[1]),
-                               vz = __dsub_rn(pd.zs[item], ck[2]);
-                        ConeGeom g = geom_weights<T, PS, PA>(pd, L, vx, vy, vz, w);
-                        f = cconj(green_r<T>(pd.kappa, g.r));
-                        v = ld<T>(vs, (size_t)item);
-                    } else {
-                        const LevelDev &Lp = pd.lev[d - 1];
-                        const int psl = item / P, pnode = item % P;
-                        const int oct = (int)(L.key[k] & 7u);
-                        const int pcone = Lp.act_cone[psl];
-                        const int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
-                        if (row >= 0) {
-                            const UpEntry<T, NW> &en =
-                                ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
-#pragma unroll
-                            for (int m = 0; m < NW; ++m) w[m] = en.w[m];
-                            f = cconj(cpx<T>{en.fr, en.fi});
-                        } else {
-                            cpx<T> ff;
-                            up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
-                            f = cconj(ff);
-                        }
-                        v = ld<T>(Lp.Fadj, (size_t)psl * P + pnode);
-                    }
+                    cpx<T> f;
+                    adj_reader<T, PS, PA>(pd, L, d, k, ck, pass, item, e, al, w, f);
+                    const cpx<T> v = pass == 0 ? ld<T>(vs, (size_t)item) : ld<T>(pd.lev[d - 1].Fadj, (size_t)item);
                     const cpx<T> z = cmul(f, v);
 #pragma unroll
                     for (int a = 0; a < PS; ++a)
@@ -1101,7 +1118,7 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
             if (nact == 0) continue;
             NvtxRange range("adjoint level", d);
             const LevelDev &L = pd.lev[d];
-            const AdjLists al = {L.tl_start, L.tl, 0, L.ul_start, L.ul, 0, 0, nact, 3, 0};
+            const AdjLists al = {L.tl_start, L.tl, 0, L.ul_start, L.ul, 0, 0, nact, 3, 0, L.tl_cache};
             launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
             ++nl;
         }
@@ -1134,7 +1151,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
             s = ifgf_jit_targets(p, d, &tl, st);
             if (s != IFGF_OK) break;
             {
-                const AdjLists al = {tl.start, tl.list, 0, nullptr, nullptr, 0, 0, nact, 1, 0};
+                const AdjLists al = {tl.start, tl.list, 0, nullptr, nullptr, 0, 0, nact, 1, 0, nullptr};
                 launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                 if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; break; }
             }
@@ -1144,7 +1161,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                 for (size_t c = 0; c + 1 < bounds.size() && s == IFGF_OK; ++c) {
                     s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, st);
                     if (s != IFGF_OK || ul.s1 == ul.s0) continue;
-                    const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1};
+                    const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1, nullptr};
                     launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; }
                     // the lists are freed (and rebuilt) only after the launch has read them

@@ -69,6 +69,7 @@ struct LevelDev {
     void *Fadj = nullptr;              // adjoint values
     const int *tl_start = nullptr;     // adjoint: per slot, cousin targets landing in it
     const int *tl = nullptr;
+    const int *tl_cache = nullptr;     // per entry of tl, its evaluation's index in tcache
     const int *ul_start = nullptr;     // adjoint: per slot, parent (slot*P + node) landing in it
     const int *ul = nullptr;
     // batched plans: per entry of tl, the target's local coordinates in its cone

@@ -460,6 +460,19 @@ __global__ void k_emit_tlist(PlanDev pd, int d, const int *off, int *keys, int *
     }
 }
 
+__global__ void k_iota(int *a, int64_t m)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] = (int)i;
+}
+
+// out[j] = src[idx[j]]
+__global__ void k_gather_int(int *out, const int *src, const int *idx, int64_t m)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) out[j] = src[idx[j]];
+}
+
 __global__ void k_point_cousin_count(PlanDev pd, int d, int *cnt)
 {
     const LevelDev &L = pd.lev[d];
@@ -1181,10 +1194,29 @@ ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
             k_emit_tlist<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)off.ptr, (int *)keys.ptr, (int *)vals.ptr);
             CK(cudaGetLastError());
             int *start = nullptr, *list = nullptr;
-            s = sort_to_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, &start, &list, st);
-            if (s != IFGF_OK) return s;
-            L.tl_start = start;
-            L.tl = list;
+            if (L.tcache && P == 75 && m > 0) {
+                // an entry's emission offset is its index in the level's target cache
+                // (both are the per-point cousin-count prefix): sort the offsets, then
+                // gather the points, so the adjoint reads the cached geometry
+                Scratch idx;
+                if (!idx.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+                k_iota<<<nblocks(m), kThreads, 0, st>>>((int *)idx.ptr, m);
+                CK(cudaGetLastError());
+                s = sort_to_csr(p, (int *)keys.ptr, (int *)idx.ptr, m, L.nact, &start, &list, st);
+                if (s != IFGF_OK) return s;
+                DALLOC(pts_list, int, m);
+                k_gather_int<<<nblocks(m), kThreads, 0, st>>>(pts_list, (const int *)vals.ptr, list, m);
+                CK(cudaGetLastError());
+                CK(cudaStreamSynchronize(st));
+                L.tl_start = start;
+                L.tl = pts_list;
+                L.tl_cache = list;
+            } else {
+                s = sort_to_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, &start, &list, st);
+                if (s != IFGF_OK) return s;
+                L.tl_start = start;
+                L.tl = list;
+            }
             if (p->precision == IFGF_BATCHED_BF16 && !(p->flags & 4) && m > 0) {
                 DALLOC(tloc, float4, m);
                 DALLOC(tfac, float2, m);

@@ -318,6 +318,11 @@ def test_evaluation_caches_match_on_the_fly_geometry(pkg, torch_cuda, precision,
         ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
         assert rel(ua, ub) < tol
         assert rel(ua, uo) < (1e-10 if precision == "fp64" else 2e-5)
+        # the adjoint reads the same caches (resident plans: the target cache through
+        # the transpose lists' cache indices; both: the untabled upward cache)
+        wa, wb = a.apply_adjoint(s).cpu().numpy(), b.apply_adjoint(s).cpu().numpy()
+        assert rel(wa, wb) < tol
+        assert rel(wa, o.apply_adjoint(sigma)) < (1e-10 if precision == "fp64" else 2e-5)
         assert a.check() == 0 and b.check() == 0
 
 
