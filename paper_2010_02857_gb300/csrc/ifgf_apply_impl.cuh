@@ -1190,10 +1190,15 @@ ifgf_status run_adjoint_jit(ifgf_plan *p, int nrhs, const void *in_user, void *o
     k_permute_in<T><<<grid_for(tot, 256), 256, 0, st>>>(in_user, p->sig_sorted, pd.perm, pd.n, nrhs);
     constexpr int RB = sizeof(T) == 8 ? 4 : 8;
     ifgf_status s;
-    if (pd.Ps == 3 && pd.Pang == 5)
-        s = nrhs == 1 ? launch_adjoint_jit<T, 1, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries)
-                      : launch_adjoint_jit<T, RB, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
-    else if (pd.Ps == 4 && pd.Pang == 7)
+    if (pd.Ps == 3 && pd.Pang == 5) {
+        if (nrhs == 1)
+            s = launch_adjoint_jit<T, 1, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
+        else if (sizeof(T) == 4 && nrhs <= 4)
+            // FP32 with 2..4 right-hand sides: blocked for 4, as the forward (more warps per SM)
+            s = launch_adjoint_jit<T, 4, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
+        else
+            s = launch_adjoint_jit<T, RB, 3, 5>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
+    } else if (pd.Ps == 4 && pd.Pang == 7)
         s = nrhs == 1 ? launch_adjoint_jit<T, 1, 4, 7>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries)
                       : launch_adjoint_jit<T, RB, 4, 7>(p, nrhs, p->sig_sorted, p->u_sorted, mode, st, max_entries);
     else
