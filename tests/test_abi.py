@@ -61,6 +61,29 @@ def test_invalid_arguments_rejected_before_any_device_work(libifgf):
         assert e.value.status == 1
 
 
+def test_plan_entry_points_reject_a_null_plan(libifgf):
+    # every call that takes a plan returns IFGF_EINVAL (1) for NULL, without touching
+    # the device
+    P, i = ctypes.c_void_p, ctypes.c_int
+    calls = [
+        ("ifgf_plan_set_graphs", [P, i], (None, 1)),
+        ("ifgf_plan_set_tiles", [P, i, i], (None, 0, 2)),
+        ("ifgf_plan_autotune", [P, i, i, P, P, P], (None, 4, 1, None, None, None)),
+        ("ifgf_plan_set_profiling", [P, i], (None, 1)),
+        ("ifgf_apply", [P, P, P, i, P], (None, None, None, 1, None)),
+        ("ifgf_apply_adjoint", [P, P, P, i, P], (None, None, None, 1, None)),
+    ]
+    for name, argtypes, args in calls:
+        f = getattr(libifgf, name)
+        f.argtypes = argtypes
+        f.restype = ctypes.c_int
+        assert f(*args) == 1, name
+    # destroying NULL is a no-op, like free(NULL)
+    libifgf.ifgf_plan_destroy.argtypes = [P]
+    libifgf.ifgf_plan_destroy.restype = ctypes.c_int
+    assert libifgf.ifgf_plan_destroy(None) == 0
+
+
 def test_options_struct_layout_matches_header(tmp_path):
     # the ctypes mirror of ifgf_options must have the C layout of include/ifgf.h
     import shutil
