@@ -11,15 +11,17 @@
 //   k_upward  F_j^{d-1} at the parent cones' interpolation points from the children's
 //             interpolants, re-centred by G(x, x_k^d) / G(x, x_j^{d-1}): one thread
 //             per (parent cone, point), looping over the children.
-//   k_near_staged  per leaf box (one block): level-D direct sums over the neighbouring
-//             boxes (skipping the self term), the sources staged through shared
-//             memory with cp.async; also the adjoint's conjugated sums.
+//   k_near_staged  per run of at most 32 targets of a leaf box (one block): level-D
+//             direct sums over the neighbouring boxes (skipping the self term), the
+//             sources staged through shared memory with cp.async; also the adjoint's
+//             conjugated sums.
 //   k_eval    per target: for d = D..3, interpolation from every cousin box's cone
 //             times G(x, x_k^d), added to the near field.
 // Adjoint (w = A^H v), same data, transposed:
-//   k_adj_level  per relevant cone slot of level d (one warp per slot): conjugated
-//             contributions of the cousin targets that read the slot and of the
-//             parent interpolation points that read it (transpose lists).
+//   k_adj_level1 / k_adj_level  per relevant cone slot of level d (one warp per slot):
+//             conjugated contributions of the cousin targets that read the slot and of
+//             the parent interpolation points that read it (transpose lists); the
+//             first sum-factorised for one right-hand side, the second R-blocked.
 //   k_adj_eval   per source: conj(g) of its leaf's cone values, added to the
 //             conjugated near field.
 #pragma once
