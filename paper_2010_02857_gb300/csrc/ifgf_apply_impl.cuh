@@ -155,13 +155,12 @@ template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, do
     return {a * c, a * s};
 }
 
-// Near-field distances of float plans without FP64 per pair.  A point's position
-// relative to the centre c_k of a leaf box k is formed once in FP64 and split into FP32
-// high and low parts; a source x_j of box k carries the same split of x_j - c_k (the
-// stored leaf offset and its remainder).  The difference of the high parts is exact
-// when the two points are close (Sterbenz), so r = |p - o_j| has FP32 relative
-// accuracy for every pair; the phase kappa r then carries an absolute error of about
-// kappa r * 6e-8.
+// Near-field distances of float plans without FP64 per pair.  Target and source
+// positions relative to the centre c of the target's leaf box are formed once each in
+// FP64 and split into FP32 high and low parts (the near-field kernels stage the
+// sources' splits in shared memory).  The difference of the high parts is exact when
+// the two points are close (Sterbenz), so r = |p - o_j| has FP32 relative accuracy for
+// every pair; the phase kappa r then carries an absolute error of about kappa r * 6e-8.
 struct Rel32 {
     float hx, hy, hz, lx, ly, lz;
 };
@@ -480,6 +479,42 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
 
+// The sources of the neighbours of leaf box b as one list (one warp, the first of the
+// block): sbeg[e] is the first point of neighbour e and spre[e] the list position where
+// its points start; spre[27] is the list length.  Neighbour lists end at the first -1.
+__device__ __forceinline__ void near_ranges(const LevelDev &LD, int b, int lane, int *sbeg, int *spre)
+{
+    int cnt = 0, beg = 0;
+    if (lane < 27) {
+        const int k = LD.nbr[27 * (size_t)b + lane];
+        if (k >= 0) {
+            beg = LD.start[k];
+            cnt = LD.start[k + 1] - beg;
+        }
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane < 27) {
+        sbeg[lane] = beg;
+        spre[lane + 1] = inc;
+    }
+    if (lane == 0) spre[0] = 0;
+}
+
+// The point at position g of that list.
+__device__ __forceinline__ int near_source(const int *sbeg, const int *spre, int g)
+{
+    int e = 0;  // the neighbour range holding g: spre[e] <= g < spre[e + 1]
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1)
+        if (e + w < 28 && spre[e + w] <= g) e += w;
+    return sbeg[e] + (g - spre[e]);
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nrhs, const void *in, void *out,
                                                               int conj)
@@ -498,28 +533,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nr
     const int2 item = pd.near_tile[blockIdx.x];
     const int b = item.x, t0 = item.y;
     const int nt = min(kNearTargets, LD.start[b + 1] - t0);  // 1 .. kNearTargets
-    if (tid < 32) {
-        // neighbour ranges and their exclusive prefix (neighbour lists end at the first -1)
-        int cnt = 0, beg = 0;
-        if (tid < 27) {
-            const int k = LD.nbr[27 * (size_t)b + tid];
-            if (k >= 0) {
-                beg = LD.start[k];
-                cnt = LD.start[k + 1] - beg;
-            }
-        }
-        int inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (tid >= o) inc += v;
-        }
-        if (tid < 27) {
-            sbeg[tid] = beg;
-            spre[tid + 1] = inc;
-        }
-        if (tid == 0) spre[0] = 0;
-    }
+    if (tid < 32) near_ranges(LD, b, tid, sbeg, spre);
     __syncthreads();
     const int ns = spre[27];
     const int q = kNearThreads / nt;
@@ -544,12 +558,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nr
         for (int g0 = 0; g0 < ns; g0 += kNearTile) {
             const int cnt = min(kNearTile, ns - g0);
             for (int s = tid; s < cnt; s += kNearThreads) {
-                const int g = g0 + s;
-                int e = 0;  // the neighbour range holding g: spre[e] <= g < spre[e + 1]
-#pragma unroll
-                for (int w = 16; w >= 1; w >>= 1)
-                    if (e + w < 28 && spre[e + w] <= g) e += w;
-                const int j = sbeg[e] + (g - spre[e]);
+                const int j = near_source(sbeg, spre, g0 + s);
                 sidx[s] = j;
                 if constexpr (sizeof(T) == 8) {
                     cp_async8(sx + s, pd.xs + j);

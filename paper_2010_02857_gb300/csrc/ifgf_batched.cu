@@ -494,50 +494,108 @@ __global__ void k_cache_target_geometry(PlanDev pd, int d, float4 *loc, float2 *
     fac[e] = make_float2(G.x, G.y);
 }
 
-// Near field, one warp per target: lanes compute G for 32 sources at a time, then
-// every lane accumulates its right-hand sides r = lane, lane + 32, ...
-template <int RPL>
-__global__ void __launch_bounds__(128) k_near_batched(PlanDev pd, int nrhs, const float2 *sig, float2 *us, int mode)
+// Near field of the batched path (Algorithm 1's level-D direct evaluations), one block
+// per near work item of the plan (up to 32 consecutive targets of one leaf box).  The
+// sources of the box's neighbours form one list (near_ranges), copied in chunks of
+// kNearKT: the densities [kNearKT][nrhs] with cp.async, the positions as FP64 offsets
+// from the box centre split into FP32 high and low parts (Rel32).  The Green function of
+// every (target, source) pair of the chunk is computed once into shared memory (zero for
+// the self pair), and thread (tx, ty) accumulates targets ty + 8 i and right-hand sides
+// tx + 16 k in registers.  Every output is one thread's sum over the sources in list
+// order.
+constexpr int kNearKT = 32;
+
+template <int RPT>
+__global__ void __launch_bounds__(128) k_near_tiled(PlanDev pd, int nrhs, const float2 *sig, float2 *us)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= pd.n) return;
-    cpx<float> acc[RPL];
+    constexpr int TX = 16, NG = 8;
+    constexpr int TPT = (kNearTargets + NG - 1) / NG;  // targets per thread
+    __shared__ float4 sth[kNearTargets], stl[kNearTargets];  // targets: split offsets
+    __shared__ float4 ssh[kNearKT], ssl[kNearKT];            // the chunk's sources
+    __shared__ float2 sG[kNearTargets][kNearKT + 1];
+    __shared__ __align__(16) float2 ssig[kNearKT * TX * RPT];
+    __shared__ int sj[kNearKT];                              // the chunk's point indices
+    __shared__ int sbeg[27], spre[28];
+    const LevelDev &LD = pd.lev[pd.D];
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int2 item = pd.near_tile[blockIdx.x];
+    const int b = item.x, t0 = item.y;
+    const int nt = min(kNearTargets, LD.start[b + 1] - t0);
+    const double *cb = LD.center + 3 * (size_t)b;
+    const float kf = (float)pd.kappa;
+    if (tid < 32) near_ranges(LD, b, tid, sbeg, spre);
+    if (tid < nt) {
+        const Rel32 p = rel32(pd.xs[t0 + tid], pd.ys[t0 + tid], pd.zs[t0 + tid], cb);
+        sth[tid] = make_float4(p.hx, p.hy, p.hz, 0.f);
+        stl[tid] = make_float4(p.lx, p.ly, p.lz, 0.f);
+    }
+    __syncthreads();
+    const int ns = spre[27];
+    float2 acc[TPT][RPT];
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) acc[q] = {0.f, 0.f};
-    if (mode & 1) {
-        const LevelDev &LD = pd.lev[pd.D];
-        const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
-        const int b = LD.pt_box[i];
-        for (int e = 0; e < 27; ++e) {
-            int k = LD.nbr[27 * (size_t)b + e];
-            if (k < 0) break;
-            const int j1 = LD.start[k + 1];
-            const Rel32 pk = rel32(x, y, z, LD.center + 3 * (size_t)k);
-            for (int j0 = LD.start[k]; j0 < j1; j0 += 32) {
-                int j = j0 + lane;
-                cpx<float> G = {0.f, 0.f};
-                if (j < j1 && j != i) G = green_near32(pk, pd.leaf_off[j], pd.leaf_lo[j], (float)pd.kappa);
-                int cnt = min(32, j1 - j0);
-                for (int t = 0; t < cnt; ++t) {
-                    float gx = __shfl_sync(0xffffffffu, G.x, t), gy = __shfl_sync(0xffffffffu, G.y, t);
+    for (int i = 0; i < TPT; ++i)
 #pragma unroll
-                    for (int q = 0; q < RPL; ++q) {
-                        int r = lane + 32 * q;
-                        if (r < nrhs) {
-                            float2 s = sig[(size_t)(j0 + t) * nrhs + r];
-                            acc[q].x += gx * s.x - gy * s.y;
-                            acc[q].y += gx * s.y + gy * s.x;
-                        }
+        for (int k = 0; k < RPT; ++k) acc[i][k] = make_float2(0.f, 0.f);
+    const int pieces = nrhs / 2;  // 16-byte pieces of a density row (nrhs is even)
+    for (int g0 = 0; g0 < ns; g0 += kNearKT) {
+        const int cnt = min(kNearKT, ns - g0);
+        if (tid < cnt) {
+            const int j = near_source(sbeg, spre, g0 + tid);
+            sj[tid] = j;
+            const Rel32 p = rel32(pd.xs[j], pd.ys[j], pd.zs[j], cb);
+            ssh[tid] = make_float4(p.hx, p.hy, p.hz, 0.f);
+            ssl[tid] = make_float4(p.lx, p.ly, p.lz, 0.f);
+        }
+        __syncthreads();  // sj is complete
+        for (int q = tid; q < cnt * pieces; q += blockDim.x) {
+            const int s = q / pieces, c = q - s * pieces;
+            cp_async16(ssig + s * nrhs + 2 * c, sig + (size_t)sj[s] * nrhs + 2 * c);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int e = tid; e < nt * cnt; e += blockDim.x) {
+            const int t = e / cnt, s = e - t * cnt;
+            float2 g = make_float2(0.f, 0.f);
+            if (sj[s] != t0 + t) {
+                const float4 th = sth[t], tl = stl[t];
+                const Rel32 pt = {th.x, th.y, th.z, tl.x, tl.y, tl.z};
+                const cpx<float> G = green_near32(pt, ssh[s], ssl[s], kf);
+                g = make_float2(G.x, G.y);
+            }
+            sG[t][s] = g;
+        }
+        __syncthreads();
+        for (int s = 0; s < cnt; ++s) {
+            float2 v[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = tx + TX * k;
+                v[k] = r < nrhs ? ssig[s * nrhs + r] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                const int t = ty + NG * i;
+                if (t < nt) {
+                    const float2 g = sG[t][s];
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        acc[i][k].x += g.x * v[k].x - g.y * v[k].y;
+                        acc[i][k].y += g.x * v[k].y + g.y * v[k].x;
                     }
                 }
             }
         }
+        __syncthreads();  // the chunk is read before the next copy overwrites it
     }
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        int r = lane + 32 * q;
-        if (r < nrhs) us[(size_t)i * nrhs + r] = make_float2(acc[q].x, acc[q].y);
+    for (int i = 0; i < TPT; ++i) {
+        const int t = ty + NG * i;
+        if (t >= nt) continue;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = tx + TX * k;
+            if (r < nrhs) us[(size_t)(t0 + t) * nrhs + r] = acc[i][k];
+        }
     }
 }
 
@@ -658,16 +716,22 @@ inline void launch_leaf(const PlanDev &pd, int nrhs, const float2 *sig, int shap
     else launch_leaf_shape<16>(pd, nrhs, sig, nact, st);
 }
 
-template <int RPL>
-cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, float2 *us, int mode, cudaStream_t st,
-                             StageTimer &tm)
+// the CUDA-core stages of the batched path: leaf factors, near field
+inline cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *sig, float2 *us, int mode,
+                                    cudaStream_t st, StageTimer &tm)
 {
     if (mode & 2) {
         launch_leaf(pd, nrhs, sig, pd.tune_leaf, st);
         tm.mark(STAGE_LEAF, pd.lev[pd.D].nact > 0, st);
     }
-    int64_t warps = pd.n;
-    k_near_batched<RPL><<<(int)((warps * 32 + 127) / 128), 128, 0, st>>>(pd, nrhs, sig, us, mode);
+    if (mode & 1) {
+        if (nrhs <= 16) k_near_tiled<1><<<pd.n_near_tile, 128, 0, st>>>(pd, nrhs, sig, us);
+        else if (nrhs <= 32) k_near_tiled<2><<<pd.n_near_tile, 128, 0, st>>>(pd, nrhs, sig, us);
+        else k_near_tiled<4><<<pd.n_near_tile, 128, 0, st>>>(pd, nrhs, sig, us);
+    } else {
+        const cudaError_t e = cudaMemsetAsync(us, 0, (size_t)pd.n * nrhs * sizeof(float2), st);
+        if (e != cudaSuccess) return e;
+    }
     tm.mark(STAGE_EVAL, 1, st);
     return cudaGetLastError();
 }
@@ -800,10 +864,7 @@ cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, v
     const float2 *sig = (const float2 *)in_sorted;
     float2 *us = (float2 *)out_sorted;
     cudaError_t e;
-    int rpl = (nrhs + 31) / 32;
-    if (rpl <= 1) e = launch_cuda_core<1>(pd, nrhs, sig, us, mode, st, tm);
-    else if (rpl <= 2) e = launch_cuda_core<2>(pd, nrhs, sig, us, mode, st, tm);
-    else e = launch_cuda_core<4>(pd, nrhs, sig, us, mode, st, tm);
+    e = launch_cuda_core(pd, nrhs, sig, us, mode, st, tm);
     if (e != cudaSuccess) return e;
     if (mode & 2) {
         int nl = 0;

@@ -107,7 +107,6 @@ struct PlanDev {
     float itsf[IFGF_MAX_P] = {}, itaf[IFGF_MAX_P] = {};
     const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     const float4 *leaf_off = nullptr;  // [N] x_j - centre of its leaf box, and its squared norm (FP32)
-    const float4 *leaf_lo = nullptr;   // [N] the rounding remainder of that offset (x, y, z), FP32
     const int *perm = nullptr;
     // near-field work items: (leaf box, first target) for each run of at most
     // kNearTargets consecutive targets of a level-D box

@@ -152,16 +152,14 @@ __global__ void k_level_boxes(const uint64_t *leafkey, const int *incl, int n, i
 // offset of every point from the centre of its leaf box, and its squared norm: formed
 // in FP64, stored in FP32 (for the FP32 leaf factor), with the rounding remainder of
 // the offset in FP32 (for FP32 near-field distances that stay exact for close pairs)
-__global__ void k_leaf_offsets(PlanDev pd, float4 *off, float4 *lo)
+__global__ void k_leaf_offsets(PlanDev pd, float4 *off)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
     const LevelDev &L = pd.lev[pd.D];
     const double *c = L.center + 3 * (size_t)L.pt_box[i];
     double dx = pd.xs[i] - c[0], dy = pd.ys[i] - c[1], dz = pd.zs[i] - c[2];
-    const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-    off[i] = make_float4(hx, hy, hz, (float)(dx * dx + dy * dy + dz * dz));
-    lo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
+    off[i] = make_float4((float)dx, (float)dy, (float)dz, (float)(dx * dx + dy * dy + dz * dz));
 }
 
 // Near-field work items: the targets of each leaf box in runs of kNearTargets.
@@ -788,11 +786,9 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
     }
     {
         DALLOC(off, float4, n);
-        DALLOC(lo, float4, n);
-        k_leaf_offsets<<<nblocks(n), kThreads, 0, st>>>(pd, off, lo);
+        k_leaf_offsets<<<nblocks(n), kThreads, 0, st>>>(pd, off);
         CK(cudaGetLastError());
         pd.leaf_off = off;
-        pd.leaf_lo = lo;
     }
     {
         const LevelDev &L = pd.lev[D];
