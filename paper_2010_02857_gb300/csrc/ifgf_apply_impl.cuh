@@ -627,7 +627,6 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
     const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
-    const LevelDev &LD = pd.lev[pd.D];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
 #pragma unroll
@@ -1009,7 +1008,6 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
     constexpr int P = PS * PA * PA;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= pd.n) return;
-    const double x = pd.xs[j], y = pd.ys[j], z = pd.zs[j];
     const LevelDev &LD = pd.lev[pd.D];
     const int b = LD.pt_box[j];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
