@@ -1,5 +1,6 @@
 """Parity at the full sizes of the benchmark workloads (ifgf_inputs.WORKLOADS), in the
-launch configuration bench.py times, on outputs the oracle computes one by one:
+launch configuration bench.py times (CUDA-graph replay; batched plans autotuned), on
+outputs the oracle computes one by one:
 
   * sphere_4lambda (N = 24,576, FP64): bit-exact tree and relevant cones against the
     oracle plan; every output against the oracle's serial IFGF (1e-10) and against the
@@ -39,8 +40,12 @@ def rel(a, b):
 
 
 def _plan(pkg, torch, wl, precision, **kw):
-    return pkg.Plan(torch.from_numpy(wl.points()).cuda(), wl.kappa, wl.levels, wl.p_radial, wl.p_angular,
-                    wl.leaf_ns, wl.leaf_nc, precision=precision, **kw)
+    g = pkg.Plan(torch.from_numpy(wl.points()).cuda(), wl.kappa, wl.levels, wl.p_radial, wl.p_angular,
+                 wl.leaf_ns, wl.leaf_nc, precision=precision, **kw)
+    if precision == "batched":
+        g.autotune(wl.nrhs)
+    g.set_graphs(True)
+    return g
 
 
 def _tree_bit_exact(g, o, D):
