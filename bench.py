@@ -65,6 +65,18 @@ TRAFFIC_BYTES_PER_LAUNCH = {
 }
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over the ranks of the process group (the slowest rank sets the
+    job's time); x itself when no group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -292,14 +304,10 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
     clk = clocks.stop()
 
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), dev)
     n, nrhs = wl.n, wl.nrhs
     value = world * n * n * nrhs / (ms * 1e-3)
-    e2e_s = float(np.median(e2e_times))
+    e2e_s = max_over_ranks(float(np.median(e2e_times)), dev)
     eb = 16 if precision == "fp64" else 8
 
     # roofline of the dominant kernel
