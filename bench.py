@@ -155,11 +155,49 @@ def fp64_peak_tflops(sm_mhz) -> tuple[float, str]:
     return peak, f"derived: {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk/SM x {NUM_SMS} SMs x {f:.0f} MHz"
 
 
+def run_reference_ifgf(args, wl: wi.Workload):
+    """The oracle's serial CPU IFGF on the whole workload (first right-hand side): the
+    plan build (T_pre) once, then warm-up and timed applies (T_acc), on the host cores."""
+    import oracle
+    oracle.build()
+    pts = wl.points()
+    sig = wl.densities()[:1]
+    t0 = time.perf_counter()
+    o = oracle.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc)
+    t_pre = time.perf_counter() - t0
+    run = o.apply if args.op == "apply" else o.apply_adjoint
+    for _ in range(args.warmup):
+        run(sig)
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        run(sig)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = wl.n * wl.n / t
+    sample = (f"serial CPU IFGF (Algorithm 1), whole workload, first right-hand side; "
+              f"T_pre {t_pre:.3f} s, T_acc {t:.3f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": max(1, args.steps), "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "op": args.op, "n": wl.n, "nrhs": 1, "kappa": wl.kappa,
+                       "reference": "oracle IFGF"},
+            "t_pre_ms": t_pre * 1e3,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
 def run_reference(args, wl: wi.Workload):
     """The oracle's direct sum on a bounded sample of targets, on the host cores."""
     import oracle
     rank, world, _ = _dist_env()
     if rank != 0:
+        return
+    if args.ref_kind == "ifgf":
+        run_reference_ifgf(args, wl)
         return
     oracle.build()
     direct = oracle.direct if args.op == "apply" else oracle.direct_adjoint
@@ -218,6 +256,10 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(wi.WORKLOADS))
     ap.add_argument("--impl", default="ifgf", choices=["ifgf", "reference"])
     ap.add_argument("--ref-targets", type=int, default=256)
+    ap.add_argument("--ref-kind", default="direct", choices=["direct", "ifgf"],
+                    help="reference arm: the FP64 direct sum on sampled targets (default), or the "
+                         "oracle's serial IFGF (Algorithm 1): plan build and full applies, one "
+                         "right-hand side (OMP_NUM_THREADS sets its threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched"],
