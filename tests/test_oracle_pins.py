@@ -168,6 +168,49 @@ def test_chebyshev_error_bound(n, alpha):
     assert err > bound / 50  # and the bound is attained to within its constant
 
 
+def _factor_interp_error(kappa, ds, dth, rng):
+    """Relative max error of the 3 x 5 x 5 Chebyshev interpolant, in (s, theta, phi), of
+    the analytic factor g_S(x, x') (Eq. factored_f, centre 0) over the cone segment
+    s in [eta - ds, eta], theta in [1, 1 + dth], phi in [0.5, 0.5 + dth], for sources x'
+    in the box [-1/2, 1/2]^3 (H = 1, h = sqrt(3)/2, x = (h/s) (sin t cos p, sin t sin p,
+    cos t)): the setting of the paper's interpolation experiment (Sec. 3.2)."""
+    h, eta = math.sqrt(3.0) / 2.0, math.sqrt(3.0) / 3.0
+    ts, ta = oracle.cheb_nodes(3), oracle.cheb_nodes(5)
+
+    def x_of(u):  # local coordinates u in [-1, 1]^3 -> point
+        s = eta - ds + (1.0 + u[0]) / 2.0 * ds
+        th = 1.0 + (1.0 + u[1]) / 2.0 * dth
+        ph = 0.5 + (1.0 + u[2]) / 2.0 * dth
+        return (h / s) * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+
+    worst = fmax = 0.0
+    zero = np.zeros(3)
+    for xp in rng.uniform(-0.5, 0.5, size=(3, 3)):
+        F = np.array([[[oracle.analytic_factor(x_of((ts[a], ta[b], ta[c])), zero, xp, kappa)
+                        for c in range(5)] for b in range(5)] for a in range(3)])
+        for u in rng.uniform(-1.0, 1.0, size=(30, 3)):
+            w = np.einsum("a,b,c->abc", oracle.lagrange(3, u[0]), oracle.lagrange(5, u[1]), oracle.lagrange(5, u[2]))
+            ex = oracle.analytic_factor(x_of(u), zero, xp, kappa)
+            worst = max(worst, abs((w * F).sum() - ex))
+            fmax = max(fmax, abs(ex))
+    return worst / fmax
+
+
+def test_analytic_factor_interpolation_with_cone_size_scaled_by_1_over_kappa_h():
+    # The paper's claim behind its cone sizes (Sec. 3.2, and the refinement rule of the
+    # cone hierarchy in Sec. 3.3.1): with segment sizes proportional to 1/(kappa H) for
+    # kappa H >= 1, the interpolation error of the analytic factor stays bounded as
+    # kappa H grows, while segments of fixed size lose all accuracy.  A phase of the
+    # wrong sign (|x - x'| + |x|) would oscillate about 2 rad across a scaled segment.
+    rng = np.random.default_rng(2010)
+    ds0, dth0 = math.sqrt(3.0) / 6.0, math.pi / 4.0
+    scaled = {kh: _factor_interp_error(kh, ds0 / max(1.0, kh), dth0 / max(1.0, kh), rng) for kh in (1, 4, 16, 64)}
+    assert all(e <= 2.0 * scaled[1] for e in scaled.values()), scaled
+    assert max(scaled.values()) < 1e-3, scaled
+    fixed_64 = _factor_interp_error(64.0, ds0, dth0, rng)
+    assert fixed_64 > 100.0 * scaled[1], (fixed_64, scaled[1])
+
+
 # --------------------------------------------------------------------------------------
 # Tree, cousins and cones, checked with an independent numpy brute force
 # --------------------------------------------------------------------------------------
