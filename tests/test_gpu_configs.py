@@ -8,7 +8,7 @@ outputs the oracle computes one by one:
   * sphere_32lambda (N = 393,216, FP64): bit-exact tree and cones; 2,000 sampled
     targets against the direct sum and 2,000 sampled sources of the adjoint against
     the direct adjoint (1e-3); the autograd gradient of ||u||^2 against central
-    differences on 32 sampled entries (the loss is quadratic, so differences are
+    differences on 64 sampled entries (the loss is quadratic, so differences are
     exact up to rounding).
   * prolate_128lambda (N = 3,145,728, mixed): 4,096 sampled targets against the direct
     sum (1e-3) and the whole field against the FP64 GPU IFGF on the same inputs
@@ -100,7 +100,7 @@ def test_sphere_32lambda_sampled_forward_adjoint_and_gradient(env):
 
     h = 1e-2
     base = sig[0].copy()
-    for m in wi.sample_targets(wl.n, 32, wl.seed + 300):
+    for m in wi.sample_targets(wl.n, 64, wl.seed + 300):
         for unit, an in ((1.0, grad[m].real), (1j, grad[m].imag)):
             xp = base.copy(); xp[m] += h * unit
             xm = base.copy(); xm[m] -= h * unit
