@@ -61,8 +61,8 @@ typedef enum {
      * (tcgen05, BF16 hi+lo operand split, FP32 accumulate), grouped by source cone;
      * for many right-hand sides.  Used by ifgf_apply for even nrhs <= 64 (other
      * nrhs and the adjoint run the IFGF_MIXED kernels); requires (P_s, P_ang) =
-     * (3, 5).  Contributions are added with asynchronous bulk reductions, so the
-     * last bits of the result vary from run to run. */
+     * (3, 5).  Contributions are added to their destinations with FP32 atomic
+     * reductions, so the last bits of the result vary from run to run. */
     IFGF_BATCHED_BF16 = 2
 } ifgf_precision;
 
@@ -86,7 +86,9 @@ typedef struct {
                        store at plan time each cousin-target evaluation's cone slot,
                        weights (local coordinates for IFGF_MIXED) and centred factor,
                        and the geometry of every upward evaluation of levels without an
-                       upward table; the evaluations then skip that geometry;
+                       upward table; the evaluations, forward and adjoint, then skip
+                       that geometry (the adjoint's transpose lists then also hold each
+                       cousin-target entry's cache index, 4 bytes per evaluation);
                        bit 6: adjoints of two-level plans build their upward transpose
                        lists in ranges of at most 4096 evaluations (testing; the
                        default range is 2^28).  Two-level plans build the adjoint's
