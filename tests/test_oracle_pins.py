@@ -455,6 +455,34 @@ def test_ifgf_matches_direct(n, nl, D, ns, nc, tol):
         assert err < tol, err
 
 
+def _degenerate(kind):
+    u = wi.uniform(77, 0, 20000)
+    if kind == "two points":      # a cube of side 0.3, the points in non-neighbouring leaves
+        return np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1]]), 2 * math.pi, 3
+    if kind == "line":            # collinear along z: zero-extent bounding box in x and y
+        z = np.sort(u[:1200]) * 2 - 1
+        return np.stack([np.zeros(1200), np.zeros(1200), z], 1), 4 * math.pi, 5
+    if kind == "disc":            # coplanar, z = 0
+        r, t = np.sqrt(u[:1500]), 2 * math.pi * u[1500:3000]
+        return np.stack([r * np.cos(t), r * np.sin(t), np.zeros(1500)], 1), 4 * math.pi, 5
+    s = wi.fibonacci_sphere(800) * 0.2   # two clusters far apart: most boxes empty
+    return np.concatenate([s, s + np.array([3.0, 2.0, -1.0])]), 2 * math.pi, 6
+
+
+@pytest.mark.parametrize("kind", ["two points", "line", "disc", "clusters"])
+def test_ifgf_on_degenerate_geometries(kind):
+    # flat, collinear, tiny and clustered point sets: the bounding cube, the clamp of
+    # the integer coordinates and the cone cells (points near the cone axis) still give
+    # the direct sum to 1e-3, forward and adjoint
+    pts, kappa, D = _degenerate(kind)
+    sig = wi.complex_normal(5, (1, len(pts)))
+    P = oracle.Plan(pts, kappa, D, 3, 5, 1, 2)
+    u, w = P.apply(sig), P.apply_adjoint(sig)
+    ex, exa = oracle.direct(pts, kappa, sig), oracle.direct_adjoint(pts, kappa, sig)
+    assert np.linalg.norm(u - ex) / np.linalg.norm(ex) < 1e-3
+    assert np.linalg.norm(w - exa) / np.linalg.norm(exa) < 1e-3
+
+
 def test_ifgf_error_decreases_with_cone_refinement_and_order():
     wl = wi.small_sphere(2500, 4, 4)
     pts = wl.points()
