@@ -233,7 +233,11 @@ ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int64_t n, cons
 /* Root cube: geom[0] = H_1, geom[1..3] = lower corner. */
 ifgf_status ifgf_plan_geometry(const ifgf_plan *plan, double *geom);
 
-/* JSON statistics (counts per level, device bytes, build time) into buf[cap]. */
+/* JSON statistics into buf[cap] (IFGF_EINVAL when cap is too small): sizes, near pairs,
+ * leaf evaluations, build time, device bytes, the two-buffer and chunking choices, cache
+ * bytes, the captured CUDA graphs ("graphs", "graph_captures", "graph_replays"), the
+ * batched tile shapes ("tune_leaf", "tune_cone_ctas"), and per level the box, cousin and
+ * relevant-cone counts, cone intervals, and cousin and upward evaluation counts. */
 ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t cap);
 
 /* Status of the device-side invariant checks of all calls since the last query
