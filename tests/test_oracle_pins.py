@@ -528,3 +528,160 @@ def test_adjoint_dot_product_and_against_direct_adjoint():
     assert np.linalg.norm(trick - Ahv) > 1e-9 * np.linalg.norm(Ahv)
     ex = oracle.direct_adjoint(pts, wl.kappa, v)
     assert np.linalg.norm(Ahv - ex) < 1e-3 * np.linalg.norm(ex)
+
+
+# --------------------------------------------------------------------------------------
+# Relevance rule (ii), Sec. 3.3.2 first paragraph (reading R7): rebuilt in numpy from
+# the paper's definitions alone and compared by set equality
+# --------------------------------------------------------------------------------------
+
+def _np_cheb(n):
+    return np.cos((2 * np.arange(n) + 1) * np.pi / (2 * n))
+
+
+def _np_cells(v, h, ds, dth, ns, nc, slack=1e-9):
+    """Cone cells of the vectors v [m,3] in the (s, theta, phi) variables of
+    Eq. (defparametrizationins), with s = h / |v|, theta = angle to +z and phi in
+    [0, 2 pi), written from Eq. (defconedomain) with numpy's own trigonometry.
+    Returns (ids [m], ambiguous [m], alt [m]): a point whose scaled coordinate lies
+    within `slack` of a cell boundary is ambiguous, and alt is its cone id on the
+    other side of the nearest such boundary (the two cell conventions may differ
+    there only by rounding)."""
+    r = np.linalg.norm(v, axis=1)
+    s = h / r
+    th = np.arctan2(np.hypot(v[:, 0], v[:, 1]), v[:, 2])
+    ph = np.mod(np.arctan2(v[:, 1], v[:, 0]), 2 * np.pi)
+    xs, xt, xp = s / ds, th / dth, ph / dth
+    lim = (ns, nc, 2 * nc)
+    g = [np.clip(np.floor(x), 0, m - 1).astype(np.int64) for x, m in zip((xs, xt, xp), lim)]
+    ids = (g[0] * nc + g[1]) * 2 * nc + g[2]
+    amb = np.zeros(len(v), dtype=bool)
+    alt = ids.copy()
+    for axis, (x, m) in enumerate(zip((xs, xt, xp), lim)):
+        frac = x - np.round(x)
+        near = np.abs(frac) < slack
+        other = [gg.copy() for gg in g]
+        # the neighbouring cell across the boundary at round(x)
+        other[axis] = np.where(np.round(x) > x, g[axis] + 1, g[axis] - 1)
+        if axis == 2:
+            other[axis] = np.mod(other[axis], m)
+        else:
+            other[axis] = np.clip(other[axis], 0, m - 1)
+        oid = (other[0] * nc + other[1]) * 2 * nc + other[2]
+        alt = np.where(near & ~amb, oid, alt)
+        amb |= near
+    return ids, amb, alt
+
+
+def _np_nodes(P, d, cones):
+    """Interpolation points (Eq. interp_pts) of the cones of level d relative to their
+    box centre: R dir per (cone, node), from the level's cell sizes and the
+    first-kind Chebyshev nodes.  Returns R [m, P] and dir [m, P, 3]."""
+    li, lp = P.level_info(d), P.level_params(d)
+    nc = li["nc"]
+    ts, ta = _np_cheb(3), _np_cheb(5)
+    cones = np.asarray(cones, dtype=np.int64)
+    g3 = cones % (2 * nc)
+    g2 = (cones // (2 * nc)) % nc
+    g1 = cones // (2 * nc) // nc
+    a, b, c = np.meshgrid(np.arange(3), np.arange(5), np.arange(5), indexing="ij")
+    a, b, c = a.ravel(), b.ravel(), c.ravel()
+    s = lp["ds"] * (g1[:, None] + (1 + ts[a])[None, :] / 2)
+    th = lp["dth"] * (g2[:, None] + (1 + ta[b])[None, :] / 2)
+    ph = lp["dth"] * (g3[:, None] + (1 + ta[c])[None, :] / 2)
+    R = lp["h"] / s
+    dirs = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=2)
+    return R, dirs
+
+
+def _rule_sets(P, pts, d, octant_map=None):
+    """Per box of level d: the cone ids required by rule (i) (cousin points) and by
+    rule (ii) (interpolation points of the parent's relevant cones), with ambiguous
+    alternatives.  octant_map(oct) -> list of octants plants mistakes: the child's
+    own octant is [oct]."""
+    H1, corner = P.geometry()
+    H = H1 / 2 ** (d - 1)
+    li, lp = P.level_info(d), P.level_params(d)
+    ns, nc = li["ns"], li["nc"]
+    perm = P.perm()
+    xs = pts[perm]
+    keys, start = P.boxes(d)
+    kc = _box_coords(keys)
+    centres = corner + (kc + 0.5) * H
+    cs, cl = P.cousins(d)
+    out = []
+    pkeys = None
+    if d >= 4:
+        pkeys, _ = P.boxes(d - 1)
+        pidx = {int(k): i for i, k in enumerate(pkeys)}
+        pcent = corner + (_box_coords(pkeys) + 0.5) * (2 * H)
+        pa_s, pa_c = P.active(d - 1)
+    for k in range(len(keys)):
+        sure, alts = set(), []
+        src = np.concatenate([np.arange(start[c], start[c + 1]) for c in cl[cs[k]:cs[k + 1]]] +
+                             [np.zeros(0, dtype=np.int64)])
+        vi = xs[src] - centres[k]
+        if len(vi):
+            ids, amb, alt = _np_cells(vi, lp["h"], lp["ds"], lp["dth"], ns, nc)
+            sure |= set(ids[~amb].tolist())
+            alts += [(int(a), int(b)) for a, b in zip(ids[amb], alt[amb])]
+        sure_i = set(sure)
+        if d >= 4:
+            j = pidx[int(keys[k] >> np.uint64(3))]
+            pc = pa_c[pa_s[j]:pa_s[j + 1]]
+            if len(pc):
+                R, dirs = _np_nodes(P, d - 1, pc)
+                q = pcent[j] + R[..., None] * dirs  # absolute positions of the parent's nodes
+                octs = [int(keys[k] & np.uint64(7))]
+                if octant_map is not None:
+                    octs = octant_map(octs[0])
+                for o in octs:
+                    ck = (2 * _box_coords(pkeys[j:j + 1])[0] + np.array([(o >> b) & 1 for b in range(3)]))
+                    cc = corner + (ck + 0.5) * H
+                    ids, amb, alt = _np_cells((q - cc).reshape(-1, 3), lp["h"], lp["ds"], lp["dth"], ns, nc)
+                    sure |= set(ids[~amb].tolist())
+                    alts += [(int(a), int(b)) for a, b in zip(ids[amb], alt[amb])]
+        out.append((sure, alts, sure_i))
+    return out
+
+
+def _matches(active, sure, alts):
+    """active equals the rule's set: every unambiguous cone is in it, every cone in it
+    is required by some point, and each ambiguous point has one of its two cells."""
+    allowed = set(sure)
+    for a, b in alts:
+        allowed |= {a, b}
+    return sure <= active and active <= allowed and all(a in active or b in active for a, b in alts)
+
+
+def test_relevant_cones_rules_i_and_ii_by_set_equality():
+    # For d >= 4 the relevant cones of box k are exactly the cones containing a point of
+    # a cousin box (rule i) or an interpolation point of a relevant cone of the parent
+    # box (rule ii), every point taken relative to x_k^d.  The sets are rebuilt here
+    # from box coordinates, the Chebyshev nodes and numpy trigonometry, with absolute
+    # node positions (not the oracle's R dir - delta form), and compared for equality,
+    # which catches cones missing and cones too many.  Mistakes planted in the rebuilt
+    # rule (the nodes seen from the wrong child's centre, or from all eight children)
+    # must not match.
+    wl = wi.small_sphere(1500, 3, 5, leaf_ns=1, leaf_nc=2)
+    pts = wl.points()
+    P = oracle.Plan(pts, wl.kappa, wl.levels, 3, 5, 1, 2)
+    planted = {"wrong octant": lambda o: [o ^ 1], "all eight children": lambda o: list(range(8))}
+    n_amb = n_ii_only = 0
+    for d in range(3, wl.levels + 1):
+        a_s, a_c = P.active(d)
+        sets = _rule_sets(P, pts, d)
+        for k, (sure, alts, sure_i) in enumerate(sets):
+            active = set(a_c[a_s[k]:a_s[k + 1]].tolist())
+            assert _matches(active, sure, alts), (d, k, sorted(active ^ sure)[:10])
+            n_amb += len(alts)
+            n_ii_only += len(sure - sure_i)
+        if d >= 4:
+            for name, omap in planted.items():
+                bad = _rule_sets(P, pts, d, omap)
+                mism = sum(not _matches(set(a_c[a_s[k]:a_s[k + 1]].tolist()), s, al)
+                           for k, (s, al, _) in enumerate(bad))
+                assert mism > len(bad) // 4, (name, d, mism, len(bad))
+    # rule (ii) contributes cones of its own (otherwise the comparison would not test it)
+    assert n_ii_only > 100
+    assert n_amb < 50
