@@ -13,6 +13,13 @@ paper's T_acc excludes T_pre; its build time is reported as t_plan_ms.
 
 --impl reference times the CPU oracle (the direct sum of Eq. field1 on a bounded
 sample of targets, all host cores) on the same workload and metric.
+
+The default workload is the largest one that fits one GPU: the 256-wavelength sphere
+(N = 25,165,824, 8 right-hand sides, mixed precision).  The line reports the accuracy
+of what it timed (rel_err_sampled: the largest relative l2 error over the right-hand
+sides at sampled targets, against the oracle's FP64 direct sum, which the cpu_baseline
+leg computes and times) and the roofline of the dominant kernel against FMA rates
+measured on the device (ifgf_device_peak).
 """
 from __future__ import annotations
 
@@ -33,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 import ifgf_inputs as wi  # noqa: E402
 
-DEFAULT_WORKLOAD = "sphere_32lambda"
+DEFAULT_WORKLOAD = "sphere_256lambda"
 METRIC = "IFGF apply time and equivalent interactions/s (N^2/t) at rel.err<=1e-3 vs FP64 direct"
 UNIT = "interactions/s"
 
@@ -50,19 +57,27 @@ UPWARD_FLOPS_PER_EVAL = 372 + 8
 # product of factor and value (8 flops) per RHS.
 ADJOINT_FLOPS_PER_EVAL = 300 + 8
 
-# FP64 FMA throughput per SM per clock on GB300: the nominal 1.25 TFLOP/s at the
-# 2070 MHz maximum SM clock over 152 SMs is 1.25e12 / (2 * 152 * 2.07e9) = 1.99,
-# i.e. 2 FMAs per clock per SM.
-FP64_FMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of
-# the same bench command (profiles/k_upward_sphere_32lambda_traffic.md), keyed by
-# (workload, precision).  A configuration without a capture of the current kernel
-# reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {
-    ("sphere_32lambda", "fp64"): 50.89e9 / 5,
-}
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of
+# the kernel, keyed by (workload, precision).  Each entry records the SHA-256 of the
+# kernel source it was captured on; when the source has changed since, the bench
+# reports null instead of a stale figure.
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02857_gb300", "csrc", "ifgf_apply_impl.cuh")
+TRAFFIC_BYTES_PER_LAUNCH = {}
+
+
+def _source_sha(path: str) -> str:
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch(workload: str, precision: str):
+    ent = TRAFFIC_BYTES_PER_LAUNCH.get((workload, precision))
+    if not ent or ent["sha"] != _source_sha(KERNEL_SOURCE):
+        return None
+    return ent["bytes"]
 
 
 def max_over_ranks(x: float, device="cpu") -> float:
@@ -148,13 +163,6 @@ def measured_peaks() -> dict:
     return {}
 
 
-def fp64_peak_tflops(sm_mhz) -> tuple[float, str]:
-    """FP64 peak derived from unit counts and the sampled SM clock."""
-    f = sm_mhz if sm_mhz else 2070.0
-    peak = 2 * FP64_FMA_PER_CLK_PER_SM * NUM_SMS * f * 1e6 / 1e12
-    return peak, f"derived: {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk/SM x {NUM_SMS} SMs x {f:.0f} MHz"
-
-
 def run_reference_ifgf(args, wl: wi.Workload):
     """The oracle's serial CPU IFGF on the whole workload (first right-hand side): the
     plan build (T_pre) once, then warm-up and timed applies (T_acc), on the host cores."""
@@ -204,9 +212,13 @@ def run_reference(args, wl: wi.Workload):
     pts = wl.points()
     sig = wl.densities()
     tg = wl.target_indices()
-    m = min(len(tg), max(8, int(args.ref_targets)))
+    # each step is a bounded sample: at most --ref-targets targets, fewer when one step
+    # would take more than about --ref-step-s seconds (the run stays within minutes)
+    t0 = time.perf_counter()
+    direct(pts, wl.kappa, sig, tg[:4])  # warms the library and sizes the sample
+    per_target = (time.perf_counter() - t0) / 4
+    m = int(min(len(tg), max(4, int(args.ref_targets)), max(4, args.ref_step_s / max(per_target, 1e-9))))
     tg = tg[:m]
-    direct(pts, wl.kappa, sig, tg[:4])  # warm the library
     times = []
     for _ in range(args.warmup):
         direct(pts, wl.kappa, sig, tg)
@@ -226,26 +238,36 @@ def run_reference(args, wl: wi.Workload):
     print(json.dumps(line))
 
 
-def cpu_baseline(wl: wi.Workload, op: str = "apply", seconds: float = 12.0) -> dict:
+def cpu_baseline(wl: wi.Workload, op: str = "apply", seconds: float = 15.0, u=None) -> tuple[dict, dict]:
+    """The oracle's FP64 direct sum (or its conjugate transpose) at sampled targets, timed
+    on the host cores, on a bounded sample: the first m of the workload's sampled targets,
+    m sized to about `seconds` of CPU work.  The same exact values give the accuracy of
+    the GPU result u [nrhs, N] at those targets: the largest relative l2 error over the
+    right-hand sides."""
     import oracle
     oracle.build()
     direct = oracle.direct if op == "apply" else oracle.direct_adjoint
     pts = wl.points()
     sig = wl.densities()
     tg = wl.target_indices()
-    m = 8
-    t = 0.0
-    while True:
-        t0 = time.perf_counter()
-        direct(pts, wl.kappa, sig, tg[:m])
-        t = time.perf_counter() - t0
-        if t > seconds / 4 or m >= len(tg):
-            break
-        m = min(len(tg), int(m * max(2.0, seconds / 4 / max(t, 1e-3))))
+    t0 = time.perf_counter()
+    direct(pts, wl.kappa, sig, tg[:4])
+    per_target = (time.perf_counter() - t0) / 4
+    m = int(min(len(tg), max(8, seconds / max(per_target, 1e-9))))
+    t0 = time.perf_counter()
+    ex = direct(pts, wl.kappa, sig, tg[:m])
+    t = time.perf_counter() - t0
     value = m * wl.n * wl.nrhs / t
-    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    base = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 direct sum of Eq. (field1){'' if op == 'apply' else ', conjugate transpose,'} "
-                      f"at {m} sampled targets x {wl.n} sources, {t:.1f} s"}
+                      f"at {m} sampled targets x {wl.n} sources x {wl.nrhs} RHS, {t:.1f} s"}
+    acc = None
+    if u is not None:
+        got = u[:, tg[:m]].astype(np.complex128)
+        errs = [float(np.linalg.norm(got[r] - ex[r]) / np.linalg.norm(ex[r])) for r in range(wl.nrhs)]
+        acc = {"rel_err_sampled": max(errs), "targets": m,
+               "reference": "oracle FP64 direct sum (the cpu_baseline sample)"}
+    return base, acc
 
 
 def main():
@@ -256,12 +278,13 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(wi.WORKLOADS))
     ap.add_argument("--impl", default="ifgf", choices=["ifgf", "reference"])
     ap.add_argument("--ref-targets", type=int, default=256)
+    ap.add_argument("--ref-step-s", type=float, default=4.0,
+                    help="reference arm: bound of one step's CPU time (sizes the target sample)")
     ap.add_argument("--ref-kind", default="direct", choices=["direct", "ifgf"],
                     help="reference arm: the FP64 direct sum on sampled targets (default), or the "
                          "oracle's serial IFGF (Algorithm 1): plan build and full applies, one "
                          "right-hand side (OMP_NUM_THREADS sets its threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--check", action="store_true", help="verify the accuracy on sampled targets")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched"],
                     help="override the workload's precision")
     ap.add_argument("--nrhs", type=int, default=None,
@@ -340,7 +363,7 @@ def main():
     u_h = torch.empty(sig.shape, dtype=sig.dtype, pin_memory=True)
     evaluate(sig_h, out=u_h)  # captures the graph of the host-pointer calls
     e2e_times = []
-    for _ in range(max(2, min(args.steps, 5))):
+    for _ in range(max(2, min(args.steps, 3))):
         t0 = time.perf_counter()
         evaluate(sig_h, out=u_h)  # host pointers: H2D, evaluation, D2H, synchronise
         e2e_times.append(time.perf_counter() - t0)
@@ -352,25 +375,25 @@ def main():
     e2e_s = max_over_ranks(float(np.median(e2e_times)), dev)
     eb = 16 if precision == "fp64" else 8
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, against FMA or tensor rates measured on this device
     st = timings["stages"]
     calls = max(1, timings["calls"])
     up_ms = st["upward"]["ms"] / calls
     up_launches = st["upward"]["launches"] / calls
     up_evals = sum(lv["upward_evals"] for lv in stats["level"])
     cousin_evals = sum(lv["cousin_evals"] for lv in stats["level"])
-    f_mhz = clk.get("sm_mhz") or 2070.0
+    fp64_peak = pkg.device_peak("fp64")
+    fp32_peak = pkg.device_peak("fp32")
+    pipe = "FP64" if precision == "fp64" else "FP32"
+    peak_src = (f"measured {pipe} FMA rate of this device (ifgf_device_peak: independent FMA chains, "
+                f"CUDA events)")
     if args.op == "adjoint":
         # k_adj_level: the transposed cousin-target and upward evaluations of every level
         ad_ms = st["adj_level"]["ms"] / calls
         ad_launches = st["adj_level"]["launches"] / calls
         flops = (up_evals + cousin_evals) * ADJOINT_FLOPS_PER_EVAL * nrhs
-        if precision == "fp64":
-            peak, psrc = fp64_peak_tflops(clk.get("sm_mhz"))
-        else:
-            peak = 2 * 128 * NUM_SMS * f_mhz * 1e6 / 1e12
-            psrc = f"derived FP32: 128 FMA/clk/SM x {NUM_SMS} SMs x {f_mhz:.0f} MHz"
-        roofline = {"bound": "alu", "kernel": "k_adj_level", "peak_source": psrc,
+        peak = fp64_peak if precision == "fp64" else fp32_peak
+        roofline = {"bound": "alu", "kernel": "k_adj_level", "peak_source": peak_src,
                     "work": f"{up_evals + cousin_evals} transposed evaluations x {ADJOINT_FLOPS_PER_EVAL} flops "
                             f"per RHS, {ad_launches:.0f} launches, {ad_ms:.3f} ms"}
         up_ms = ad_ms
@@ -384,36 +407,19 @@ def main():
         roofline = {"bound": "tensor", "kernel": "k_cone_mma", "peak_source": "measured bf16 dense (burst)",
                     "work": f"{rows} GEMM rows x {2 * 75 * 2 * nrhs} flops per apply, "
                             f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
-    elif precision == "mixed":
-        flops = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs
-        peak = 2 * 128 * NUM_SMS * f_mhz * 1e6 / 1e12
-        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source":
-                    f"derived FP32: 128 FMA/clk/SM x {NUM_SMS} SMs x {f_mhz:.0f} MHz",
-                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP32 flops per RHS, "
-                            f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
     else:
         flops = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs
-        peak, psrc = fp64_peak_tflops(clk.get("sm_mhz"))
-        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source": psrc,
-                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} FP64 flops per apply, "
-                            f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
+        peak = fp64_peak if precision == "fp64" else fp32_peak
+        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source": peak_src,
+                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} {pipe} flops per RHS, "
+                            f"{nrhs} RHS, {up_launches:.0f} launches, {up_ms:.3f} ms"}
     achieved = flops / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
-    traffic = (TRAFFIC_BYTES_PER_LAUNCH.get((wl.name, precision))
+    traffic = (traffic_per_launch(wl.name, precision)
                if nrhs == wi.WORKLOADS[wl.name].nrhs and args.op == "apply" else None)
     roofline.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None})
-
-    check = None
-    if args.check:
-        import oracle
-        tg = wl.target_indices()[:512]
-        if args.op == "apply":
-            ex = oracle.direct(wl.points(), wl.kappa, wl.densities(), tg)
-        else:
-            ex = oracle.direct_adjoint(wl.points(), wl.kappa, wl.densities(), tg)
-        got = u.cpu().numpy()[:, tg]
-        check = float(np.linalg.norm(got - ex) / np.linalg.norm(ex))
+                     "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
+                     "measured_fma_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak}})
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -434,10 +440,11 @@ def main():
                 "gpu_launches": int(sum(v["launches"] for v in st.values()) / calls * args.steps),
                 "roofline": roofline, "clocks": clk,
                 "device_bytes": stats["device_bytes"]}
-        if check is not None:
-            line["rel_err_sampled"] = check
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(wl, args.op)
+            base, acc = cpu_baseline(wl, args.op, u=u.cpu().numpy())
+            line["cpu_baseline"] = base
+            line["rel_err_sampled"] = acc["rel_err_sampled"]
+            line["accuracy"] = acc
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -185,6 +185,32 @@ def sample_targets(n: int, m: int, seed: int) -> np.ndarray:
     return out
 
 
+DEGENERATE = ("two points", "line", "disc", "clusters")
+
+
+def degenerate_points(kind: str):
+    """Small degenerate point sets for edge-case checks: (points [n,3], kappa, levels).
+
+    * "two points": two points in non-neighbouring leaves of a cube of side 0.3;
+    * "line": 1200 collinear points along z (zero extent in x and y);
+    * "disc": 1500 coplanar points on the unit disc z = 0;
+    * "clusters": two Fibonacci spheres of radius 0.2 far apart (most boxes empty).
+    """
+    u = uniform(77, 0, 20000)
+    if kind == "two points":
+        return np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1]]), 2 * math.pi, 3
+    if kind == "line":
+        z = np.sort(u[:1200]) * 2 - 1
+        return np.stack([np.zeros(1200), np.zeros(1200), z], 1), 4 * math.pi, 5
+    if kind == "disc":
+        r, t = np.sqrt(u[:1500]), 2 * math.pi * u[1500:3000]
+        return np.stack([r * np.cos(t), r * np.sin(t), np.zeros(1500)], 1), 4 * math.pi, 5
+    if kind == "clusters":
+        s = fibonacci_sphere(800) * 0.2
+        return np.concatenate([s, s + np.array([3.0, 2.0, -1.0])]), 2 * math.pi, 6
+    raise ValueError(kind)
+
+
 # --------------------------------------------------------------------------------------
 # Named workloads
 # --------------------------------------------------------------------------------------

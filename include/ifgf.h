@@ -100,7 +100,10 @@ typedef struct {
                        bit 8: the tensor-core cone kernel of IFGF_BATCHED_BF16 plans
                        issues no MMA, so its bounded waits for them run out (after a
                        shortened limit) and the device error counter records it
-                       (testing; see ifgf_plan_check). */
+                       (testing; see ifgf_plan_check);
+                       bit 9: FP32 upward steps read the child cone values from L1
+                       instead of staging them in shared memory (testing: the two
+                       kernels sum in the same order). */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels
@@ -175,15 +178,21 @@ ifgf_status ifgf_apply_partial(ifgf_plan *plan, const void *in, void *out, int n
  *     bytes); a plan whose evaluation needs more is rejected with IFGF_EINVAL.
  *     The array is a static device variable of the library: every GPU that loads
  *     the library holds it until the process exits.
- *   - sigma and u must be device pointers ([nrhs][N] complex, as for ifgf_apply).
- *   - The first call on a device looks up the array's device address (with that
- *     device current) and caches it; make that first call before any stream
- *     capture.
+ *   - sigma and u must be device pointers of the plan's device ([nrhs][N] complex,
+ *     as for ifgf_apply), and the plan's device must be current.
+ *   - The evaluation runs on the CUDA-core kernels of the plan's data type, all nrhs
+ *     in one pass: IFGF_BATCHED_BF16 plans are evaluated by the IFGF_MIXED kernels
+ *     (FP32 contraction, not the tensor cores), so their result differs from
+ *     ifgf_apply's by the BF16 operand rounding.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress).  The first call on a device may load the library's
+ *     device code there; make that first call before any stream capture.
  *   - Every call shares the array and it keeps the last call's contents; each call
  *     overwrites all of the scratch it reads, so nothing is cleared.  Calls whose
  *     work overlaps on the GPU (different streams, or different threads) race on
  *     the array and give wrong results: serialise them.
- * Errors: IFGF_EINVAL (sizes, host pointers, scratch limit), IFGF_ECUDA.
+ * Errors: IFGF_EINVAL (sizes, host pointers or another device's pointers, another
+ * device current, scratch limit), IFGF_ECUDA.
  */
 ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma, void *u, int nrhs, void *stream);
 
@@ -223,8 +232,10 @@ ifgf_status ifgf_plan_get_values(const ifgf_plan *plan, int level, void *out);
  * Cone cells (Eq. defconedomain, defconedomainproduct) of the vectors v[n][3]
  * (host; a vector is a point minus a box centre) at level d >= 3, by the two
  * device paths the library uses: exact[i] from correctly rounded FP64 operations
- * (plan construction) and fast[i] from Newton-refined estimates with a correctly
- * rounded fallback near cell boundaries (evaluation).  Both are linear cone ids
+ * (plan construction) and fast[i] from the evaluation path of the plan's precision
+ * (FP64 plans: Newton-refined FP64 estimates; other plans: FP64 radius and FP32 angle
+ * decisions with a margin), each with a correctly rounded fallback near cell
+ * boundaries.  Both are linear cone ids
  * (g1 n_C + g2) 2 n_C + g3 and must be equal; for tests.
  */
 ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int64_t n, const double *v,
@@ -306,6 +317,17 @@ ifgf_status ifgf_plan_set_graphs(ifgf_plan *plan, int on);
  */
 ifgf_status ifgf_plan_timings(const ifgf_plan *plan, double *ms, int64_t *launches, int64_t *calls,
                               int count);
+
+/*
+ * Roofline probe (not part of the paper's method): the device's sustained fused
+ * multiply-add rate, *tflops in TFLOP/s (2 flops per FMA), for which = 0 (FP64) or
+ * which = 1 (FP32), measured on the current device by a kernel of independent FMA
+ * chains with no memory traffic (best of 5 timed runs after a warm-up, CUDA events on
+ * `stream`; synchronises it).  The FP64 and mixed evaluation kernels are bound by these
+ * pipes, so their roofline fractions divide by these rates.
+ * Errors: IFGF_EINVAL (which, NULL), IFGF_ECUDA.
+ */
+ifgf_status ifgf_device_peak(int which, double *tflops, void *stream);
 
 /* Message of the last failed call on this plan (or of the last failed
  * ifgf_plan_create when plan is NULL).  Never NULL. */

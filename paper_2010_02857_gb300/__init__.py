@@ -37,7 +37,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_p
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
            "ifgf_plan_geometry",
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_autotune", "ifgf_plan_set_tiles", "ifgf_plan_timings",
-           "ifgf_last_error"]
+           "ifgf_device_peak", "ifgf_last_error"]
 STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
 
 
@@ -85,6 +85,7 @@ def lib():
         L.ifgf_plan_autotune.argtypes = [P, i, i, P, P, P]
         L.ifgf_plan_set_tiles.argtypes = [P, i, i]
         L.ifgf_plan_timings.argtypes = [P, P, P, P, i]
+        L.ifgf_device_peak.argtypes = [i, P, P]
         L.ifgf_last_error.argtypes = [P]
         L.ifgf_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -166,6 +167,15 @@ def apply_noalloc(handle, sigma, u, nrhs: int, stream=None):
     device array (device tensors only; the library allocates nothing)."""
     _check(lib().ifgf_apply_noalloc(handle, _ptr(sigma), _ptr(u), int(nrhs),
                                     stream if stream is not None else _stream(sigma)), handle)
+
+
+def device_peak(which: str, stream=None) -> float:
+    """ifgf_device_peak: the current device's measured FMA rate in TFLOP/s, which =
+    "fp64" or "fp32" (a roofline denominator)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ifgf_device_peak({"fp64": 0, "fp32": 1}[which], ctypes.byref(out),
+                                  stream if stream is not None else _stream()))
+    return float(out.value)
 
 
 def plan_destroy(handle):

@@ -115,6 +115,12 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     p->max_nrhs = o.max_nrhs;
     p->flags = o.flags;
     p->dev.flags = o.flags;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        g_create_error = "no CUDA device";
+        return IFGF_ECUDA;
+    }
     p->timeout_s = o.timeout_s;
     p->value_budget = (size_t)o.value_budget_bytes;
     cudaStream_t st = (cudaStream_t)stream;
@@ -563,14 +569,14 @@ extern "C" ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors)
     return IFGF_OK;
 }
 
-__global__ void k_cone_ids(PlanDev pd, int d, int n, const double *v, int *exact, int *fast)
+__global__ void k_cone_ids(PlanDev pd, int d, int n, const double *v, int *exact, int *fast, int mixed)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const LevelDev &L = pd.lev[d];
     double x = v[3 * (size_t)i], y = v[3 * (size_t)i + 1], z = v[3 * (size_t)i + 2];
     exact[i] = ifgf::cone_of(L, x, y, z).cone;
-    fast[i] = ifgf::cone_of_fast(L, x, y, z).cone;
+    fast[i] = mixed ? ifgf::cone_of_mixed(L, x, y, z).cone : ifgf::cone_of_fast(L, x, y, z).cone;
 }
 
 extern "C" ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int64_t n, const double *v,
@@ -590,7 +596,8 @@ extern "C" ifgf_status ifgf_plan_cone_ids(const ifgf_plan *plan, int level, int6
     ifgf_status st = IFGF_OK;
     if (cudaMemcpy(dv, v, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) st = IFGF_ECUDA;
     if (st == IFGF_OK) {
-        k_cone_ids<<<(int)((n + 255) / 256), 256>>>(p->dev, level, (int)n, dv, de, de + n);
+        k_cone_ids<<<(int)((n + 255) / 256), 256>>>(p->dev, level, (int)n, dv, de, de + n,
+                                                     p->precision != IFGF_FP64);
         if (cudaDeviceSynchronize() != cudaSuccess) st = IFGF_ECUDA;
     }
     if (st == IFGF_OK && (cudaMemcpy(exact, de, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||

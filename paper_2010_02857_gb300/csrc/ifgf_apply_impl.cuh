@@ -36,6 +36,8 @@ namespace ifgf {
 
 constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
 
+inline int grid_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
 template <typename T> struct Vec { using type = double2; };
 template <> struct Vec<float> { using type = float2; };
 
@@ -138,20 +140,22 @@ __device__ __forceinline__ double rsqrt64(double r2)
 __device__ __forceinline__ cpx<double> green_r2_64(double kappa, double r2)
 {
     const double y = rsqrt64(r2);
+    const double a = kInv4Pi * y;
+    if (kappa == 0.0) return {a, 0.0};  // Laplace kernel: no phase
     double c, s;
     expi(kappa * (r2 * y), c, s);
-    const double a = kInv4Pi * y;
     return {a * c, a * s};
 }
 
 // e^{i kappa r} / (4 pi r)
 template <typename T> __device__ __forceinline__ cpx<T> green_r(double kappa, double r)
 {
-    T c, s;
-    expi(kappa * r, c, s);
     T a;
     if constexpr (sizeof(T) == 8) a = kInv4Pi / r;
     else a = (float)kInv4Pi / (float)r;
+    if (kappa == 0.0) return {a, T(0)};  // Laplace kernel: no phase
+    T c, s;
+    expi(kappa * r, c, s);
     return {a * c, a * s};
 }
 
@@ -185,9 +189,10 @@ __device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 
     const float dy = (p.hy - oh.y) + (p.ly - ol.y);
     const float dz = (p.hz - oh.z) + (p.lz - ol.z);
     const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float a = __fdividef((float)kInv4Pi, r);
+    if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
     float c, s;
     sincosf(kf * r, &s, &c);
-    const float a = __fdividef((float)kInv4Pi, r);
     return {a * c, a * s};
 }
 
@@ -205,10 +210,11 @@ __device__ __forceinline__ cpx<float> leaf_factor32(float Rf, float dx, float dy
 {
     const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
     const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
+    const float a = __fdividef(Rf, r1);
+    if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
     const float ph = __fdividef(kf * num, r1 + Rf);
     float c, s;
     sincosf(ph, &s, &c);
-    const float a = __fdividef(Rf, r1);
     return {a * c, a * s};
 }
 
@@ -219,9 +225,10 @@ __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const
         const double dx = q[0] - pd.xs[j], dy = q[1] - pd.ys[j], dz = q[2] - pd.zs[j];
         const double r2 = dx * dx + dy * dy + dz * dz;
         const double y = rsqrt64(r2);
+        const double a = R * y;
+        if (pd.kappa == 0.0) return {a, 0.0};  // Laplace kernel: no phase
         double c, s;
         expi(pd.kappa * (r2 * y - R), c, s);
-        const double a = R * y;
         return {a * c, a * s};
     } else {
         // the quotients need FP32 relative accuracy only (r1 + R and r1 lie far inside
@@ -235,7 +242,7 @@ template <typename T, int PS, int PA>
 __device__ __forceinline__ ConeGeom geom_weights(const PlanDev &pd, const LevelDev &L, double vx, double vy,
                                                  double vz, T *w)
 {
-    ConeGeom g = cone_of_fast(L, vx, vy, vz);
+    ConeGeom g = sizeof(T) == 8 ? cone_of_fast(L, vx, vy, vz) : cone_of_mixed(L, vx, vy, vz);
     if constexpr (sizeof(T) == 8) {
         double loc[3];
         local_coords(L, g, vx, vy, vz, loc);
@@ -261,21 +268,24 @@ __device__ __forceinline__ cpx<T> recentre(double kappa, double Rj, const double
                                            double dx, double dy, double dz)
 {
     if constexpr (sizeof(T) == 8) {
+        T a = Rj / rk;
+        if (kappa == 0.0) return {a, T(0)};  // Laplace kernel: a real ratio
         double dd = dx * dx + dy * dy + dz * dz;
         double yd = dir[0] * dx + dir[1] * dy + dir[2] * dz;
         double diff = (dd - 2.0 * Rj * yd) / (rk + Rj);
         T c, s;
         expi(kappa * diff, c, s);
-        T a = Rj / rk;
         return {a * c, a * s};
     } else {
-        const float fx = (float)dx, fy = (float)dy, fz = (float)dz, Rf = (float)Rj, rkf = (float)rk;
+        const float Rf = (float)Rj, rkf = (float)rk;
+        const float a = __fdividef(Rf, rkf);
+        if (kappa == 0.0) return {a, 0.f};  // Laplace kernel: a real ratio
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
         const float dd = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
         const float yd = fmaf((float)dir[0], fx, fmaf((float)dir[1], fy, (float)dir[2] * fz));
         const float diff = __fdividef(fmaf(-2.0f * Rf, yd, dd), rkf + Rf);
         float c, s;
         sincosf((float)kappa * diff, &s, &c);
-        const float a = __fdividef(Rf, rkf);
         return {a * c, a * s};
     }
 }
@@ -440,6 +450,193 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
         for (int r = 0; r < R; ++r)
             if (R == 1 || r0 + r < nrhs) st<T>(Lp.F, ((size_t)slot * P + node) * nrhs + r0 + r, acc[r]);
     }
+}
+
+// FP32 upward step with the children's cone values staged in shared memory.
+//
+// The thread layout and the arithmetic are those of k_upward (one thread per (parent
+// slot, node); children in order; the same sum-factorised contraction), but a warp
+// reads cone values from shared memory instead of from L1.  In k_upward the 32 lanes of
+// a warp interpolate, at each child step, from the 2-3 child cones their nodes fall in,
+// so every value load costs 2-3 L1 wavefronts and the kernel is bound by L1 throughput.
+// Here, at each child step, the warp finds the distinct child slots of its lanes
+// (__match_any_sync), copies the values of up to kUpStage of them into its shared-memory
+// stage (coalesced 16-byte or 8-byte loads), and each lane contracts from its cone's
+// copy.  A staged cone takes P * nrhs complex values; the copies follow one another
+// without padding, so the copies start 600 * nrhs (mod 32) banks apart: for nrhs = 1..4
+// the same node of up to four cones lies in disjoint banks, and a warp's load is one
+// shared-memory wavefront whichever of the staged cones its lanes read.  Lanes whose
+// cone is beyond the first kUpStage distinct ones (rare) read from global memory.  Every
+// lane sums its children in the same order with the same operations as k_upward.
+// nrhs <= R <= 4.
+constexpr int kUpStage = 4;
+constexpr int kUpWarps = 4;
+
+template <int R, int PS, int PA>
+__device__ __forceinline__ void contract_staged(const float2 *s, int nrhs, const float *ws, const float *wt,
+                                                const float *wp, cpx<float> *out)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = {0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < PS; ++a) {
+        cpx<float> mid[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) mid[r] = {0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < PA; ++b) {
+            cpx<float> in[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) in[r] = {0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < PA; ++c) {
+                const int idx = (a * PA + b) * PA + c;
+                if (R == 4 && nrhs == 4) {
+                    const float4 v01 = reinterpret_cast<const float4 *>(s)[idx * 2];
+                    const float4 v23 = reinterpret_cast<const float4 *>(s)[idx * 2 + 1];
+                    const float v[8] = {v01.x, v01.y, v01.z, v01.w, v23.x, v23.y, v23.z, v23.w};
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        in[r].x += wp[c] * v[2 * r];
+                        in[r].y += wp[c] * v[2 * r + 1];
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r < nrhs) {
+                            const float2 v = s[idx * nrhs + r];
+                            in[r].x += wp[c] * v.x;
+                            in[r].y += wp[c] * v.y;
+                        }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) { mid[r].x += wt[b] * in[r].x; mid[r].y += wt[b] * in[r].y; }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) { out[r].x += ws[a] * mid[r].x; out[r].y += ws[a] * mid[r].y; }
+    }
+}
+
+template <int R, int PS, int PA, bool TAB>
+__global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int d, int nrhs)
+{
+    constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) float2 s_up_stage[];
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = t < (int64_t)Lp.nact * P;
+    if (__all_sync(kFull, !valid)) return;  // whole warps past the end
+    const int slot = valid ? (int)(t / P) : 0, node = valid ? (int)(t % P) : 0;
+    const int j = valid ? Lp.act_box[slot] : 0;
+    const int pcone = valid ? Lp.act_cone[slot] : 0;
+    const UpEntry<float, NW> *tab = nullptr;
+    if constexpr (TAB) {
+        if (valid) {
+            const int row = table_row(L.ubits, L.urank, pcone);
+            if (row < 0) { atomicAdd(pd.err, 1); valid = false; }
+            else tab = (const UpEntry<float, NW> *)L.utab + (size_t)row * 8 * P + node;
+        }
+    }
+    const int k0 = valid ? Lp.child_start[j] : 0;
+    const int nch = valid ? Lp.child_start[j + 1] - k0 : 0;
+    const int maxch = __reduce_max_sync(kFull, nch);
+    const int vals = P * nrhs;  // complex values per staged cone
+    float2 *stg = s_up_stage + (size_t)warp * kUpStage * vals;
+    cpx<float> acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = {0.f, 0.f};
+    for (int kk = 0; kk < maxch; ++kk) {
+        int sl = -1;
+        float w[NW];
+        cpx<float> f = {0.f, 0.f};
+        if (kk < nch) {
+            const int k = k0 + kk;
+            const int oct = (int)(L.key[k] & 7u);
+            int cone;
+            if constexpr (TAB) {
+                const UpEntry<float, NW> &e = tab[(size_t)oct * P];
+#pragma unroll
+                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
+                f = {e.fr, e.fi};
+                cone = e.cone;
+            } else if (L.ucache) {
+                const UpEntry<float, NW> &e =
+                    ((const UpEntry<float, NW> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * nch + kk];
+#pragma unroll
+                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
+                f = {e.fr, e.fi};
+                cone = e.cone;
+            } else {
+                cone = up_geometry<float, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
+            }
+            sl = cone_slot(L, k, cone);
+            if (sl < 0) atomicAdd(pd.err, 1);
+        }
+        // the warp's distinct child slots; the first kUpStage are staged
+        const unsigned same = __match_any_sync(kFull, sl);
+        const int leader = __ffs(same) - 1;
+        const unsigned leaders = __ballot_sync(kFull, lane == leader && sl >= 0);
+        const int mine = sl >= 0 ? __popc(leaders & ((1u << leader) - 1u)) : -1;
+        const int nst = min(__popc(leaders), kUpStage);
+        unsigned rem = leaders;
+        for (int g = 0; g < nst; ++g) {
+            const int src = __ffs(rem) - 1;
+            rem &= rem - 1u;
+            const int gsl = __shfl_sync(kFull, sl, src);
+            const float2 *from = (const float2 *)L.F + (size_t)gsl * vals;
+            float2 *to = stg + (size_t)g * vals;
+            if ((vals & 1) == 0) {
+                for (int e = lane; e < vals / 2; e += 32)
+                    reinterpret_cast<float4 *>(to)[e] = __ldg(reinterpret_cast<const float4 *>(from) + e);
+            } else {
+                for (int e = lane; e < vals; e += 32) to[e] = __ldg(from + e);
+            }
+        }
+        __syncwarp();
+        if (sl >= 0) {
+            cpx<float> val[R];
+            if (mine < kUpStage) contract_staged<R, PS, PA>(stg + (size_t)mine * vals, nrhs, w, w + PS, w + PS + PA, val);
+            else contract<float, R, PS, PA>(L.F, (size_t)sl * P, nrhs, 0, w, w + PS, w + PS + PA, val);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cpx<float> m = cmul(f, val[r]);
+                acc[r].x += m.x;
+                acc[r].y += m.y;
+            }
+        }
+        __syncwarp();  // the stage is read before the next child step overwrites it
+    }
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r < nrhs) st<float>(Lp.F, ((size_t)slot * P + node) * nrhs + r, acc[r]);
+    }
+}
+
+// Launch of the upward step d -> d-1: the staged kernel for FP32 values with up to 4
+// right-hand sides per pass (flags bit 9 selects k_upward, for comparison tests), else
+// k_upward.
+template <typename T, int R, int PS, int PA>
+inline void launch_upward(const PlanDev &pd, int d, int nrhs, int64_t np, cudaStream_t st)
+{
+    if constexpr (sizeof(T) == 4 && R <= 4) {
+        if (nrhs <= R && !(pd.flags & 512)) {
+            constexpr int P = PS * PA * PA;
+            const size_t smem = (size_t)kUpWarps * kUpStage * P * nrhs * sizeof(float2);
+            if (pd.lev[d].utab)
+                k_upward_staged<R, PS, PA, true><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, smem, st>>>(pd, d, nrhs);
+            else
+                k_upward_staged<R, PS, PA, false><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, smem, st>>>(pd, d, nrhs);
+            return;
+        }
+    }
+    if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+    else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1049,7 +1246,6 @@ __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const vo
 // ---------------------------------------------------------------------------------
 // Host launcher
 // ---------------------------------------------------------------------------------
-inline int grid_for(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 template <typename T, int R, int PS, int PA>
 cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *us, int mode, cudaStream_t st,
@@ -1070,8 +1266,7 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
                 int64_t np = (int64_t)pd.lev[d - 1].nact * P;
                 if (np == 0) continue;
                 NvtxRange range("upward", d);
-                if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
-                else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+                launch_upward<T, R, PS, PA>(pd, d, nrhs, np, st);
                 ++nl;
             }
             tm.mark(STAGE_UPWARD, nl, st);
@@ -1105,10 +1300,7 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
             tm.mark(STAGE_EVAL, 1, st);
             if (d > 3) {
                 int64_t np = (int64_t)pd.lev[d - 1].nact * P;
-                if (np > 0) {
-                    if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
-                    else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
-                }
+                if (np > 0) launch_upward<T, R, PS, PA>(pd, d, nrhs, np, st);
                 tm.mark(STAGE_UPWARD, np > 0, st);
             }
         }
@@ -1252,7 +1444,7 @@ __global__ void __launch_bounds__(128) k_build_tcache(PlanDev pd, int d)
         const int k = L.cous[e];
         const double *ck = L.center + 3 * (size_t)k;
         double vx = __dsub_rn(x, ck[0]), vy = __dsub_rn(y, ck[1]), vz = __dsub_rn(z, ck[2]);
-        ConeGeom g = cone_of_fast(L, vx, vy, vz);
+        ConeGeom g = sizeof(T) == 8 ? cone_of_fast(L, vx, vy, vz) : cone_of_mixed(L, vx, vy, vz);
         int sl = cone_slot(L, k, g.cone);
         if (sl < 0) { atomicAdd(pd.err, 1); sl = 0; }
         if constexpr (sizeof(T) == 8) {

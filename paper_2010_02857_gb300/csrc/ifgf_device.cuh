@@ -167,6 +167,83 @@ __device__ __forceinline__ ConeGeom cone_of_fast(const LevelDev &L, double vx, d
     return o;
 }
 
+// Cone cell for the FP32 value path, with FP64 only where the value path needs it.
+// r, 1/r, s / Delta_s and rho are formed in FP64 (1/r and 1/rho from FP32 estimates and
+// one FP64 Newton step each, relative error < 1e-13): the local coordinates need them to
+// ~1e-10.  The theta and phi cells are decided in FP32 instead: v_z/r and v_x/rho are
+// estimated to within 6e-7 (FP32 rounding of the operands, of the product and of the
+// FP32 reciprocal square root) and compared with FP32 copies of the boundary cosines
+// (rounding 6e-8).  When an estimate lies farther than 2e-6 from both boundaries that
+// decide its cell, every comparison has the sign the correctly rounded path finds;
+// otherwise, and for a radial quotient within 1e-11 of a boundary or a vector on or
+// near the axis, the correctly rounded cone_of decides.  The cells therefore equal
+// those of cone_of (and of the plan's activation) bit for bit.
+__device__ __forceinline__ int count_le_f(const float *tab, int lo, int hi, float x)
+{
+    // number of k in [lo, hi) with x <= tab[k], tab strictly decreasing
+    int a = lo, b = hi;
+    while (a < b) {
+        int mid = (a + b) >> 1;
+        if (x <= tab[mid]) a = mid + 1; else b = mid;
+    }
+    return a - lo;
+}
+
+__device__ __forceinline__ bool near_edge_f(float x, const float *tab, int k, int lo, int hi)
+{
+    const float m = 2e-6f;
+    return (k - 1 >= lo && fabsf(x - tab[k - 1]) < m) || (k < hi && fabsf(x - tab[k]) < m);
+}
+
+__device__ __forceinline__ ConeGeom cone_of_mixed(const LevelDev &L, double vx, double vy, double vz)
+{
+    const int nc = L.nc, ns = L.ns;
+    const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+    const float rho2f = fx * fx + fy * fy;
+    const float r2f = rho2f + fz * fz;
+    if (!(rho2f > 1e-30f) || !(r2f > 1e-30f) || !(r2f < 1e30f)) return cone_of(L, vx, vy, vz);
+    const double rho2 = vx * vx + vy * vy;
+    const double r2 = rho2 + vz * vz;
+    const float rif = rsqrtf(r2f), hif = rsqrtf(rho2f);
+    double ri = (double)rif;
+    ri = ri * fma(-0.5 * r2, ri * ri, 1.5);
+    double hi = (double)hif;
+    hi = hi * fma(-0.5 * rho2, hi * hi, 1.5);
+    ConeGeom o;
+    o.r = r2 * ri;
+    o.rho = rho2 * hi;
+    const double q = L.hds * ri;
+    o.s_over_ds = q;
+    const double fq = floor(q);
+    const double fr = q - fq;
+    const double mq = 1e-11 * fmax(q, 1.0);
+    bool edge = (fr < mq) || (1.0 - fr < mq);
+    o.g1 = fq < 0.0 ? 0 : (fq > (double)(ns - 1) ? ns - 1 : (int)fq);
+    const float ct = fz * rif;
+    const int m2 = count_le_f(L.coskf, 1, nc, ct);
+    edge = edge || near_edge_f(ct, L.coskf, m2 + 1, 1, nc);
+    o.g2 = m2;
+    const float cp = fx * hif;
+    if (vy >= 0.0) {
+        const int m3 = count_le_f(L.coskf, 1, nc + 1, cp);
+        edge = edge || near_edge_f(cp, L.coskf, m3 + 1, 1, nc + 1);
+        o.g3 = m3;
+    } else {
+        const int m3 = count_le_f(L.coskf, 1, nc, -cp);
+        edge = edge || near_edge_f(-cp, L.coskf, m3 + 1, 1, nc);
+        o.g3 = nc + m3;
+    }
+    if (edge) {
+        ConeGeom e = cone_of(L, vx, vy, vz);
+        e.r = o.r;
+        e.rho = o.rho;
+        e.s_over_ds = q;
+        return e;
+    }
+    o.cone = (o.g1 * nc + o.g2) * (2 * nc) + o.g3;
+    return o;
+}
+
 // Local coordinates with FP32 angles: the polar and azimuthal angles are rotated to
 // the start of their cell in FP64 (no input rounding), and only the in-cell angle,
 // in [0, Delta_theta), goes through FP32 atan2 (relative error ~1e-7 of the in-cell

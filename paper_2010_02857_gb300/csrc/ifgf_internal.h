@@ -54,6 +54,7 @@ struct LevelDev {
     const int *cous = nullptr;
     const double *center = nullptr;    // [nbox][3]
     const double *cosk = nullptr;      // [nc+1]
+    const float *coskf = nullptr;      // [nc+1] the same in FP32 (cell decisions of the FP32 path)
     const double *nodeR = nullptr;     // [ns*Ps]
     const double *sth = nullptr, *cth = nullptr;  // [nc*Pang]
     const double *sph = nullptr, *cph = nullptr;  // [2nc*Pang]
@@ -179,6 +180,7 @@ struct ifgf_plan {
     int precision = IFGF_FP64;
     int max_nrhs = 1;
     int flags = 0;
+    int device = 0;            // the CUDA device current at ifgf_plan_create (owns every buffer)
     double timeout_s = 0;      // host-side wait limit of an evaluation (0: none)
     size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
     bool pingpong = false;     // two alternating level buffers instead of one per level

@@ -13,7 +13,14 @@
 // (2 x N x nrhs complex) and the cone values of every level (sum_d A_d x P x nrhs
 // complex), each rounded up to 256 bytes.  It must fit in
 // IFGF_NOALLOC_SCRATCH_BYTES (64 MiB); larger requests are rejected.
-#include <mutex>
+//
+// Every plan is evaluated by the CUDA-core kernels of its data type in one pass over all
+// nrhs right-hand sides, with every level's cone values resident: FP64 plans by the FP64
+// kernels, IFGF_MIXED and IFGF_BATCHED_BF16 plans by the mixed-precision kernels (the
+// tensor-core path needs buffers this entry point does not have).  A batched plan thus
+// gives the mixed path's result here, which differs from ifgf_apply's tensor-core result
+// by the BF16 operand rounding; plans with two level buffers or right-hand-side chunks
+// give the same operator as ifgf_apply.
 #include <string>
 
 #include "ifgf_internal.h"
@@ -26,44 +33,35 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
                                StageTimer &tm);
 
 #define IFGF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
-#define IFGF_NOALLOC_MAX_DEVICES 64
 
 // One array per device that loads the library, held until the process exits.  Every
 // call shares it: it keeps the previous call's contents, and calls whose work
 // overlaps on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[IFGF_NOALLOC_SCRATCH_BYTES];
 
-// In host code g_noalloc_scratch names a host-side stand-in, not device memory, so
-// the device address is looked up once per device (with that device current) and
-// cached here.
-static void *g_scratch_addr[IFGF_NOALLOC_MAX_DEVICES];
-static std::mutex g_scratch_mu;
-
+// In host code g_noalloc_scratch names a host-side stand-in, not device memory.  Every
+// call looks up the array's device address for the current device (cudaGetSymbolAddress,
+// cheap once the library's device code is loaded) instead of caching it: after a
+// cudaDeviceReset or a new primary context the array may live at another address.
 static cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= IFGF_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
-static bool on_device(const void *ptr)
+// A device (or managed) pointer of the given device.
+static bool on_device(const void *ptr, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -75,8 +73,14 @@ extern "C" ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma, vo
         plan->last_error = "nrhs must be in [1, max_nrhs]";
         return IFGF_EINVAL;
     }
-    if (!on_device(sigma) || !on_device(u)) {
-        plan->last_error = "ifgf_apply_noalloc takes device pointers only";
+    int cur_dev = -1;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess || cur_dev != plan->device) {
+        cudaGetLastError();
+        plan->last_error = "ifgf_apply_noalloc: make the plan's device current";
+        return IFGF_EINVAL;
+    }
+    if (!on_device(sigma, plan->device) || !on_device(u, plan->device)) {
+        plan->last_error = "ifgf_apply_noalloc takes device pointers of the plan's device only";
         return IFGF_EINVAL;
     }
     const size_t eb = ifgf_elem_bytes(plan->precision);

@@ -890,6 +890,11 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         L.cosk = dtab + o_cosk; L.nodeR = dtab + o_R;
         L.sth = dtab + o_sth; L.cth = dtab + o_cth; L.sph = dtab + o_sph; L.cph = dtab + o_cph;
         L.cs_edge = dtab + o_cs;
+        std::vector<float> ftab(tab.begin() + o_cosk, tab.begin() + o_cosk + nc[d] + 1);
+        DALLOC(coskf, float, ftab.size());
+        CK(cudaMemcpyAsync(coskf, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        L.coskf = coskf;
     }
 
     // relevant cones, top-down

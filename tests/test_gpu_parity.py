@@ -187,12 +187,14 @@ def test_upward_tables_match_on_the_fly_geometry(pkg, torch_cuda, precision, tol
     assert a.check() == 0 and b.check() == 0
 
 
-def test_cone_index_fast_path_is_exact_on_cell_boundaries(pkg, torch_cuda):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cone_index_fast_path_is_exact_on_cell_boundaries(pkg, torch_cuda, precision):
     # vectors on and next to every kind of cell boundary (s, theta, phi, the poles):
     # the GPU's correctly rounded path must equal the oracle bit for bit, and the
-    # fast path must equal both
+    # evaluation path of each precision (FP64 estimates; FP32 angle decisions with a
+    # margin) must equal both
     wl, pts, _ = _make((3000, 8, 6, 1, 2))
-    g = pkg.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    g = pkg.Plan(pts, wl.kappa, 6, 3, 5, 1, 2, precision=precision)
     o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
     rng = np.random.default_rng(5)
     for d in range(3, 7):
@@ -200,7 +202,8 @@ def test_cone_index_fast_path_is_exact_on_cell_boundaries(pkg, torch_cuda):
         li = o.level_info(d)
         ns, nc = li["ns"], li["nc"]
         vecs = []
-        eps = [0.0, 1e-16, -1e-16, 1e-14, -1e-14, 1e-12, -1e-12, 1e-11, -1e-11, 1e-9, -1e-9]
+        eps = [0.0, 1e-16, -1e-16, 1e-14, -1e-14, 1e-12, -1e-12, 1e-11, -1e-11, 1e-9, -1e-9,
+               1e-7, -1e-7, 1e-6, -1e-6, 3e-6, -3e-6, 1e-5, -1e-5]
         for _ in range(600):
             m = rng.integers(0, ns + 1)
             k = rng.integers(0, nc + 1)
@@ -558,3 +561,131 @@ def test_autograd_gradient_matches_finite_differences(pkg, torch_cuda):
             fd = (L(xp) - L(xm)) / (2 * h)
             an = grad[m].real if part == 0 else grad[m].imag
             assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + 1e-6 * np.abs(grad).max(), (m, part, fd, an)
+
+
+# ------------------------------------------------------------------------------------
+# Element-wise bounds.  ELEM_* bound max_i |a_i - b_i| / max_i |b_i| for one right-hand
+# side: every output, scaled by the field's largest value (a relative bound per element
+# is not defined where the field passes near zero).
+#   * mixed (FP32 values, FP64 geometry): each output sums ~10^3 FP32-rounded terms per
+#     level (unit roundoff 6e-8) whose magnitudes reach a few times max|u|, through
+#     interpolants of Lebesgue constant below 8: 1e-4.
+#   * batched (BF16 hi+lo operands, FP32 accumulate): each operand keeps 16 significant
+#     bits (relative error 2^-17 per operand, 2^-16 for the dropped lo*lo term), which
+#     the interpolant's Lebesgue constant (< 8) and the up to 7 levels carry to the
+#     outputs: 2e-3 per element, and 2e-4 relative l2 per right-hand side.
+# ------------------------------------------------------------------------------------
+ELEM_MIXED = 1e-4
+ELEM_BATCHED = 2e-3
+
+
+def _tree_and_cones_equal(g, o, D):
+    H1, corner = g.geometry()
+    oH1, ocorner = o.geometry()
+    assert H1 == oH1 and np.array_equal(corner, ocorner)
+    assert np.array_equal(g.perm(), o.perm())
+    for d in range(1, D + 1):
+        gk, gs = g.boxes(d)
+        ok, os_ = o.boxes(d)
+        assert np.array_equal(gk, ok) and np.array_equal(gs, os_), d
+    for d in range(3, D + 1):
+        gs, gl = g.cousins(d)
+        os_, ol = o.cousins(d)
+        assert np.array_equal(gs, os_) and np.array_equal(gl, ol), d
+        ga, gc = g.active(d)
+        oa, oc = o.active(d)
+        assert np.array_equal(ga, oa) and np.array_equal(gc, oc), d
+
+
+@pytest.mark.parametrize("kind", wi.DEGENERATE)
+def test_degenerate_geometries_match_oracle(pkg, torch_cuda, kind):
+    # two points, collinear points, a flat disc and two far-apart clusters: bounding
+    # cubes with zero extent along some axes, clamped integer coordinates, points on the
+    # cone axes and mostly empty boxes.  Tree and cones bit-exact; FP64 forward and
+    # adjoint to 1e-10 of the oracle's IFGF, mixed to the element-wise FP32 bound.
+    torch = torch_cuda
+    pts, kappa, D = wi.degenerate_points(kind)
+    n = len(pts)
+    dp = torch.from_numpy(pts).cuda()
+    g = pkg.Plan(dp, kappa, D, 3, 5, 1, 2)
+    o = oracle.Plan(pts, kappa, D, 3, 5, 1, 2)
+    _tree_and_cones_equal(g, o, D)
+    sig = wi.complex_normal(5, (1, n))
+    v = wi.complex_normal(6, (1, n))
+    uo, wo = o.apply(sig), o.apply_adjoint(v)
+    u = g.apply(torch.from_numpy(sig).cuda()).cpu().numpy()
+    w = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert maxrel(u, uo) < 1e-10, maxrel(u, uo)
+    assert maxrel(w, wo) < 1e-10, maxrel(w, wo)
+    m = pkg.Plan(dp, kappa, D, 3, 5, 1, 2, precision="mixed")
+    um = m.apply(torch.from_numpy(sig).cuda()).cpu().numpy()
+    wm = m.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert maxrel(um, uo) < ELEM_MIXED, maxrel(um, uo)
+    assert maxrel(wm, wo) < ELEM_MIXED, maxrel(wm, wo)
+    assert g.check() == 0 and m.check() == 0
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_mixed_elementwise_vs_oracle(pkg, torch_cuda, case):
+    # the mixed path, forward and adjoint, every output against the FP64 oracle IFGF
+    torch = torch_cuda
+    wl, pts, _ = _make(case)
+    n, nl, D, ns, nc = case
+    sig = wi.complex_normal(80, (3, n))
+    g = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, D, 3, 5, ns, nc, precision="mixed", max_nrhs=3)
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    s = torch.from_numpy(sig).cuda()
+    u, uo = g.apply(s).cpu().numpy(), o.apply(sig)
+    w, wo = g.apply_adjoint(s).cpu().numpy(), o.apply_adjoint(sig)
+    for r in range(3):
+        assert maxrel(u[r], uo[r]) < ELEM_MIXED, (r, maxrel(u[r], uo[r]))
+        assert maxrel(w[r], wo[r]) < ELEM_MIXED, (r, maxrel(w[r], wo[r]))
+    assert g.check() == 0
+
+
+@pytest.mark.parametrize("nrhs", [2, 16, 64])
+def test_batched_every_rhs_elementwise_vs_oracle(pkg, torch_cuda, nrhs):
+    # the tensor-core path against the FP64 oracle IFGF, right-hand side by right-hand
+    # side: every output within ELEM_BATCHED and each field within 2e-4 relative l2;
+    # the adjoint (run by the mixed kernels) within ELEM_MIXED
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    sig = wi.complex_normal(160 + nrhs, (nrhs, wl.n))
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 3, 5, 1, 2, max_nrhs=nrhs, precision="batched")
+    o = oracle.Plan(pts, wl.kappa, 5, 3, 5, 1, 2)
+    s = torch.from_numpy(sig).cuda()
+    ub, uo = b.apply(s).cpu().numpy(), o.apply(sig)
+    for r in range(nrhs):
+        assert maxrel(ub[r], uo[r]) < ELEM_BATCHED, (r, maxrel(ub[r], uo[r]))
+        assert rel(ub[r], uo[r]) < 2e-4, (r, rel(ub[r], uo[r]))
+    wb, wo = b.apply_adjoint(s).cpu().numpy(), o.apply_adjoint(sig)
+    for r in range(nrhs):
+        assert maxrel(wb[r], wo[r]) < ELEM_MIXED, (r, maxrel(wb[r], wo[r]))
+    assert b.check() == 0
+
+
+@pytest.mark.parametrize("nrhs,flags", [(1, 0), (2, 0), (3, 0), (4, 0), (4, 2), (4, 8 | 32)])
+def test_staged_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
+    # the FP32 upward step with child cone values staged in shared memory (default) and
+    # the kernel reading them from L1 (flags bit 9) sum every parent node over the same
+    # children in the same order with the same operations: equal cone values at every
+    # level; tabled (default) and on-the-fly geometry (bit 1); two-level buffers without
+    # caches (bits 3 and 5)
+    torch = torch_cuda
+    wl, pts, _ = _make((6000, 6, 6, 1, 2))
+    sig = wi.complex_normal(200 + nrhs, (nrhs, wl.n))
+    kw = dict(max_nrhs=nrhs, precision="mixed")
+    a = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, flags=flags, **kw)
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, flags=flags | 512, **kw)
+    s = torch.from_numpy(sig).cuda().to(torch.complex64)
+    ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
+    assert maxrel(ua, ub) < 1e-6, maxrel(ua, ub)
+    if not flags & 8:
+        for d in range(3, 7):
+            va, vb = a.values(d, nrhs), b.values(d, nrhs)
+            assert maxrel(va, vb) < 1e-6, (d, maxrel(va, vb))
+    o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
+    uo = o.apply(sig)
+    for r in range(nrhs):
+        assert maxrel(ua[r], uo[r]) < ELEM_MIXED, (r, maxrel(ua[r], uo[r]))
+    assert a.check() == 0 and b.check() == 0

@@ -455,26 +455,12 @@ def test_ifgf_matches_direct(n, nl, D, ns, nc, tol):
         assert err < tol, err
 
 
-def _degenerate(kind):
-    u = wi.uniform(77, 0, 20000)
-    if kind == "two points":      # a cube of side 0.3, the points in non-neighbouring leaves
-        return np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1]]), 2 * math.pi, 3
-    if kind == "line":            # collinear along z: zero-extent bounding box in x and y
-        z = np.sort(u[:1200]) * 2 - 1
-        return np.stack([np.zeros(1200), np.zeros(1200), z], 1), 4 * math.pi, 5
-    if kind == "disc":            # coplanar, z = 0
-        r, t = np.sqrt(u[:1500]), 2 * math.pi * u[1500:3000]
-        return np.stack([r * np.cos(t), r * np.sin(t), np.zeros(1500)], 1), 4 * math.pi, 5
-    s = wi.fibonacci_sphere(800) * 0.2   # two clusters far apart: most boxes empty
-    return np.concatenate([s, s + np.array([3.0, 2.0, -1.0])]), 2 * math.pi, 6
-
-
-@pytest.mark.parametrize("kind", ["two points", "line", "disc", "clusters"])
+@pytest.mark.parametrize("kind", wi.DEGENERATE)
 def test_ifgf_on_degenerate_geometries(kind):
     # flat, collinear, tiny and clustered point sets: the bounding cube, the clamp of
     # the integer coordinates and the cone cells (points near the cone axis) still give
     # the direct sum to 1e-3, forward and adjoint
-    pts, kappa, D = _degenerate(kind)
+    pts, kappa, D = wi.degenerate_points(kind)
     sig = wi.complex_normal(5, (1, len(pts)))
     P = oracle.Plan(pts, kappa, D, 3, 5, 1, 2)
     u, w = P.apply(sig), P.apply_adjoint(sig)

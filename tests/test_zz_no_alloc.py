@@ -31,22 +31,55 @@ def _call(pkg, plan, sigma, u, nrhs, torch):
     return rc
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
-def test_noalloc_matches_apply_on_two_calls(precision, tol):
+@pytest.mark.parametrize("precision,flags,tol", [("fp64", 0, 1e-12), ("mixed", 0, 1e-6),
+                                                 ("fp64", 8 | 16, 1e-12), ("mixed", 8 | 16, 1e-6)])
+def test_noalloc_matches_apply_on_two_calls(precision, flags, tol):
+    # flags 8 | 16: a plan with two alternating level buffers that applies 2 right-hand
+    # sides per pass; the allocation-free call runs all 4 in one pass with every level
+    # resident in its scratch, and must give the same operator
     torch, pkg = _setup()
-    wl = wi.small_sphere(2400, 3, 4, leaf_ns=2, leaf_nc=4, nrhs=2)
+    nrhs = 4
+    wl = wi.small_sphere(2400, 3, 4, leaf_ns=2, leaf_nc=4, nrhs=nrhs)
     pts = torch.from_numpy(wl.points()).cuda()
-    plan = pkg.Plan(pts, wl.kappa, 4, 3, 5, 2, 4, max_nrhs=2, precision=precision)
+    plan = pkg.Plan(pts, wl.kappa, 4, 3, 5, 2, 4, max_nrhs=nrhs, precision=precision, flags=flags)
+    if flags:
+        assert plan.stats()["pingpong"] == 1 and plan.stats()["rhs_chunk"] == 2
     sig = torch.from_numpy(wl.densities()).to(plan.complex_dtype).cuda().contiguous()
     ref = plan.apply(sig).cpu().numpy()
     for call in range(2):
         u = torch.full_like(sig, complex(float("nan"), float("nan")))
-        assert _call(pkg, plan, sig, u, 2, torch) == 0
+        assert _call(pkg, plan, sig, u, nrhs, torch) == 0
         torch.cuda.synchronize()
         got = u.cpu().numpy()
-        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
-        assert err <= tol, (call, err)
+        for r in range(nrhs):
+            err = np.max(np.abs(got[r] - ref[r])) / np.max(np.abs(ref[r]))
+            assert err <= tol, (call, r, err)
     assert plan.check() == 0
+
+
+def test_noalloc_batched_plan_runs_the_mixed_kernels():
+    # a tensor-core (batched) plan is evaluated here by the mixed-precision CUDA-core
+    # kernels: equal to a mixed plan's ifgf_apply up to FP32 rounding, and to the batched
+    # plan's own ifgf_apply up to the BF16 operand rounding of the tensor-core path
+    torch, pkg = _setup()
+    nrhs = 4
+    wl = wi.small_sphere(3000, 4, 4, leaf_ns=2, leaf_nc=4, nrhs=nrhs)
+    pts = torch.from_numpy(wl.points()).cuda()
+    b = pkg.Plan(pts, wl.kappa, 4, 3, 5, 2, 4, max_nrhs=nrhs, precision="batched")
+    m = pkg.Plan(pts, wl.kappa, 4, 3, 5, 2, 4, max_nrhs=nrhs, precision="mixed")
+    sig = torch.from_numpy(wl.densities()).to(torch.complex64).cuda().contiguous()
+    ref_m = m.apply(sig).cpu().numpy()
+    ref_b = b.apply(sig).cpu().numpy()
+    for call in range(2):
+        u = torch.full_like(sig, complex(float("nan"), float("nan")))
+        assert _call(pkg, b, sig, u, nrhs, torch) == 0
+        torch.cuda.synchronize()
+        got = u.cpu().numpy()
+        for r in range(nrhs):
+            scale = np.max(np.abs(ref_m[r]))
+            assert np.max(np.abs(got[r] - ref_m[r])) <= 1e-5 * scale, (call, r)
+            assert np.max(np.abs(got[r] - ref_b[r])) <= 2e-3 * scale, (call, r)
+    assert b.check() == 0 and m.check() == 0
 
 
 def test_noalloc_second_plan_and_scratch_limit():
