@@ -49,6 +49,12 @@ def lib():
             L.oracle_direct_adjoint.argtypes = [i64, P, d, i, P, i64, P, P]
             L.oracle_plan_create.argtypes = [i64, P, d, i, i, i, i, i]
             L.oracle_plan_create.restype = P
+            L.oracle_plan_create_adaptive.argtypes = [i64, P, d, i, i, i, i, i, i64]
+            L.oracle_plan_create_adaptive.restype = P
+            L.oracle_get_box_ends.argtypes = [P, i, P, P]
+            L.oracle_get_near.argtypes = [P, i, P, P, P]
+            L.oracle_get_near.restype = i64
+            L.oracle_get_point_levels.argtypes = [P, P]
             L.oracle_plan_destroy.argtypes = [P]
             L.oracle_apply.argtypes = [P, i, P, P, i]
             L.oracle_apply_adjoint.argtypes = [P, i, P, P, i]
@@ -146,13 +152,17 @@ def num_threads() -> int:
 class Plan:
     """Serial CPU IFGF (Algorithm 1) on a fixed point set."""
 
-    def __init__(self, points, kappa, levels, p_radial=3, p_angular=5, leaf_ns=1, leaf_nc=2):
+    def __init__(self, points, kappa, levels, p_radial=3, p_angular=5, leaf_ns=1, leaf_nc=2, leaf_max=0):
+        """leaf_max > 0 builds the adaptive octree (a box of level >= 3 with at most
+        leaf_max points is a leaf); 0 the uniform one of `levels` levels."""
         self.points = np.ascontiguousarray(points, dtype=np.float64)
         self.n = self.points.shape[0]
         self.kappa = float(kappa)
         self.levels = int(levels)
-        self.h = lib().oracle_plan_create(self.n, _p(self.points), self.kappa, self.levels,
-                                          int(p_radial), int(p_angular), int(leaf_ns), int(leaf_nc))
+        self.leaf_max = int(leaf_max)
+        self.h = lib().oracle_plan_create_adaptive(self.n, _p(self.points), self.kappa, self.levels,
+                                                   int(p_radial), int(p_angular), int(leaf_ns), int(leaf_nc),
+                                                   self.leaf_max)
         if not self.h:
             raise ValueError("oracle_plan_create rejected the input")
         info = np.zeros(6, dtype=np.int64)
@@ -214,6 +224,31 @@ class Plan:
         start = np.zeros(nb + 1, dtype=np.int64)
         lib().oracle_get_boxes(self.h, d, _p(keys), _p(start))
         return keys, start
+
+    def box_ends(self, d: int):
+        """(end, leaf) of the boxes of level d: box b holds the sorted points
+        start[b] .. end[b] - 1; leaf boxes are not subdivided."""
+        nb = self.level_info(d)["nbox"]
+        end = np.zeros(nb, dtype=np.int64)
+        leaf = np.zeros(nb, dtype=np.int64)
+        lib().oracle_get_box_ends(self.h, d, _p(end), _p(leaf))
+        return end, leaf.astype(bool)
+
+    def near(self, d: int):
+        """Near-field point ranges of the leaf boxes of level d >= 3: (start, lo, hi)."""
+        m = lib().oracle_get_near(self.h, d, None, None, None)
+        nb = self.level_info(d)["nbox"]
+        start = np.zeros(nb + 1, dtype=np.int64)
+        lo = np.zeros(max(m, 1), dtype=np.int64)
+        hi = np.zeros(max(m, 1), dtype=np.int64)
+        lib().oracle_get_near(self.h, d, _p(start), _p(lo), _p(hi))
+        return start, lo[:m], hi[:m]
+
+    def point_levels(self):
+        """Leaf level of every point, in sorted (Morton) order."""
+        out = np.zeros(self.n, dtype=np.int64)
+        lib().oracle_get_point_levels(self.h, _p(out))
+        return out
 
     def neighbors(self, d: int):
         li = self.level_info(d)

@@ -192,7 +192,12 @@ typedef struct {
     /* boxes of one level, in ascending Morton order */
     int64_t nbox;
     uint64_t *key;     /* Morton key of the box's integer coordinate */
-    int64_t *start;    /* [nbox+1] range of sorted points in the box */
+    int64_t *start;    /* [nbox+1] first sorted point of the box (start[nbox] = n) */
+    int64_t *end;      /* [nbox] one past its last point: start[b+1] in a uniform tree; in
+                        * an adaptive tree the points of coarser leaves lie between boxes */
+    unsigned char *leaf; /* [nbox] the box is a leaf (not subdivided) */
+    int64_t *near_start, *near_lo, *near_hi; /* leaf boxes: CSR of the point ranges of
+                        * the near field of their targets, ascending (reading R13) */
     int64_t *parent;   /* index of the parent box at level d-1 (level >= 2) */
     int64_t *child0;   /* [nbox+1] first child at level d+1 (level < D) */
     int64_t *nbr_start, *nbr;   /* neighbours N B (includes the box itself) */
@@ -221,6 +226,8 @@ typedef struct {
     int64_t *perm;   /* sorted position -> user index */
     double *xs;      /* sorted points [n][3] */
     uint64_t *leafkey;
+    int64_t leaf_max; /* adaptive tree: a box with at most leaf_max points is a leaf (0: uniform) */
+    int *ptlev;      /* [n] level of the leaf box of each sorted point */
     double ts[64], ta[64]; /* Chebyshev nodes for P_s and P_ang */
     olevel lev[ORACLE_MAXLEV + 1];
     int nrhs_F;
@@ -416,7 +423,8 @@ static int64_t find_slot(const olevel *L, int64_t b, int64_t cone)
 
 static void free_level(olevel *L)
 {
-    free(L->key); free(L->start); free(L->parent); free(L->child0);
+    free(L->key); free(L->start); free(L->end); free(L->leaf); free(L->parent); free(L->child0);
+    free(L->near_start); free(L->near_lo); free(L->near_hi);
     free(L->nbr_start); free(L->nbr); free(L->cous_start); free(L->cous);
     free(L->cosk); free(L->nodeR); free(L->sth); free(L->cth); free(L->sph); free(L->cph);
     free(L->act_start); free(L->act_cone); free(L->F); free(L->Fadj);
@@ -428,7 +436,7 @@ void oracle_plan_destroy(void *h)
     oplan *p = h;
     if (!p) return;
     for (int d = 0; d <= ORACLE_MAXLEV; ++d) free_level(&p->lev[d]);
-    free(p->perm); free(p->xs); free(p->leafkey);
+    free(p->perm); free(p->xs); free(p->leafkey); free(p->ptlev);
     free(p);
 }
 
@@ -454,15 +462,23 @@ static int64_t sort_unique(int64_t *v, int64_t n)
     return m;
 }
 
+static int cmp_range(const void *a, const void *b)
+{
+    const int64_t *x = a, *y = b;
+    return x[0] < y[0] ? -1 : (x[0] > y[0]);
+}
+
 /*
- * Build the plan.  pts: [n][3] user order.  Returns NULL on invalid input
- * (n < 2, D < 3, D > 22, P < 1, kappa < 0, non-finite coordinates).
+ * Build the plan.  pts: [n][3] user order.  leaf_max = 0 builds the uniform octree of
+ * D levels (Sec. 3.3.1); leaf_max > 0 the adaptive one of reading R13: a box of level
+ * >= 3 with at most leaf_max points is not subdivided.  Returns NULL on invalid input
+ * (n < 2, D < 3, D > 22, P < 1, kappa < 0, leaf_max < 0, non-finite coordinates).
  */
-void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int Ps, int Pang,
-                         int leaf_ns, int leaf_nc)
+static void *plan_create(int64_t n, const double *pts, double kappa, int D, int Ps, int Pang,
+                         int leaf_ns, int leaf_nc, int64_t leaf_max)
 {
     if (n < 2 || D < 3 || D > ORACLE_MAXLEV || Ps < 1 || Pang < 1 || Ps > 64 || Pang > 64 ||
-        kappa < 0 || leaf_ns < 1 || leaf_nc < 1)
+        kappa < 0 || leaf_ns < 1 || leaf_nc < 1 || leaf_max < 0)
         return NULL;
     for (int64_t i = 0; i < 3 * n; ++i)
         if (!isfinite(pts[i])) return NULL;
@@ -511,24 +527,42 @@ void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int 
     }
     free(ki);
 
-    /* relevant boxes per level: unique level keys of the sorted points */
+    /* relevant boxes per level: unique level keys of the sorted points.  In the
+     * adaptive tree (reading R13) a box exists when its parent exists and is not a
+     * leaf; a box is a leaf at level D, or at a level >= 3 when it holds at most
+     * leaf_max points.  The points of a level's boxes are contiguous per box; the
+     * points of coarser leaves lie between them (start/end per box). */
+    p->leaf_max = leaf_max;
+    p->ptlev = malloc((size_t)n * sizeof(int));
+    for (int64_t j = 0; j < n; ++j) p->ptlev[j] = D;
     for (int d = 1; d <= D; ++d) {
         olevel *L = &p->lev[d];
         int sh = 3 * (D - d);
         int64_t nb = 0;
         for (int64_t j = 0; j < n; ++j)
-            if (j == 0 || (p->leafkey[j] >> sh) != (p->leafkey[j - 1] >> sh)) nb++;
+            if (p->ptlev[j] >= d && (j == 0 || p->ptlev[j - 1] < d || (p->leafkey[j] >> sh) != (p->leafkey[j - 1] >> sh)))
+                nb++;
         L->nbox = nb;
-        L->key = malloc((size_t)nb * sizeof(uint64_t));
+        L->key = malloc((size_t)(nb > 0 ? nb : 1) * sizeof(uint64_t));
         L->start = malloc((size_t)(nb + 1) * sizeof(int64_t));
-        int64_t b = 0;
-        for (int64_t j = 0; j < n; ++j)
-            if (j == 0 || (p->leafkey[j] >> sh) != (p->leafkey[j - 1] >> sh)) {
+        L->end = malloc((size_t)(nb > 0 ? nb : 1) * sizeof(int64_t));
+        L->leaf = malloc((size_t)(nb > 0 ? nb : 1));
+        int64_t b = -1;
+        for (int64_t j = 0; j < n; ++j) {
+            if (p->ptlev[j] < d) continue;
+            if (b < 0 || p->ptlev[j - 1] < d || (p->leafkey[j] >> sh) != (p->leafkey[j - 1] >> sh)) {
+                ++b;
                 L->key[b] = p->leafkey[j] >> sh;
                 L->start[b] = j;
-                b++;
             }
+            L->end[b] = j + 1;
+        }
         L->start[nb] = n;
+        for (b = 0; b < nb; ++b) {
+            L->leaf[b] = d == D || (leaf_max > 0 && d >= 3 && L->end[b] - L->start[b] <= leaf_max);
+            if (L->leaf[b] && d < D)
+                for (int64_t j = L->start[b]; j < L->end[b]; ++j) p->ptlev[j] = d;
+        }
     }
     /* parent / children */
     for (int d = 2; d <= D; ++d) {
@@ -602,6 +636,46 @@ void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int 
         L->cous = list.v;
     }
 
+    /* near-field ranges of every leaf box B of level l (reading R13): the points of all
+     * neighbours of B at level l, and for each level d = 3 .. l-1 the points of the leaf
+     * neighbours of B's ancestor at level d.  With leaves on level D only (the uniform
+     * tree) these are the level-D neighbours of Algorithm 1's direct evaluations.  The
+     * relation is symmetric, so the adjoint's direct sums use the same ranges. */
+    for (int l = 3; l <= D; ++l) {
+        olevel *L = &p->lev[l];
+        L->near_start = malloc((size_t)(L->nbox + 1) * sizeof(int64_t));
+        ivec lo = {0}, hi = {0};
+        for (int64_t b = 0; b < L->nbox; ++b) {
+            L->near_start[b] = lo.n;
+            if (!L->leaf[b]) continue;
+            ivec rg = {0};
+            for (int64_t e = L->nbr_start[b]; e < L->nbr_start[b + 1]; ++e) {
+                ipush(&rg, L->start[L->nbr[e]]);
+                ipush(&rg, L->end[L->nbr[e]]);
+            }
+            int64_t a = b;
+            for (int d = l - 1; d >= 3; --d) {
+                a = p->lev[d + 1].parent[a];
+                olevel *La = &p->lev[d];
+                for (int64_t e = La->nbr_start[a]; e < La->nbr_start[a + 1]; ++e) {
+                    int64_t q = La->nbr[e];
+                    if (!La->leaf[q]) continue;
+                    ipush(&rg, La->start[q]);
+                    ipush(&rg, La->end[q]);
+                }
+            }
+            qsort(rg.v, (size_t)(rg.n / 2), 2 * sizeof(int64_t), cmp_range);
+            for (int64_t i = 0; i < rg.n; i += 2) {
+                ipush(&lo, rg.v[i]);
+                ipush(&hi, rg.v[i + 1]);
+            }
+            free(rg.v);
+        }
+        L->near_start[L->nbox] = lo.n;
+        L->near_lo = lo.v ? lo.v : malloc(sizeof(int64_t));
+        L->near_hi = hi.v ? hi.v : malloc(sizeof(int64_t));
+    }
+
     /* cone levels (reading R5) and per-level tables */
     const double eta = sqrt(3.0) / 3.0;
     p->lev[D].ns = leaf_ns;
@@ -658,7 +732,7 @@ void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int 
             /* (i) cones containing a surface point of a cousin box */
             for (int64_t e = L->cous_start[k]; e < L->cous_start[k + 1]; ++e) {
                 int64_t cb = L->cous[e];
-                for (int64_t j = L->start[cb]; j < L->start[cb + 1]; ++j)
+                for (int64_t j = L->start[cb]; j < L->end[cb]; ++j)
                     ipush(&ids, cone_of(p, d, p->xs + 3 * j, xk, NULL, NULL));
             }
             /* (ii) cones containing an interpolation point of a relevant parent cone */
@@ -690,6 +764,18 @@ void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int 
         L->nact = tot;
     }
     return p;
+}
+
+void *oracle_plan_create(int64_t n, const double *pts, double kappa, int D, int Ps, int Pang,
+                         int leaf_ns, int leaf_nc)
+{
+    return plan_create(n, pts, kappa, D, Ps, Pang, leaf_ns, leaf_nc, 0);
+}
+
+void *oracle_plan_create_adaptive(int64_t n, const double *pts, double kappa, int D, int Ps, int Pang,
+                                  int leaf_ns, int leaf_nc, int64_t leaf_max)
+{
+    return plan_create(n, pts, kappa, D, Ps, Pang, leaf_ns, leaf_nc, leaf_max);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -736,46 +822,54 @@ int oracle_apply(void *h, int nrhs, const double *sigma_in, double *u_out, int m
     int err = 0;
     int64_t near_pairs = 0;
 
-    /* Direct evaluations on level D: I_k^D at neighbouring surface points
-     * (the pairs with target == source are skipped, Eq. field1). */
+    /* Direct evaluations: I_k at the surface points of the near field of every leaf
+     * box (its level-D neighbours in the uniform tree, Algorithm 1; the ranges of
+     * reading R13 in the adaptive tree); the pairs with target == source are skipped,
+     * Eq. (field1). */
     if (mode & 1) {
-        olevel *L = &p->lev[D];
+        for (int l = 3; l <= D; ++l) {
+            olevel *L = &p->lev[l];
 #pragma omp parallel for schedule(dynamic, 8) reduction(+ : near_pairs)
-        for (int64_t b = 0; b < L->nbox; ++b)
-            for (int64_t i = L->start[b]; i < L->start[b + 1]; ++i) {
-                cplx acc[nrhs];
-                for (int r = 0; r < nrhs; ++r) acc[r] = 0;
-                for (int64_t e = L->nbr_start[b]; e < L->nbr_start[b + 1]; ++e) {
-                    int64_t k = L->nbr[e];
-                    for (int64_t j = L->start[k]; j < L->start[k + 1]; ++j) {
-                        if (j == i) continue;
-                        cplx g = green(p->xs + 3 * i, p->xs + 3 * j, kappa);
-                        for (int r = 0; r < nrhs; ++r) acc[r] += a[j * nrhs + r] * g;
-                        near_pairs++;
-                    }
+            for (int64_t b = 0; b < L->nbox; ++b) {
+                if (!L->leaf[b]) continue;
+                for (int64_t i = L->start[b]; i < L->end[b]; ++i) {
+                    cplx acc[nrhs];
+                    for (int r = 0; r < nrhs; ++r) acc[r] = 0;
+                    for (int64_t e = L->near_start[b]; e < L->near_start[b + 1]; ++e)
+                        for (int64_t j = L->near_lo[e]; j < L->near_hi[e]; ++j) {
+                            if (j == i) continue;
+                            cplx g = green(p->xs + 3 * i, p->xs + 3 * j, kappa);
+                            for (int r = 0; r < nrhs; ++r) acc[r] += a[j * nrhs + r] * g;
+                            near_pairs++;
+                        }
+                    for (int r = 0; r < nrhs; ++r) us[i * nrhs + r] += acc[r];
                 }
-                for (int r = 0; r < nrhs; ++r) us[i * nrhs + r] += acc[r];
             }
+        }
     }
     p->near_pairs = near_pairs;
 
     if (mode & 2) {
-        /* F_k^D at the interpolation points of every relevant level-D cone, Eq. (I_k). */
-        olevel *L = &p->lev[D];
+        /* F_k at the interpolation points of every relevant cone of every leaf box k,
+         * Eq. (I_k): level D in the uniform tree, any level >= 3 in the adaptive one. */
+        for (int l = 3; l <= D; ++l) {
+            olevel *L = &p->lev[l];
 #pragma omp parallel for schedule(dynamic, 4)
-        for (int64_t k = 0; k < L->nbox; ++k) {
-            double xk[3];
-            box_center(p, D, L->key[k], xk);
-            for (int64_t sl = L->act_start[k]; sl < L->act_start[k + 1]; ++sl)
-                for (int node = 0; node < P; ++node) {
-                    double q[3];
-                    node_pos(p, D, L->act_cone[sl], node, xk, q);
-                    cplx *F = L->F + (sl * P + node) * nrhs;
-                    for (int64_t j = L->start[k]; j < L->start[k + 1]; ++j) {
-                        cplx g = analytic_factor(q, xk, p->xs + 3 * j, kappa);
-                        for (int r = 0; r < nrhs; ++r) F[r] += a[j * nrhs + r] * g;
+            for (int64_t k = 0; k < L->nbox; ++k) {
+                if (!L->leaf[k]) continue;
+                double xk[3];
+                box_center(p, l, L->key[k], xk);
+                for (int64_t sl = L->act_start[k]; sl < L->act_start[k + 1]; ++sl)
+                    for (int node = 0; node < P; ++node) {
+                        double q[3];
+                        node_pos(p, l, L->act_cone[sl], node, xk, q);
+                        cplx *F = L->F + (sl * P + node) * nrhs;
+                        for (int64_t j = L->start[k]; j < L->end[k]; ++j) {
+                            cplx g = analytic_factor(q, xk, p->xs + 3 * j, kappa);
+                            for (int r = 0; r < nrhs; ++r) F[r] += a[j * nrhs + r] * g;
+                        }
                     }
-                }
+            }
         }
         for (int d = D; d >= 3; --d) {
             olevel *Ld = &p->lev[d];
@@ -787,7 +881,7 @@ int oracle_apply(void *h, int nrhs, const double *sigma_in, double *u_out, int m
              * the (k, x) pairs of Algorithm 1, each target's terms in ascending k. */
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : cev, err)
             for (int64_t b = 0; b < Ld->nbox; ++b) {
-                for (int64_t i = Ld->start[b]; i < Ld->start[b + 1]; ++i) {
+                for (int64_t i = Ld->start[b]; i < Ld->end[b]; ++i) {
                     for (int64_t e = Ld->cous_start[b]; e < Ld->cous_start[b + 1]; ++e) {
                         int64_t k = Ld->cous[e];
                         double xk[3], loc[3];
@@ -869,24 +963,26 @@ int oracle_apply_adjoint(void *h, int nrhs, const double *v_in, double *w_out, i
     }
     int err = 0;
     if (mode & 1) {
-        /* N^H: source j gathers conj(G(x_i, x_j)) v_i over targets i in the
-         * neighbourhood (the neighbour relation is symmetric). */
-        olevel *L = &p->lev[D];
+        /* N^H: source j gathers conj(G(x_i, x_j)) v_i over the targets i of its own
+         * near-field ranges (the near relation is symmetric). */
+        for (int l = 3; l <= D; ++l) {
+            olevel *L = &p->lev[l];
 #pragma omp parallel for schedule(dynamic, 8)
-        for (int64_t b = 0; b < L->nbox; ++b)
-            for (int64_t j = L->start[b]; j < L->start[b + 1]; ++j) {
-                cplx acc[nrhs];
-                for (int r = 0; r < nrhs; ++r) acc[r] = 0;
-                for (int64_t e = L->nbr_start[b]; e < L->nbr_start[b + 1]; ++e) {
-                    int64_t k = L->nbr[e];
-                    for (int64_t i = L->start[k]; i < L->start[k + 1]; ++i) {
-                        if (i == j) continue;
-                        cplx g = conj(green(p->xs + 3 * i, p->xs + 3 * j, kappa));
-                        for (int r = 0; r < nrhs; ++r) acc[r] += v[i * nrhs + r] * g;
-                    }
+            for (int64_t b = 0; b < L->nbox; ++b) {
+                if (!L->leaf[b]) continue;
+                for (int64_t j = L->start[b]; j < L->end[b]; ++j) {
+                    cplx acc[nrhs];
+                    for (int r = 0; r < nrhs; ++r) acc[r] = 0;
+                    for (int64_t e = L->near_start[b]; e < L->near_start[b + 1]; ++e)
+                        for (int64_t i = L->near_lo[e]; i < L->near_hi[e]; ++i) {
+                            if (i == j) continue;
+                            cplx g = conj(green(p->xs + 3 * i, p->xs + 3 * j, kappa));
+                            for (int r = 0; r < nrhs; ++r) acc[r] += v[i * nrhs + r] * g;
+                        }
+                    for (int r = 0; r < nrhs; ++r) ws[j * nrhs + r] += acc[r];
                 }
-                for (int r = 0; r < nrhs; ++r) ws[j * nrhs + r] += acc[r];
             }
+        }
     }
     if (mode & 2) {
         for (int d = 3; d <= D; ++d) {
@@ -899,7 +995,7 @@ int oracle_apply_adjoint(void *h, int nrhs, const double *v_in, double *w_out, i
                 box_center(p, d, Ld->key[k], xk);
                 for (int64_t e = Ld->cous_start[k]; e < Ld->cous_start[k + 1]; ++e) {
                     int64_t b = Ld->cous[e];
-                    for (int64_t i = Ld->start[b]; i < Ld->start[b + 1]; ++i) {
+                    for (int64_t i = Ld->start[b]; i < Ld->end[b]; ++i) {
                         double loc[3], wsd[64], wt[64], wp[64];
                         int64_t cone = cone_of(p, d, p->xs + 3 * i, xk, NULL, loc);
                         int64_t sl = find_slot(Ld, k, cone);
@@ -952,23 +1048,26 @@ int oracle_apply_adjoint(void *h, int nrhs, const double *v_in, double *w_out, i
                 }
             }
         }
-        /* L^H: each source gathers conj(g(q, x')) Fbar^D over its leaf's cone nodes */
-        olevel *L = &p->lev[D];
+        /* L^H: each source gathers conj(g(q, x')) Fbar over its leaf's cone nodes */
+        for (int l = 3; l <= D; ++l) {
+            olevel *L = &p->lev[l];
 #pragma omp parallel for schedule(dynamic, 4)
-        for (int64_t k = 0; k < L->nbox; ++k) {
-            double xk[3];
-            box_center(p, D, L->key[k], xk);
-            for (int64_t j = L->start[k]; j < L->start[k + 1]; ++j) {
-                cplx acc[nrhs];
-                for (int r = 0; r < nrhs; ++r) acc[r] = 0;
-                for (int64_t sl = L->act_start[k]; sl < L->act_start[k + 1]; ++sl)
-                    for (int node = 0; node < P; ++node) {
-                        double q[3];
-                        node_pos(p, D, L->act_cone[sl], node, xk, q);
-                        cplx g = conj(analytic_factor(q, xk, p->xs + 3 * j, kappa));
-                        for (int r = 0; r < nrhs; ++r) acc[r] += g * L->Fadj[(sl * P + node) * nrhs + r];
-                    }
-                for (int r = 0; r < nrhs; ++r) ws[j * nrhs + r] += acc[r];
+            for (int64_t k = 0; k < L->nbox; ++k) {
+                if (!L->leaf[k]) continue;
+                double xk[3];
+                box_center(p, l, L->key[k], xk);
+                for (int64_t j = L->start[k]; j < L->end[k]; ++j) {
+                    cplx acc[nrhs];
+                    for (int r = 0; r < nrhs; ++r) acc[r] = 0;
+                    for (int64_t sl = L->act_start[k]; sl < L->act_start[k + 1]; ++sl)
+                        for (int node = 0; node < P; ++node) {
+                            double q[3];
+                            node_pos(p, l, L->act_cone[sl], node, xk, q);
+                            cplx g = conj(analytic_factor(q, xk, p->xs + 3 * j, kappa));
+                            for (int r = 0; r < nrhs; ++r) acc[r] += g * L->Fadj[(sl * P + node) * nrhs + r];
+                        }
+                    for (int r = 0; r < nrhs; ++r) ws[j * nrhs + r] += acc[r];
+                }
             }
         }
     }
@@ -1033,6 +1132,35 @@ void oracle_get_boxes(void *h, int d, uint64_t *keys, int64_t *start)
     olevel *L = &p->lev[d];
     memcpy(keys, L->key, (size_t)L->nbox * sizeof(uint64_t));
     memcpy(start, L->start, (size_t)(L->nbox + 1) * sizeof(int64_t));
+}
+
+/* end[nbox] and leaf[nbox] of level d (adaptive trees: the point ranges of the boxes
+ * are [start[b], end[b]) and leaf boxes are not subdivided) */
+void oracle_get_box_ends(void *h, int d, int64_t *end, int64_t *leaf)
+{
+    oplan *p = h;
+    olevel *L = &p->lev[d];
+    for (int64_t b = 0; b < L->nbox; ++b) { end[b] = L->end[b]; leaf[b] = L->leaf[b]; }
+}
+
+/* near-field ranges of the leaf boxes of level d >= 3: start[nbox+1] into lo/hi */
+int64_t oracle_get_near(void *h, int d, int64_t *start, int64_t *lo, int64_t *hi)
+{
+    oplan *p = h;
+    olevel *L = &p->lev[d];
+    int64_t m = L->near_start[L->nbox];
+    if (start) {
+        for (int64_t b = 0; b <= L->nbox; ++b) start[b] = L->near_start[b];
+        for (int64_t e = 0; e < m; ++e) { lo[e] = L->near_lo[e]; hi[e] = L->near_hi[e]; }
+    }
+    return m;
+}
+
+/* leaf level of every point, in sorted (Morton) order */
+void oracle_get_point_levels(void *h, int64_t *lev)
+{
+    oplan *p = h;
+    for (int64_t j = 0; j < p->n; ++j) lev[j] = p->ptlev[j];
 }
 
 void oracle_get_neighbors(void *h, int d, int64_t *start, int64_t *list)

@@ -671,3 +671,132 @@ def test_relevant_cones_rules_i_and_ii_by_set_equality():
     # rule (ii) contributes cones of its own (otherwise the comparison would not test it)
     assert n_ii_only > 100
     assert n_amb < 50
+
+
+# --------------------------------------------------------------------------------------
+# Adaptive octree (reading R13: a box of level >= 3 with at most leaf_max points is a
+# leaf; near field and cousins of mixed-level leaves), checked against the definitions
+# rebuilt in numpy and by brute force over all pairs
+# --------------------------------------------------------------------------------------
+
+ADAPTIVE = [(6, 30), (7, 40)]  # (D, leaf_max): leaves on levels 4..6; 4..6 with level 7 empty
+
+
+def _adaptive_case(D=6, kmax=30):
+    pts = wi.spheroid_points(2000, (0.1, 0.1, 1.0), seed=9)  # uneven leaf occupancy
+    return pts, 4 * math.pi, D, kmax
+
+
+def _np_adaptive_tree(pts, corner, H1, D, leaf_max):
+    """Per level: (keys of the existing boxes, point index sets, leaf flags) and the leaf
+    level of every point, from the definition alone."""
+    n = len(pts)
+    lev = np.full(n, D)
+    out = {}
+    for d in range(1, D + 1):
+        k = _int_coords(pts, corner, H1 / 2 ** (d - 1), 2 ** (d - 1))
+        keys = _morton(k)
+        alive = lev >= d
+        boxes = {}
+        for i in np.nonzero(alive)[0]:
+            boxes.setdefault(int(keys[i]), []).append(i)
+        ks = sorted(boxes)
+        leaf = [d == D or (d >= 3 and len(boxes[q]) <= leaf_max) for q in ks]
+        for q, lf in zip(ks, leaf):
+            if lf and d < D:
+                lev[boxes[q]] = d
+        out[d] = (np.array(ks, dtype=np.uint64), [sorted(boxes[q]) for q in ks], np.array(leaf))
+    return out, lev
+
+
+@pytest.mark.parametrize("D,kmax", ADAPTIVE)
+def test_adaptive_tree_by_definition(D, kmax):
+    pts, kappa, D, kmax = _adaptive_case(D, kmax)
+    P = oracle.Plan(pts, kappa, D, 3, 5, 1, 2, leaf_max=kmax)
+    H1, corner = P.geometry()
+    ref, lev = _np_adaptive_tree(pts, corner, H1, D, kmax)
+    perm = P.perm()
+    assert np.array_equal(P.point_levels(), lev[perm])
+    nleaf_above_D = 0
+    for d in range(1, D + 1):
+        keys, start = P.boxes(d)
+        end, leaf = P.box_ends(d)
+        rk, rsets, rleaf = ref[d]
+        assert np.array_equal(keys, rk), d
+        assert np.array_equal(leaf, rleaf), d
+        for b in range(len(keys)):
+            assert sorted(perm[start[b]:end[b]]) == rsets[b]
+        if d < D:
+            nleaf_above_D += int(leaf.sum())
+    assert nleaf_above_D > 20  # the case has leaves on several levels
+    assert len(set(P.point_levels().tolist())) >= 3
+
+
+@pytest.mark.parametrize("D,kmax", ADAPTIVE)
+def test_adaptive_every_pair_covered_exactly_once(D, kmax):
+    # every ordered pair (x, y != x) is evaluated once: by a direct sum of the near field
+    # (the oracle's ranges) or by the interpolation of exactly one level d, where the
+    # level-d boxes of x and y are cousins (parents adjacent, boxes not) and both points
+    # lie in boxes of that level
+    pts, kappa, D, kmax = _adaptive_case(D, kmax)
+    P = oracle.Plan(pts, kappa, D, 3, 5, 1, 2, leaf_max=kmax)
+    H1, corner = P.geometry()
+    perm = P.perm()
+    n = len(pts)
+    lev = P.point_levels()            # sorted order
+    xs = pts[perm]
+    count = np.zeros((n, n), dtype=np.int32)
+    near = np.zeros((n, n), dtype=bool)
+    for l in range(3, D + 1):
+        keys, start = P.boxes(l)
+        end, leaf = P.box_ends(l)
+        ns, lo, hi = P.near(l)
+        for b in np.nonzero(leaf)[0]:
+            for e in range(ns[b], ns[b + 1]):
+                near[start[b]:end[b], lo[e]:hi[e]] = True
+    count += near
+    for d in range(3, D + 1):
+        k = _int_coords(xs, corner, H1 / 2 ** (d - 1), 2 ** (d - 1))
+        kp = k // 2
+        ok = lev >= d
+        cous = (np.max(np.abs(kp[:, None, :] - kp[None, :, :]), axis=2) <= 1) & \
+               (np.max(np.abs(k[:, None, :] - k[None, :, :]), axis=2) > 1)
+        count += cous & ok[:, None] & ok[None, :]
+    np.fill_diagonal(count, 1)
+    assert np.all(count == 1), np.argwhere(count != 1)[:5]
+    # the near relation is symmetric and is adjacency at the coarser of the two leaf levels
+    assert np.array_equal(near, near.T)
+    m = np.minimum(lev[:, None], lev[None, :])
+    adj = np.zeros((n, n), dtype=bool)
+    for d in range(3, D + 1):
+        k = _int_coords(xs, corner, H1 / 2 ** (d - 1), 2 ** (d - 1))
+        a = np.max(np.abs(k[:, None, :] - k[None, :, :]), axis=2) <= 1
+        adj |= a & (m == d)
+    assert np.array_equal(near, adj)
+
+
+@pytest.mark.parametrize("D,leaf_max", ADAPTIVE + [(6, 100000)])
+def test_adaptive_ifgf_matches_direct(D, leaf_max):
+    # leaf_max = 100000: every box of level 3 is a leaf (no upward step)
+    pts, kappa, D, _ = _adaptive_case(D, leaf_max)
+    sig = wi.complex_normal(17, (2, len(pts)))
+    P = oracle.Plan(pts, kappa, D, 3, 5, 1, 2, leaf_max=leaf_max)
+    u, w = P.apply(sig), P.apply_adjoint(sig)
+    ex, exa = oracle.direct(pts, kappa, sig), oracle.direct_adjoint(pts, kappa, sig)
+    for r in range(2):
+        assert np.linalg.norm(u[r] - ex[r]) / np.linalg.norm(ex[r]) < 1e-3
+        assert np.linalg.norm(w[r] - exa[r]) / np.linalg.norm(exa[r]) < 1e-3
+    v = wi.complex_normal(18, (1, len(pts)))
+    lhs, rhs = np.vdot(v, P.apply(sig[:1])), np.vdot(P.apply_adjoint(v), sig[:1])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_adaptive_without_coarse_leaves_is_the_uniform_plan():
+    # a leaf_max below every box count of levels 3..D-1 leaves the uniform tree
+    wl = wi.small_sphere(3000, 3, 4)
+    pts, sig = wl.points(), wl.densities()
+    a = oracle.Plan(pts, wl.kappa, 4, 3, 5, 1, 2)
+    counts = np.diff(a.boxes(3)[1])
+    b = oracle.Plan(pts, wl.kappa, 4, 3, 5, 1, 2, leaf_max=int(counts.min()) - 1)
+    assert not b.box_ends(3)[1].any()
+    assert np.array_equal(a.apply(sig), b.apply(sig))
