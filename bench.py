@@ -11,6 +11,10 @@ paper's T_acc excludes T_pre; its build time is reported as t_plan_ms.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ifgf|reference]
 
+With N > 1 (one process per GPU under torchrun) the job is a batch of N * nrhs
+right-hand sides split over the ranks (rhs_shard): each rank builds its own plan of the
+same geometry and applies its rows; no data crosses ranks while they evaluate.
+
 --impl reference times the CPU oracle (the direct sum of Eq. field1 on a bounded
 sample of targets, all host cores) on the same workload and metric.
 
@@ -214,10 +218,11 @@ def run_reference(args, wl: wi.Workload):
     tg = wl.target_indices()
     # each step is a bounded sample: at most --ref-targets targets, fewer when one step
     # would take more than about --ref-step-s seconds (the run stays within minutes)
+    m0 = min(len(tg), max(1, oracle.num_threads()))  # one target per host core
     t0 = time.perf_counter()
-    direct(pts, wl.kappa, sig, tg[:4])  # warms the library and sizes the sample
-    per_target = (time.perf_counter() - t0) / 4
-    m = int(min(len(tg), max(4, int(args.ref_targets)), max(4, args.ref_step_s / max(per_target, 1e-9))))
+    direct(pts, wl.kappa, sig, tg[:m0])  # warms the library and sizes the sample
+    per_target = (time.perf_counter() - t0) / m0
+    m = int(min(len(tg), max(m0, int(args.ref_targets)), max(m0, args.ref_step_s / max(per_target, 1e-9))))
     tg = tg[:m]
     times = []
     for _ in range(args.warmup):
@@ -250,10 +255,13 @@ def cpu_baseline(wl: wi.Workload, op: str = "apply", seconds: float = 15.0, u=No
     pts = wl.points()
     sig = wl.densities()
     tg = wl.target_indices()
+    # the oracle runs its targets in parallel over the host cores: size the sample from
+    # a first call with one target per core
+    m0 = min(len(tg), max(1, oracle.num_threads()))
     t0 = time.perf_counter()
-    direct(pts, wl.kappa, sig, tg[:4])
-    per_target = (time.perf_counter() - t0) / 4
-    m = int(min(len(tg), max(8, seconds / max(per_target, 1e-9))))
+    direct(pts, wl.kappa, sig, tg[:m0])
+    per_target = (time.perf_counter() - t0) / m0
+    m = int(min(len(tg), max(m0, seconds / max(per_target, 1e-9))))
     t0 = time.perf_counter()
     ex = direct(pts, wl.kappa, sig, tg[:m])
     t = time.perf_counter() - t0
@@ -312,11 +320,16 @@ def main():
     pts = torch.from_numpy(wl.points()).to(dev)
     t0 = time.perf_counter()
     plan = pkg.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc,
-                    max_nrhs=wl.nrhs, precision=precision)
+                    max_nrhs=wl.nrhs, precision=precision, leaf_max=wl.leaf_max)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
     stats = plan.stats()
-    sig_np = wl.densities().astype(plan.numpy_dtype)
+    # right-hand sides sharded over the ranks: the job is a batch of world * nrhs
+    # right-hand sides of the workload's kind, and rank r applies rows
+    # [r nrhs, (r + 1) nrhs) of it on its own plan (weak scaling; no data crosses ranks)
+    batch = world * wl.nrhs
+    r0, r1 = pkg.rhs_shard(batch, rank, world)
+    sig_np = wl.densities((r0, r1, batch)).astype(plan.numpy_dtype)
     sig = torch.from_numpy(sig_np).to(dev)
     u = torch.empty_like(sig)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -430,8 +443,9 @@ def main():
                 "config": {"workload": wl.name, "op": args.op, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
                            "p_radial": wl.p_radial, "p_angular": wl.p_angular,
                            "leaf_cones": [wl.leaf_ns, wl.leaf_nc], "precision": precision,
+                           "leaf_max": wl.leaf_max,
                            "l2": "flushed between steps (256 MB write)", "launch": "CUDA graph replay",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"rhs-sharded x{world}", "batch_nrhs": batch},
                 "t_plan_ms": t_plan * 1e3, "tiles": tiles,
                 "stage_ms": {k: v["ms"] / calls for k, v in st.items() if v["launches"]},
                 "e2e": {"value": world * n * n * nrhs / e2e_s, "unit": UNIT,

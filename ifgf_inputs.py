@@ -65,6 +65,20 @@ def complex_normal(seed: int, shape) -> np.ndarray:
     return (z[0::2] + 1j * z[1::2]).reshape(shape)
 
 
+def complex_normal_rows(seed: int, nrows: int, ncols: int, r0: int, r1: int) -> np.ndarray:
+    """Rows r0..r1-1 of complex_normal(seed, (nrows, ncols)), generated alone.
+
+    Element f (row-major) of that array is the Box-Muller pair of uniforms 2f and 2f+1
+    of the stream, so a block of rows is a contiguous range of pairs: a rank that owns
+    some rows of a large batch generates only those."""
+    assert 0 <= r0 <= r1 <= nrows
+    f0, cnt = r0 * ncols, (r1 - r0) * ncols
+    u = uniform(seed, 2 * f0, 2 * cnt)
+    rad = np.sqrt(-2.0 * np.log(1.0 - u[0::2]))
+    ang = 2.0 * np.pi * u[1::2]
+    return (rad * np.cos(ang) + 1j * (rad * np.sin(ang))).reshape(r1 - r0, ncols)
+
+
 # --------------------------------------------------------------------------------------
 # Surfaces
 # --------------------------------------------------------------------------------------
@@ -155,14 +169,16 @@ def cube_union_points(n: int, cubes=CUBES, seed: int = 4) -> np.ndarray:
     return np.concatenate(out, axis=0)[:n]
 
 
-def plane_wave_densities(points: np.ndarray, kappa: float, nrhs: int, seed: int) -> np.ndarray:
+def plane_wave_densities(points: np.ndarray, kappa: float, nrhs: int, seed: int, r0: int = 0,
+                         r1: int | None = None) -> np.ndarray:
     """sigma_r(x) = A_r exp(i kappa d_r . x), d_r seeded unit vectors, A_r complex N(0,1).
 
-    Returns complex128 [nrhs, N].
+    Returns complex128 [r1 - r0, N]: right-hand sides r0..r1-1 of the nrhs.
     """
-    d = _unit_directions(seed, 0, nrhs)
-    amp = complex_normal(seed + 0x77, (nrhs,))
-    phase = kappa * (points @ d.T)  # [N, nrhs]
+    r1 = nrhs if r1 is None else r1
+    d = _unit_directions(seed, r0, r1 - r0)
+    amp = complex_normal(seed + 0x77, (nrhs,))[r0:r1]
+    phase = kappa * (points @ d.T)  # [N, r1 - r0]
     return (amp[None, :] * np.exp(1j * phase)).T.copy()
 
 
@@ -231,6 +247,7 @@ class Workload:
     targets: int = 1000
     seed: int = 0
     surface: str = "sphere"
+    leaf_max: int = 0
     description: str = ""
     _points: np.ndarray | None = field(default=None, repr=False)
 
@@ -249,11 +266,14 @@ class Workload:
                 raise ValueError(self.surface)
         return self._points
 
-    def densities(self) -> np.ndarray:
-        """complex128 [nrhs, N]."""
-        if self.surface == "cubes" and self.nrhs > 1:
-            return plane_wave_densities(self.points(), self.kappa, self.nrhs, self.seed + 100)
-        return complex_normal(self.seed + 100, (self.nrhs, self.n))
+    def densities(self, rows=None) -> np.ndarray:
+        """complex128 [nrhs, N]; rows = (r0, r1, batch) gives right-hand sides r0..r1-1 of
+        a batch of `batch` right-hand sides drawn the same way (batch >= nrhs; the first
+        nrhs rows of any batch are this workload's densities)."""
+        r0, r1, batch = rows if rows is not None else (0, self.nrhs, self.nrhs)
+        if self.surface == "cubes" and batch > 1:
+            return plane_wave_densities(self.points(), self.kappa, batch, self.seed + 100, r0, r1)
+        return complex_normal_rows(self.seed + 100, batch, self.n, r0, r1)
 
     def target_indices(self) -> np.ndarray:
         return sample_targets(self.n, self.targets, self.seed + 200)
@@ -287,6 +307,14 @@ WORKLOADS = {
                                   leaf_ns=1, leaf_nc=2, targets=4_096, seed=3, surface="prolate",
                                   precision="mixed",
                                   description="prolate spheroid N=3145728, 128 lambda, D=10, mixed"),
+    # the same spheroid on an adaptive octree of at most the same depth: boxes of level
+    # >= 3 with at most 32 points are leaves (the cone sizes per level are those of the
+    # uniform tree, whose leaf cones are chosen at level 10)
+    "prolate_128lambda_adaptive": Workload("prolate_128lambda_adaptive", 3_145_728, wavelengths_to_kappa(2.0, 128),
+                                           10, leaf_ns=1, leaf_nc=2, targets=4_096, seed=3, surface="prolate",
+                                           precision="mixed", leaf_max=32,
+                                           description="prolate spheroid N=3145728, 128 lambda, adaptive "
+                                                       "octree (leaf_max 32, D <= 10), mixed"),
     # union of three cubes of side 20 wavelengths, 64 plane-wave RHS, D = 8
     "cubes_64rhs": Workload("cubes_64rhs", 1_572_864, 2.0 * math.pi, 8,
                             leaf_ns=1, leaf_nc=2, nrhs=64, targets=2_048, seed=4, surface="cubes",
@@ -299,6 +327,12 @@ WORKLOADS = {
                                 leaf_ns=1, leaf_nc=2, nrhs=64, targets=512, seed=4, surface="cubes",
                                 precision="batched",
                                 description="three-cube union N=98304, 64 RHS (profiling size)"),
+    # Laplace kernel (kappa = 0) on the unit sphere, N = 6,291,456 (the largest sphere of
+    # the paper's Laplace table), D = 8 (about 82 points per leaf box); a fixed number of
+    # cone segments per box at every level, (n_s, n_C) = (3, 6)
+    "sphere_laplace_6M": Workload("sphere_laplace_6M", 6_291_456, 0.0, 8, leaf_ns=3, leaf_nc=6,
+                                  targets=1_000, seed=8, surface="sphere", precision="mixed",
+                                  description="Fibonacci sphere N=6291456, Laplace (kappa=0), D=8, mixed"),
     # unit sphere, diameter 256 wavelengths, D = 9, 8 RHS
     "sphere_256lambda": Workload("sphere_256lambda", 25_165_824, wavelengths_to_kappa(2.0, 256), 9,
                                  leaf_ns=3, leaf_nc=6, nrhs=8, targets=1_024, seed=5, surface="sphere",

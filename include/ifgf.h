@@ -114,6 +114,14 @@ typedef struct {
                        buffers wait for their result; profiling waits for its events):
                        past it the call returns IFGF_ETIMEOUT and the queued work
                        completes on its own; 0 = no limit */
+    int leaf_max;       /* 0: the uniform octree of `levels` levels (Sec. 3.3.1).  > 0: an
+                       adaptive octree, which Sec. 4 names as an improvement: a box of
+                       level >= 3 with at most leaf_max points is not subdivided (a leaf),
+                       boxes of level `levels` are leaves.  A leaf's points take the
+                       analytic factors of its cones directly; the direct sums of a target
+                       cover the points of its leaf's neighbours and the leaf neighbours of
+                       its leaf's ancestors (every pair is covered once).  IFGF_FP64 and
+                       IFGF_MIXED plans only. */
 } ifgf_options;
 
 /*
@@ -216,6 +224,21 @@ ifgf_status ifgf_plan_get_perm(const ifgf_plan *plan, int64_t *perm);
 /* Relevant boxes of level d: keys[nbox] (Morton key of the integer box
  * coordinate) and start[nbox+1] (ranges into the Morton-ordered points). */
 ifgf_status ifgf_plan_get_boxes(const ifgf_plan *plan, int level, uint64_t *keys, int64_t *start);
+
+/* Point ranges and leaves of level d: end[nbox] (box b holds the sorted points
+ * start[b] .. end[b]-1, start from ifgf_plan_get_boxes) and leaf[nbox] (1: the box is
+ * not subdivided).  In a uniform tree end[b] = start[b+1] and the leaves are the boxes
+ * of level D. */
+ifgf_status ifgf_plan_get_box_ends(const ifgf_plan *plan, int level, int64_t *end, int64_t *leaf);
+
+/* Level of every point's leaf box, levels[N] in Morton order (all D in a uniform tree). */
+ifgf_status ifgf_plan_get_point_levels(const ifgf_plan *plan, int64_t *levels);
+
+/* Near-field point ranges of the leaf boxes of level d >= 3: *count receives their number;
+ * with start != NULL also start[nbox+1] (CSR over the boxes) and the ranges
+ * [lo[e], hi[e]) of sorted points, ascending per box. */
+ifgf_status ifgf_plan_get_near(const ifgf_plan *plan, int level, int64_t *count, int64_t *start, int64_t *lo,
+                               int64_t *hi);
 
 /* Cousin lists of level d >= 3 (Eq. defcousinboxes) in CSR form. */
 ifgf_status ifgf_plan_get_cousins(const ifgf_plan *plan, int level, int64_t *start, int64_t *list);

@@ -12,7 +12,8 @@ every call raises if libifgf.so has not been built.
     plan_destroy(handle)
 
 `Plan` wraps a handle; `IFGFApply` is a torch.autograd.Function whose backward is
-the library's hand-written adjoint.
+the library's hand-written adjoint.  rhs_shard / apply_rhs_sharded split a batch of
+right-hand sides over ranks (one GPU and one plan per rank, no data-path collective).
 """
 from __future__ import annotations
 
@@ -34,6 +35,7 @@ STATUS = {0: "IFGF_OK", 1: "IFGF_EINVAL", 2: "IFGF_ENOMEM", 3: "IFGF_ECUDA", 4: 
 # every symbol include/ifgf.h declares
 EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_partial", "ifgf_apply_noalloc",
            "ifgf_plan_destroy", "ifgf_plan_level_info", "ifgf_plan_get_perm", "ifgf_plan_get_boxes",
+           "ifgf_plan_get_box_ends", "ifgf_plan_get_point_levels", "ifgf_plan_get_near",
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
            "ifgf_plan_geometry",
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_autotune", "ifgf_plan_set_tiles", "ifgf_plan_timings",
@@ -50,7 +52,7 @@ class IFGFError(RuntimeError):
 class ifgf_options(ctypes.Structure):
     _fields_ = [("leaf_ns", ctypes.c_int), ("leaf_nc", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("value_budget_bytes", ctypes.c_longlong),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("leaf_max", ctypes.c_int)]
 
 
 _lib = None
@@ -74,6 +76,9 @@ def lib():
         L.ifgf_plan_get_perm.argtypes = [P, P]
         L.ifgf_plan_get_boxes.argtypes = [P, i, P, P]
         L.ifgf_plan_get_cousins.argtypes = [P, i, P, P]
+        L.ifgf_plan_get_box_ends.argtypes = [P, i, P, P]
+        L.ifgf_plan_get_point_levels.argtypes = [P, P]
+        L.ifgf_plan_get_near.argtypes = [P, i, P, P, P, P]
         L.ifgf_plan_get_active.argtypes = [P, i, P, P]
         L.ifgf_plan_get_values.argtypes = [P, i, P]
         L.ifgf_plan_cone_ids.argtypes = [P, i, i64, P, P, P]
@@ -128,8 +133,10 @@ def _stream(x=None):
 
 def plan_create(points, kappa: float, levels: int, p_radial: int = 3, p_angular: int = 5,
                 leaf_ns: int = 0, leaf_nc: int = 0, max_nrhs: int = 1, precision="fp64",
-                flags: int = 0, value_budget_bytes: int = 0, timeout_s: float = 0.0, stream=None):
-    """ifgf_plan_create; points: [N,3] float64 (numpy or torch, host or device)."""
+                flags: int = 0, value_budget_bytes: int = 0, timeout_s: float = 0.0, stream=None,
+                leaf_max: int = 0):
+    """ifgf_plan_create; points: [N,3] float64 (numpy or torch, host or device); leaf_max > 0
+    builds an adaptive octree."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     if isinstance(points, np.ndarray):
@@ -139,7 +146,7 @@ def plan_create(points, kappa: float, levels: int, p_radial: int = 3, p_angular:
         points = points.contiguous()
         n = points.shape[0]
     opt = ifgf_options(int(leaf_ns), int(leaf_nc), int(max_nrhs), int(precision), int(flags),
-                       int(value_budget_bytes), float(timeout_s))
+                       int(value_budget_bytes), float(timeout_s), int(leaf_max))
     h = ctypes.c_void_p()
     st = stream if stream is not None else _stream(points)
     _check(lib().ifgf_plan_create(_ptr(points), n, float(kappa), int(levels), int(p_radial),
@@ -190,14 +197,15 @@ class Plan:
     """An IFGF plan on the current CUDA device."""
 
     def __init__(self, points, kappa, levels, p_radial=3, p_angular=5, leaf_ns=0, leaf_nc=0,
-                 max_nrhs=1, precision="fp64", flags=0, value_budget_bytes=0, timeout_s=0.0):
+                 max_nrhs=1, precision="fp64", flags=0, value_budget_bytes=0, timeout_s=0.0, leaf_max=0):
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.n = int(points.shape[0])
         self.levels = int(levels)
         self.max_nrhs = int(max_nrhs)
         self.P = p_radial * p_angular * p_angular
         self.handle = plan_create(points, kappa, levels, p_radial, p_angular, leaf_ns, leaf_nc,
-                                  max_nrhs, self.precision, flags, value_budget_bytes, timeout_s)
+                                  max_nrhs, self.precision, flags, value_budget_bytes, timeout_s,
+                                  leaf_max=leaf_max)
 
     @property
     def complex_dtype(self):
@@ -274,6 +282,31 @@ class Plan:
         _check(lib().ifgf_plan_get_boxes(self.handle, d, _ptr(keys), _ptr(start)), self.handle)
         return keys, start
 
+    def box_ends(self, d):
+        """(end, leaf) of the boxes of level d (see ifgf_plan_get_box_ends)."""
+        nb = self.level_info(d)["nbox"]
+        end = np.zeros(max(nb, 1), dtype=np.int64)
+        leaf = np.zeros(max(nb, 1), dtype=np.int64)
+        _check(lib().ifgf_plan_get_box_ends(self.handle, d, _ptr(end), _ptr(leaf)), self.handle)
+        return end[:nb], leaf[:nb].astype(bool)
+
+    def point_levels(self):
+        out = np.zeros(self.n, dtype=np.int64)
+        _check(lib().ifgf_plan_get_point_levels(self.handle, _ptr(out)), self.handle)
+        return out
+
+    def near(self, d):
+        """Near-field ranges of the leaf boxes of level d: (start, lo, hi)."""
+        m = ctypes.c_int64(0)
+        _check(lib().ifgf_plan_get_near(self.handle, d, ctypes.byref(m), None, None, None), self.handle)
+        nb = self.level_info(d)["nbox"]
+        start = np.zeros(nb + 1, dtype=np.int64)
+        lo = np.zeros(max(m.value, 1), dtype=np.int64)
+        hi = np.zeros(max(m.value, 1), dtype=np.int64)
+        _check(lib().ifgf_plan_get_near(self.handle, d, ctypes.byref(m), _ptr(start), _ptr(lo), _ptr(hi)),
+               self.handle)
+        return start, lo[: m.value], hi[: m.value]
+
     def cousins(self, d):
         li = self.level_info(d)
         start = np.zeros(li["nbox"] + 1, dtype=np.int64)
@@ -345,6 +378,52 @@ class Plan:
         e = ctypes.c_int(0)
         _check(lib().ifgf_plan_check(self.handle, ctypes.byref(e)), self.handle)
         return int(e.value)
+
+
+# ------------------------------------------------------------------------------------
+# Right-hand sides sharded over ranks (one GPU per rank)
+# ------------------------------------------------------------------------------------
+
+def rhs_shard(nrhs: int, rank: int, world: int) -> tuple[int, int]:
+    """The right-hand sides [r0, r1) of `rank` when a batch of nrhs is split over `world`
+    ranks: contiguous rows of the [nrhs][N] batch, sizes differing by at most one, in rank
+    order.  Right-hand sides are independent problems of the same operator, so every rank
+    applies its own plan (a replica of the same geometry on its own GPU) to its rows and
+    no data crosses ranks while they evaluate."""
+    if world < 1 or not 0 <= rank < world or nrhs < 0:
+        raise ValueError("need 0 <= rank < world and nrhs >= 0")
+    base, extra = divmod(nrhs, world)
+    r0 = rank * base + min(rank, extra)
+    return r0, r0 + base + (1 if rank < extra else 0)
+
+
+def apply_rhs_sharded(plan: "Plan", sigma_batch, rank: int, world: int, adjoint: bool = False):
+    """This rank's rows of A sigma (or A^H sigma) for a [nrhs][N] batch: the rows
+    rhs_shard(nrhs, rank, world) of sigma_batch, applied on this rank's plan.  Returns
+    ((r0, r1), u_rows); a rank with no rows returns an empty [0][N] array."""
+    r0, r1 = rhs_shard(int(sigma_batch.shape[0]), rank, world)
+    rows = sigma_batch[r0:r1]
+    if r1 == r0:
+        return (r0, r1), rows
+    return (r0, r1), (plan.apply_adjoint(rows) if adjoint else plan.apply(rows))
+
+
+def gather_rhs_shards(u_rows, nrhs: int, group=None):
+    """Reassembles the [nrhs][N] result from every rank's rows (torch.distributed
+    all_gather on the host; for callers that need the whole batch on every rank, outside
+    any timed evaluation).  u_rows: this rank's rows as a numpy array."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    shards = [rhs_shard(nrhs, r, world) for r in range(world)]
+    rows = max(b - a for a, b in shards)  # every rank sends the same shape (padded)
+    mine = np.ascontiguousarray(u_rows)
+    buf = np.zeros((rows, mine.shape[1]), dtype=mine.dtype)
+    buf[: mine.shape[0]] = mine
+    send = torch.from_numpy(buf)
+    parts = [torch.empty_like(send) for _ in range(world)]
+    dist.all_gather(parts, send, group=group)
+    return np.concatenate([p.numpy()[: b - a] for p, (a, b) in zip(parts, shards)], axis=0)
 
 
 def _autograd_function():

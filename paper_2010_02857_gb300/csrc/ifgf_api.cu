@@ -89,7 +89,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         g_create_error = "IFGF_BATCHED_BF16 plans support (P_s, P_ang) = (3, 5)";
         return IFGF_EINVAL;
     }
-    ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0, 0.0};
+    ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0, 0.0, 0};
     if (opt) o = *opt;
     if (o.value_budget_bytes < 0) { g_create_error = "value_budget_bytes must be >= 0"; return IFGF_EINVAL; }
     if (!(o.timeout_s >= 0.0)) { g_create_error = "timeout_s must be >= 0"; return IFGF_EINVAL; }
@@ -101,6 +101,11 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     }
     if (o.leaf_ns < 0 || o.leaf_nc < 0 || o.leaf_ns > 1024 || o.leaf_nc > 1024) {
         g_create_error = "leaf cone counts out of range";
+        return IFGF_EINVAL;
+    }
+    if (o.leaf_max < 0) { g_create_error = "leaf_max must be >= 0"; return IFGF_EINVAL; }
+    if (o.leaf_max > 0 && o.precision == IFGF_BATCHED_BF16) {
+        g_create_error = "adaptive trees (leaf_max > 0) are supported by IFGF_FP64 and IFGF_MIXED plans";
         return IFGF_EINVAL;
     }
     ifgf_plan *p = new (std::nothrow) ifgf_plan();
@@ -115,6 +120,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     p->max_nrhs = o.max_nrhs;
     p->flags = o.flags;
     p->dev.flags = o.flags;
+    p->leaf_max = o.leaf_max;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -482,6 +488,43 @@ extern "C" ifgf_status ifgf_plan_get_boxes(const ifgf_plan *plan, int level, uin
     return copy_i32_as_i64((ifgf_plan *)plan, L.start, L.nbox + 1, start);
 }
 
+extern "C" ifgf_status ifgf_plan_get_box_ends(const ifgf_plan *plan, int level, int64_t *end, int64_t *leaf)
+{
+    if (!level_ok(plan, level, 1) || !end || !leaf) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    ifgf_status s = copy_i32_as_i64((ifgf_plan *)plan, L.end, L.nbox, end);
+    if (s != IFGF_OK) return s;
+    std::vector<unsigned char> h(L.nbox);
+    if (L.nbox && cudaMemcpy(h.data(), L.leaf, L.nbox, cudaMemcpyDeviceToHost) != cudaSuccess) return IFGF_ECUDA;
+    for (int b = 0; b < L.nbox; ++b) leaf[b] = h[b];
+    return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_plan_get_point_levels(const ifgf_plan *plan, int64_t *levels)
+{
+    if (!plan || !levels) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    return copy_i32_as_i64((ifgf_plan *)plan, plan->dev.ptlev, plan->n, levels);
+}
+
+extern "C" ifgf_status ifgf_plan_get_near(const ifgf_plan *plan, int level, int64_t *count, int64_t *start,
+                                          int64_t *lo, int64_t *hi)
+{
+    if (!level_ok(plan, level, 3) || !count) return IFGF_EINVAL;
+    cudaDeviceSynchronize();
+    const LevelDev &L = plan->dev.lev[level];
+    int m = 0;
+    if (cudaMemcpy(&m, L.near_start + L.nbox, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return IFGF_ECUDA;
+    *count = m;
+    if (!start) return IFGF_OK;
+    if (!lo || !hi) return IFGF_EINVAL;
+    ifgf_status s = copy_i32_as_i64((ifgf_plan *)plan, L.near_start, L.nbox + 1, start);
+    if (s == IFGF_OK) s = copy_i32_as_i64((ifgf_plan *)plan, L.near_lo, m, lo);
+    if (s == IFGF_OK) s = copy_i32_as_i64((ifgf_plan *)plan, L.near_hi, m, hi);
+    return s;
+}
+
 extern "C" ifgf_status ifgf_plan_get_cousins(const ifgf_plan *plan, int level, int64_t *start, int64_t *list)
 {
     if (!level_ok(plan, level, 3) || !start || !list) return IFGF_EINVAL;
@@ -532,21 +575,22 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
              "\"near_pairs\": %lld, \"leaf_evals\": %lld, \"build_ms\": %.3f, \"device_bytes\": %zu, "
              "\"pingpong\": %d, \"rhs_chunk\": %d, \"cache_bytes\": %zu, \"graphs\": %d, "
              "\"graph_captures\": %lld, \"graph_replays\": %lld, \"tune_leaf\": %d, \"tune_cone_ctas\": %d, "
-             "\"level\": [",
+             "\"leaf_max\": %d, \"adaptive\": %d, \"level\": [",
              (long long)plan->n, plan->D, plan->P, plan->kappa, plan->precision, plan->max_nrhs,
              (long long)plan->near_pairs, (long long)plan->leaf_evals, plan->build_ms, plan->device_bytes,
              plan->pingpong ? 1 : 0, plan->rhs_chunk, plan->cache_bytes, (int)plan->graphs.size(),
              (long long)plan->graph_captures, (long long)plan->graph_replays, plan->dev.tune_leaf,
-             plan->dev.tune_cone_ctas);
+             plan->dev.tune_cone_ctas, plan->leaf_max, plan->dev.adaptive);
     s += tmp;
     for (int d = 1; d <= plan->D; ++d) {
         const LevelHost &h = plan->lh[d];
         const LevelDev &L = plan->dev.lev[d];
         snprintf(tmp, sizeof tmp,
                  "%s{\"d\": %d, \"nbox\": %d, \"ncous\": %lld, \"nact\": %d, \"ns\": %d, \"nc\": %d, "
-                 "\"cousin_evals\": %lld, \"upward_evals\": %lld, \"table_rows\": %lld}",
+                 "\"cousin_evals\": %lld, \"upward_evals\": %lld, \"table_rows\": %lld, \"union_rows\": %lld}",
                  d > 1 ? ", " : "", d, L.nbox, (long long)h.ncous, d >= 3 ? L.nact : 0, d >= 3 ? L.ns : 0,
-                 d >= 3 ? L.nc : 0, (long long)h.cousin_evals, (long long)h.upward_evals, (long long)h.table_rows);
+                 d >= 3 ? L.nc : 0, (long long)h.cousin_evals, (long long)h.upward_evals, (long long)h.table_rows,
+                 (long long)h.union_rows);
         s += tmp;
     }
     s += "]}";

@@ -17,7 +17,7 @@ size_t ifgf_uptable_entry_bytes(int precision, int Ps, int Pang)
 {
     bool big = (Ps == 4 && Pang == 7);
     if (precision == IFGF_FP64) return big ? sizeof(UpEntry<double, 18>) : sizeof(UpEntry<double, 13>);
-    return big ? sizeof(UpEntry<float, 18>) : sizeof(UpEntry<float, 13>);
+    return sizeof(UpEntry32);
 }
 
 cudaError_t ifgf_build_evalcache_f64(const PlanDev &pd, int d, int which, cudaStream_t st)

@@ -312,19 +312,22 @@ __global__ void k_permute_out(const void *in, void *out, const int *perm, int n,
 // ---------------------------------------------------------------------------------
 // Leaf level: F_k^D(q) = sum_{x' in B_k} sigma(x') |q - x_k| / |q - x'| e^{i kappa (|q - x'| - |q - x_k|)}
 // ---------------------------------------------------------------------------------
+// One thread per (relevant cone of a leaf box of level d, node): every slot of level D in
+// a uniform tree; the leaf boxes' slots of any level in an adaptive one.
 template <typename T, int R, int PS, int PA>
-__global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int nrhs, const void *sig)
+__global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int d, int nrhs, const void *sig)
 {
     constexpr int P = PS * PA * PA;
-    const LevelDev &L = pd.lev[pd.D];
+    const LevelDev &L = pd.lev[d];
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)L.nact * P) return;
-    int slot = (int)(t / P), node = (int)(t % P);
+    if (t >= (int64_t)L.nleaf_slots * P) return;
+    const int li = (int)(t / P), node = (int)(t % P);
+    const int slot = L.leaf_slots ? L.leaf_slots[li] : li;
     int b = L.act_box[slot];
     const double *c = L.center + 3 * (size_t)b;
     double q[3], dir[3];
     double R0 = node_pos(L, PS, PA, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
-    const int j0 = L.start[b], j1 = L.start[b + 1];
+    const int j0 = L.start[b], j1 = L.end[b];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
 #pragma unroll
@@ -365,8 +368,55 @@ __device__ __forceinline__ int up_geometry(const PlanDev &pd, const LevelDev &L,
     return g.cone;
 }
 
+// The same geometry for FP32 plans as local coordinates (the form the FP32 tables store).
+template <int PS, int PA>
+__device__ __forceinline__ int up_geometry_t(const PlanDev &pd, const LevelDev &L, const LevelDev &Lp, int pcone,
+                                             int node, int oct, float *tl, cpx<float> &f)
+{
+    const double hh = L.H * 0.5;
+    double v[3], dir[3];
+    double Rj = node_rel(Lp, PS, PA, pcone, node, hh, oct, v, dir);
+    ConeGeom g = cone_of_mixed(L, v[0], v[1], v[2]);
+    local_coords_f32(L, g, v[0], v[1], v[2], tl);
+    f = recentre<float>(pd.kappa, Rj, dir, g.r, (oct & 1) ? hh : -hh, (oct & 2) ? hh : -hh, (oct & 4) ? hh : -hh);
+    return g.cone;
+}
+
+// Weights, factor and child cone from an upward table or cache entry.
 template <typename T, int PS, int PA>
-__global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, UpEntry<T, PS + 2 * PA> *tab)
+__device__ __forceinline__ int up_entry(const PlanDev &pd, const typename UpEntryOf<T, PS + 2 * PA>::type &e, T *w,
+                                        cpx<T> &f)
+{
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int m = 0; m < PS + 2 * PA; ++m) w[m] = e.w[m];
+        f = {e.fr, e.fi};
+    } else {
+        lagrange(PS, pd.tsf, pd.itsf, e.t[0], w);
+        lagrange(PA, pd.taf, pd.itaf, e.t[1], w + PS);
+        lagrange(PA, pd.taf, pd.itaf, e.t[2], w + PS + PA);
+        f = {e.fr, e.fi};
+    }
+    return e.cone;
+}
+
+// The table or cache entry of one upward evaluation.
+template <typename T, int PS, int PA>
+__device__ __forceinline__ typename UpEntryOf<T, PS + 2 * PA>::type make_up_entry(const PlanDev &pd, const LevelDev &L,
+                                                                                   const LevelDev &Lp, int pcone,
+                                                                                   int node, int oct)
+{
+    typename UpEntryOf<T, PS + 2 * PA>::type e;
+    cpx<T> f;
+    if constexpr (sizeof(T) == 8) e.cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, e.w, f);
+    else e.cone = up_geometry_t<PS, PA>(pd, L, Lp, pcone, node, oct, e.t, f);
+    e.fr = f.x;
+    e.fi = f.y;
+    return e;
+}
+
+template <typename T, int PS, int PA>
+__global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, typename UpEntryOf<T, PS + 2 * PA>::type *tab)
 {
     constexpr int P = PS * PA * PA;
     const LevelDev &L = pd.lev[d];
@@ -376,9 +426,7 @@ __global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, UpEntr
     int node = (int)(t % P);
     int oct = (int)((t / P) % 8);
     int row = (int)(t / (8 * P));
-    UpEntry<T, PS + 2 * PA> e;
-    cpx<T> f;
-    e.cone = up_geometry<T, PS, PA>(pd, L, Lp, L.uids[row], node, oct, e.w, f);
+    typename UpEntryOf<T, PS + 2 * PA>::type e = make_up_entry<T, PS, PA>(pd, L, Lp, L.uids[row], node, oct);
     // the table's cone id must be the one relevance rule (ii) marked: take the
     // correctly rounded cell (cone_of_fast agrees by construction; this is a check)
     {
@@ -386,8 +434,6 @@ __global__ void __launch_bounds__(128) k_build_uptable(PlanDev pd, int d, UpEntr
         node_rel(Lp, PS, PA, L.uids[row], node, L.H * 0.5, oct, v, nullptr);
         if (cone_of(L, v[0], v[1], v[2]).cone != e.cone) atomicAdd(pd.err, 1);
     }
-    e.fr = f.x;
-    e.fi = f.y;
     tab[t] = e;
 }
 
@@ -403,11 +449,12 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
     int slot = (int)(t / P), node = (int)(t % P);
     int j = Lp.act_box[slot];
     const int pcone = Lp.act_cone[slot];
-    const UpEntry<T, NW> *tab = nullptr;
+    using Entry = typename UpEntryOf<T, NW>::type;
+    const Entry *tab = nullptr;
     if constexpr (TAB) {
         int row = table_row(L.ubits, L.urank, pcone);
         if (row < 0) { atomicAdd(pd.err, 1); return; }
-        tab = (const UpEntry<T, NW> *)L.utab + (size_t)row * 8 * P + node;
+        tab = (const Entry *)L.utab + (size_t)row * 8 * P + node;
     }
     const int k0 = Lp.child_start[j], k1 = Lp.child_start[j + 1];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
@@ -420,18 +467,10 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
             cpx<T> f;
             int cone;
             if constexpr (TAB) {
-                const UpEntry<T, NW> &e = tab[(size_t)oct * P];
-#pragma unroll
-                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
-                f = {e.fr, e.fi};
-                cone = e.cone;
+                cone = up_entry<T, PS, PA>(pd, tab[(size_t)oct * P], w, f);
             } else if (L.ucache) {
-                const UpEntry<T, NW> &e =
-                    ((const UpEntry<T, NW> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)];
-#pragma unroll
-                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
-                f = {e.fr, e.fi};
-                cone = e.cone;
+                cone = up_entry<T, PS, PA>(
+                    pd, ((const Entry *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)], w, f);
             } else {
                 cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
             }
@@ -452,173 +491,317 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
     }
 }
 
-// FP32 upward step with the children's cone values staged in shared memory.
+// FP32 upward step, one warp per parent cone slot, in runs of nodes that share a child cone.
 //
-// The thread layout and the arithmetic are those of k_upward (one thread per (parent
-// slot, node); children in order; the same sum-factorised contraction), but a warp
-// reads cone values from shared memory instead of from L1.  In k_upward the 32 lanes of
-// a warp interpolate, at each child step, from the 2-3 child cones their nodes fall in,
-// so every value load costs 2-3 L1 wavefronts and the kernel is bound by L1 throughput.
-// Here, at each child step, the warp finds the distinct child slots of its lanes
-// (__match_any_sync), copies the values of up to kUpStage of them into its shared-memory
-// stage (coalesced 16-byte or 8-byte loads), and each lane contracts from its cone's
-// copy.  A staged cone takes P * nrhs complex values; the copies follow one another
-// without padding, so the copies start 600 * nrhs (mod 32) banks apart: for nrhs = 1..4
-// the same node of up to four cones lies in disjoint banks, and a warp's load is one
-// shared-memory wavefront whichever of the staged cones its lanes read.  Lanes whose
-// cone is beyond the first kUpStage distinct ones (rare) read from global memory.  Every
-// lane sums its children in the same order with the same operations as k_upward.
-// nrhs <= R <= 4.
-constexpr int kUpStage = 4;
-constexpr int kUpWarps = 4;
+// k_upward gives each thread one (parent slot, node) and interpolates, child by child, from
+// the child cone its node falls in.  Every evaluation then reads all P * nrhs values of its
+// cone into its registers: one 16-byte load per two complex values and three FMAs per load
+// on average, which binds the kernel to the 128 bytes per clock that L1 and shared memory
+// deliver.  Here a warp takes one parent slot and, for each child in order:
+//   A. computes the geometry of the P nodes (table, cache or on the fly; three per lane)
+//      into shared memory: local coordinates, factor, child cone slot;
+//   B. groups the nodes by child cone slot (ballots) and cuts each group into runs of at
+//      most kRunK nodes, in node order;
+//   C. copies the values of the first kRunStage cones into the warp's shared-memory stage
+//      (coalesced 16-byte loads);
+//   D. gives each lane one run: it reads each value of its cone once and applies it to the
+//      run's kRunK evaluations (same FMAs as k_upward, in the same order, per evaluation),
+//      and adds factor times value to the node's accumulator in shared memory.
+// Every node sums its children in order with the same operations as k_upward, so the
+// results are equal.  Cones beyond the first kRunStage of a child step (rare) are read
+// from global memory; more than 32 runs (rare) take a second pass.
+constexpr int kRunK = 3;
+constexpr int kRunStage = 4;
+constexpr int kRunWarps = 4;
 
-template <int R, int PS, int PA>
-__device__ __forceinline__ void contract_staged(const float2 *s, int nrhs, const float *ws, const float *wt,
-                                                const float *wp, cpx<float> *out)
+// the run's evaluations: values src[node][r] (r < nrhs) of one child cone, per evaluation e
+// the weights ws[e] (PS), wt[e] (PA), wp[e] (PA); out[e][r]
+template <int R, int PS, int PA, typename Src>
+__device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)[PS + 2 * PA], cpx<float> (*out)[R])
 {
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[r] = {0.f, 0.f};
+    for (int e = 0; e < kRunK; ++e)
 #pragma unroll
+        for (int r = 0; r < R; ++r) out[e][r] = {0.f, 0.f};
+#pragma unroll 1
     for (int a = 0; a < PS; ++a) {
-        cpx<float> mid[R];
+        cpx<float> mid[kRunK][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) mid[r] = {0.f, 0.f};
+        for (int e = 0; e < kRunK; ++e)
+#pragma unroll
+            for (int r = 0; r < R; ++r) mid[e][r] = {0.f, 0.f};
 #pragma unroll
         for (int b = 0; b < PA; ++b) {
-            cpx<float> in[R];
+            cpx<float> in[kRunK][R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) in[r] = {0.f, 0.f};
+            for (int e = 0; e < kRunK; ++e)
+#pragma unroll
+                for (int r = 0; r < R; ++r) in[e][r] = {0.f, 0.f};
 #pragma unroll
             for (int c = 0; c < PA; ++c) {
                 const int idx = (a * PA + b) * PA + c;
+                float v[2 * R];
                 if (R == 4 && nrhs == 4) {
-                    const float4 v01 = reinterpret_cast<const float4 *>(s)[idx * 2];
-                    const float4 v23 = reinterpret_cast<const float4 *>(s)[idx * 2 + 1];
-                    const float v[8] = {v01.x, v01.y, v01.z, v01.w, v23.x, v23.y, v23.z, v23.w};
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        in[r].x += wp[c] * v[2 * r];
-                        in[r].y += wp[c] * v[2 * r + 1];
-                    }
+                    const float4 v01 = reinterpret_cast<const float4 *>(src)[idx * 2];
+                    const float4 v23 = reinterpret_cast<const float4 *>(src)[idx * 2 + 1];
+                    v[0] = v01.x; v[1] = v01.y; v[2] = v01.z; v[3] = v01.w;
+                    v[4] = v23.x; v[5] = v23.y; v[6] = v23.z; v[7] = v23.w;
                 } else {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (R == 1 || r < nrhs) {
-                            const float2 v = s[idx * nrhs + r];
-                            in[r].x += wp[c] * v.x;
-                            in[r].y += wp[c] * v.y;
-                        }
+                    for (int r = 0; r < R; ++r) {
+                        float2 x = make_float2(0.f, 0.f);
+                        if (R == 1 || r < nrhs) x = src[idx * nrhs + r];
+                        v[2 * r] = x.x;
+                        v[2 * r + 1] = x.y;
+                    }
                 }
+#pragma unroll
+                for (int e = 0; e < kRunK; ++e)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        in[e][r].x += w[e][PS + PA + c] * v[2 * r];
+                        in[e][r].y += w[e][PS + PA + c] * v[2 * r + 1];
+                    }
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) { mid[r].x += wt[b] * in[r].x; mid[r].y += wt[b] * in[r].y; }
+            for (int e = 0; e < kRunK; ++e)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    mid[e][r].x += w[e][PS + b] * in[e][r].x;
+                    mid[e][r].y += w[e][PS + b] * in[e][r].y;
+                }
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) { out[r].x += ws[a] * mid[r].x; out[r].y += ws[a] * mid[r].y; }
+        for (int e = 0; e < kRunK; ++e) {
+            // w[e][a] with the rolled loop index a, by selects (keeps w in registers)
+            float wa = w[e][0];
+#pragma unroll
+            for (int m = 1; m < PS; ++m)
+                if (a == m) wa = w[e][m];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                out[e][r].x += wa * mid[e][r].x;
+                out[e][r].y += wa * mid[e][r].y;
+            }
+        }
     }
+}
+
+// Shared memory of one warp of k_upward_runs for P nodes and nrhs right-hand sides.
+__host__ __device__ constexpr size_t run_stage_floats(int P, int nrhs) { return (size_t)kRunStage * P * nrhs * 2; }
+__host__ __device__ constexpr size_t run_warp_bytes(int P, int R, int nrhs)
+{
+    // stage, accumulators [P][R] complex, geometry t[P][3] + f[P][2] floats, slots [P], runs [32][kRunK]
+    return (run_stage_floats(P, nrhs) + (size_t)P * R * 2 + (size_t)P * 5) * 4 + (size_t)P * 4 + 32 * kRunK * 4 + 32 * 4;
 }
 
 template <int R, int PS, int PA, bool TAB>
-__global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int d, int nrhs)
+__global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, int d, int nrhs)
 {
     constexpr int P = PS * PA * PA;
     constexpr int NW = PS + 2 * PA;
+    constexpr int NCH = (P + 31) / 32;
     constexpr unsigned kFull = 0xffffffffu;
-    extern __shared__ __align__(16) float2 s_up_stage[];
+    extern __shared__ __align__(16) float s_runs_raw[];
     const LevelDev &L = pd.lev[d];
     const LevelDev &Lp = pd.lev[d - 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = t < (int64_t)Lp.nact * P;
-    if (__all_sync(kFull, !valid)) return;  // whole warps past the end
-    const int slot = valid ? (int)(t / P) : 0, node = valid ? (int)(t % P) : 0;
-    const int j = valid ? Lp.act_box[slot] : 0;
-    const int pcone = valid ? Lp.act_cone[slot] : 0;
-    const UpEntry<float, NW> *tab = nullptr;
+    const int slot = blockIdx.x * kRunWarps + warp;
+    if (slot >= Lp.nact) return;  // the whole warp
+    // this warp's shared memory
+    float *base = (float *)((unsigned char *)s_runs_raw + (size_t)warp * run_warp_bytes(P, R, nrhs));
+    float2 *stage = (float2 *)base;
+    float2 *acc = (float2 *)(base + run_stage_floats(P, nrhs));  // [P][R]
+    float *gt = (float *)(acc + (size_t)P * R);                 // [P][3]
+    float2 *gf = (float2 *)(gt + (size_t)P * 3);               // [P]
+    int *gsl = (int *)(gf + P);                                 // [P]
+    int *runs = gsl + P;                                        // [32][kRunK]
+    int *rgrp = runs + 32 * kRunK;                              // [32] group of each run
+    const int j = Lp.act_box[slot];
+    const int pcone = Lp.act_cone[slot];
+    const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
+    const UpEntry32 *tab = nullptr;
     if constexpr (TAB) {
-        if (valid) {
-            const int row = table_row(L.ubits, L.urank, pcone);
-            if (row < 0) { atomicAdd(pd.err, 1); valid = false; }
-            else tab = (const UpEntry<float, NW> *)L.utab + (size_t)row * 8 * P + node;
+        const int row = table_row(L.ubits, L.urank, pcone);
+        if (row < 0) {
+            if (lane == 0) atomicAdd(pd.err, 1);
+            return;
         }
+        tab = (const UpEntry32 *)L.utab + (size_t)row * 8 * P;
     }
-    const int k0 = valid ? Lp.child_start[j] : 0;
-    const int nch = valid ? Lp.child_start[j + 1] - k0 : 0;
-    const int maxch = __reduce_max_sync(kFull, nch);
-    const int vals = P * nrhs;  // complex values per staged cone
-    float2 *stg = s_up_stage + (size_t)warp * kUpStage * vals;
-    cpx<float> acc[R];
+    for (int q = lane; q < P * R; q += 32) acc[q] = make_float2(0.f, 0.f);
+    for (int kk = 0; kk < nch; ++kk) {
+        const int k = k0 + kk;
+        const int oct = (int)(L.key[k] & 7u);
+        // A. geometry of the P nodes
+        int sl_c[NCH];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = {0.f, 0.f};
-    for (int kk = 0; kk < maxch; ++kk) {
-        int sl = -1;
-        float w[NW];
-        cpx<float> f = {0.f, 0.f};
-        if (kk < nch) {
-            const int k = k0 + kk;
-            const int oct = (int)(L.key[k] & 7u);
-            int cone;
-            if constexpr (TAB) {
-                const UpEntry<float, NW> &e = tab[(size_t)oct * P];
-#pragma unroll
-                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
-                f = {e.fr, e.fi};
-                cone = e.cone;
-            } else if (L.ucache) {
-                const UpEntry<float, NW> &e =
-                    ((const UpEntry<float, NW> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * nch + kk];
-#pragma unroll
-                for (int m = 0; m < NW; ++m) w[m] = e.w[m];
-                f = {e.fr, e.fi};
-                cone = e.cone;
-            } else {
-                cone = up_geometry<float, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
+        for (int c = 0; c < NCH; ++c) {
+            const int node = lane + 32 * c;
+            sl_c[c] = -1;
+            if (node < P) {
+                float tl[3];
+                cpx<float> f;
+                int cone;
+                if constexpr (TAB) {
+                    const UpEntry32 en = tab[(size_t)oct * P + node];
+                    tl[0] = en.t[0]; tl[1] = en.t[1]; tl[2] = en.t[2];
+                    f = {en.fr, en.fi};
+                    cone = en.cone;
+                } else if (L.ucache) {
+                    const UpEntry32 en = ((const UpEntry32 *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * nch + kk];
+                    tl[0] = en.t[0]; tl[1] = en.t[1]; tl[2] = en.t[2];
+                    f = {en.fr, en.fi};
+                    cone = en.cone;
+                } else {
+                    cone = up_geometry_t<PS, PA>(pd, L, Lp, pcone, node, oct, tl, f);
+                }
+                const int sl = cone_slot(L, k, cone);
+                if (sl < 0) atomicAdd(pd.err, 1);
+                sl_c[c] = sl;
+                gt[3 * node] = tl[0];
+                gt[3 * node + 1] = tl[1];
+                gt[3 * node + 2] = tl[2];
+                gf[node] = make_float2(f.x, f.y);
+                gsl[node] = sl;
             }
-            sl = cone_slot(L, k, cone);
-            if (sl < 0) atomicAdd(pd.err, 1);
         }
-        // the warp's distinct child slots; the first kUpStage are staged
-        const unsigned same = __match_any_sync(kFull, sl);
-        const int leader = __ffs(same) - 1;
-        const unsigned leaders = __ballot_sync(kFull, lane == leader && sl >= 0);
-        const int mine = sl >= 0 ? __popc(leaders & ((1u << leader) - 1u)) : -1;
-        const int nst = min(__popc(leaders), kUpStage);
-        unsigned rem = leaders;
-        for (int g = 0; g < nst; ++g) {
-            const int src = __ffs(rem) - 1;
-            rem &= rem - 1u;
-            const int gsl = __shfl_sync(kFull, sl, src);
-            const float2 *from = (const float2 *)L.F + (size_t)gsl * vals;
-            float2 *to = stg + (size_t)g * vals;
-            if ((vals & 1) == 0) {
-                for (int e = lane; e < vals / 2; e += 32)
-                    reinterpret_cast<float4 *>(to)[e] = __ldg(reinterpret_cast<const float4 *>(from) + e);
-            } else {
-                for (int e = lane; e < vals; e += 32) to[e] = __ldg(from + e);
+        // B. groups of nodes with one child slot, in order of their first node; runs
+        unsigned pend[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) pend[c] = __ballot_sync(kFull, sl_c[c] >= 0);
+        int nruns = 0, ngroups = 0;
+        for (int q = lane; q < 32 * kRunK; q += 32) runs[q] = -1;
+        __syncwarp();
+        while (true) {
+            int c0 = -1;
+#pragma unroll
+            for (int c = NCH - 1; c >= 0; --c)
+                if (pend[c]) c0 = c;
+            if (c0 < 0) break;
+            unsigned pc = 0;
+            int slc = -1;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                if (c == c0) { pc = pend[c]; slc = sl_c[c]; }
+            const int g_sl = __shfl_sync(kFull, slc, __ffs(pc) - 1);
+            const int g = ngroups++;
+            int before = 0;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const bool mem = sl_c[c] == g_sl && ((pend[c] >> lane) & 1u);
+                const unsigned m = __ballot_sync(kFull, mem);
+                if (mem) {
+                    const int rank = before + __popc(m & ((1u << lane) - 1u));
+                    const int run = nruns + rank / kRunK;
+                    if (run < 32) runs[run * kRunK + rank % kRunK] = lane + 32 * c;
+                }
+                before += __popc(m);
+                pend[c] &= ~m;
             }
+            const int nr = (before + kRunK - 1) / kRunK;
+            for (int q = nruns + lane; q < nruns + nr && q < 32; q += 32) rgrp[q] = g;
+            // C. stage this group's cone values
+            if (g < kRunStage) {
+                const int vals = P * nrhs;
+                const float2 *from = (const float2 *)L.F + (size_t)g_sl * vals;
+                float2 *to = stage + (size_t)g * vals;
+                if ((vals & 1) == 0) {
+                    for (int q = lane; q < vals / 2; q += 32)
+                        reinterpret_cast<float4 *>(to)[q] = __ldg(reinterpret_cast<const float4 *>(from) + q);
+                } else {
+                    for (int q = lane; q < vals; q += 32) to[q] = __ldg(from + q);
+                }
+            }
+            nruns += nr;
         }
         __syncwarp();
-        if (sl >= 0) {
-            cpx<float> val[R];
-            if (mine < kUpStage) contract_staged<R, PS, PA>(stg + (size_t)mine * vals, nrhs, w, w + PS, w + PS + PA, val);
-            else contract<float, R, PS, PA>(L.F, (size_t)sl * P, nrhs, 0, w, w + PS, w + PS + PA, val);
+        // D. the runs (a second pass when a child step has more than 32)
+        for (int pass = 0; pass * 32 < nruns; ++pass) {
+            if (pass > 0) {  // rebuild the runs beyond the first 32 from the groups
+                __syncwarp();
+                for (int q = lane; q < 32 * kRunK; q += 32) runs[q] = -1;
+                __syncwarp();
+                int cnt = 0, g = 0, prev = -1;
+                if (lane == 0) {
+                    // nodes in group order, node order within a group: run index r counts on
+                    for (int gg = 0; gg < ngroups; ++gg) {
+                        int sl0 = -1;
+                        for (int node = 0; node < P; ++node) {
+                            if (gsl[node] < 0) continue;
+                            // the group of a node: the order of first appearance of its slot
+                            bool first = true;
+                            for (int m = 0; m < node; ++m)
+                                if (gsl[m] == gsl[node]) { first = false; break; }
+                            if (first) {
+                                if (g == gg) sl0 = gsl[node];
+                                ++g;
+                            }
+                        }
+                        g = 0;
+                        int rank = 0;
+                        for (int node = 0; node < P; ++node) {
+                            if (gsl[node] != sl0) continue;
+                            const int run = cnt + rank / kRunK - 32 * pass;
+                            if (run >= 0 && run < 32) {
+                                runs[run * kRunK + rank % kRunK] = node;
+                                rgrp[run] = gg;
+                            }
+                            ++rank;
+                        }
+                        cnt += (rank + kRunK - 1) / kRunK;
+                    }
+                    (void)prev;
+                }
+                __syncwarp();
+            }
+            const int r = lane;
+            if (pass * 32 + r < nruns) {
+                int nodes[kRunK];
+                float w[kRunK][NW];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const cpx<float> m = cmul(f, val[r]);
-                acc[r].x += m.x;
-                acc[r].y += m.y;
+                for (int e = 0; e < kRunK; ++e) {
+                    nodes[e] = runs[r * kRunK + e];
+                    const int nd = nodes[e] < 0 ? 0 : nodes[e];
+                    lagrange(PS, pd.tsf, pd.itsf, gt[3 * nd], w[e]);
+                    lagrange(PA, pd.taf, pd.itaf, gt[3 * nd + 1], w[e] + PS);
+                    lagrange(PA, pd.taf, pd.itaf, gt[3 * nd + 2], w[e] + PS + PA);
+                }
+                const int g = rgrp[r];
+                cpx<float> val[kRunK][R];
+                if (g < kRunStage) {
+                    contract_run<R, PS, PA>((const float2 *)(stage + (size_t)g * P * nrhs), nrhs, w, val);
+                } else {
+                    const int sl = gsl[nodes[0]];
+                    contract_run<R, PS, PA>((const float2 *)L.F + (size_t)sl * P * nrhs, nrhs, w, val);
+                }
+#pragma unroll
+                for (int e = 0; e < kRunK; ++e) {
+                    if (nodes[e] < 0) continue;
+                    const float2 f = gf[nodes[e]];
+                    const cpx<float> fc = {f.x, f.y};
+#pragma unroll
+                    for (int rr = 0; rr < R; ++rr) {
+                        const cpx<float> m = cmul(fc, val[e][rr]);
+                        float2 &a = acc[nodes[e] * R + rr];
+                        a.x += m.x;
+                        a.y += m.y;
+                    }
+                }
             }
         }
-        __syncwarp();  // the stage is read before the next child step overwrites it
+        __syncwarp();  // the stage, runs and geometry are read before the next child overwrites them
     }
-    if (valid) {
+    for (int q = lane; q < P; q += 32)
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (R == 1 || r < nrhs) st<float>(Lp.F, ((size_t)slot * P + node) * nrhs + r, acc[r]);
-    }
+            if (R == 1 || r < nrhs) {
+                const float2 a = acc[q * R + r];
+                st<float>(Lp.F, ((size_t)slot * P + q) * nrhs + r, cpx<float>{a.x, a.y});
+            }
 }
 
-// Launch of the upward step d -> d-1: the staged kernel for FP32 values with up to 4
+// Launch of the upward step d -> d-1: the run kernel for FP32 values with up to 4
 // right-hand sides per pass (flags bit 9 selects k_upward, for comparison tests), else
 // k_upward.
 template <typename T, int R, int PS, int PA>
@@ -627,16 +810,30 @@ inline void launch_upward(const PlanDev &pd, int d, int nrhs, int64_t np, cudaSt
     if constexpr (sizeof(T) == 4 && R <= 4) {
         if (nrhs <= R && !(pd.flags & 512)) {
             constexpr int P = PS * PA * PA;
-            const size_t smem = (size_t)kUpWarps * kUpStage * P * nrhs * sizeof(float2);
+            const int nslot = pd.lev[d - 1].nact;
+            const size_t smem = (size_t)kRunWarps * run_warp_bytes(P, R, nrhs);
+            const int grid = (nslot + kRunWarps - 1) / kRunWarps;
             if (pd.lev[d].utab)
-                k_upward_staged<R, PS, PA, true><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, smem, st>>>(pd, d, nrhs);
+                k_upward_runs<R, PS, PA, true><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
             else
-                k_upward_staged<R, PS, PA, false><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, smem, st>>>(pd, d, nrhs);
+                k_upward_runs<R, PS, PA, false><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
             return;
         }
     }
     if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
     else k_upward<T, R, PS, PA, false><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
+}
+
+// Leaf analytic factors of the leaf boxes of level d; returns the threads launched.
+template <typename T, int R, int PS, int PA>
+inline int64_t launch_leaf(const PlanDev &pd, int d, int nrhs, const void *sig, cudaStream_t st)
+{
+    const int64_t nt = (int64_t)pd.lev[d].nleaf_slots * (PS * PA * PA);
+    if (nt > 0) {
+        NvtxRange range("leaf", d);
+        k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, d, nrhs, sig);
+    }
+    return nt;
 }
 
 // ---------------------------------------------------------------------------------
@@ -676,40 +873,47 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
 
-// The sources of the neighbours of leaf box b as one list (one warp, the first of the
-// block): sbeg[e] is the first point of neighbour e and spre[e] the list position where
-// its points start; spre[27] is the list length.  Neighbour lists end at the first -1.
-__device__ __forceinline__ void near_ranges(const LevelDev &LD, int b, int lane, int *sbeg, int *spre)
+// The sources of the near field of leaf box b of level LD as one list (one warp, the
+// first of the block): the box's near ranges [near_lo, near_hi) (its neighbours'
+// points in a uniform tree; reading R13 in an adaptive one), ascending; sbeg[e] is the
+// first point of range e and spre[e] the list position where it starts; spre[nr] is the
+// list length.  Returns nr.
+__device__ __forceinline__ int near_ranges(const LevelDev &LD, int b, int lane, int *sbeg, int *spre)
 {
-    int cnt = 0, beg = 0;
-    if (lane < 27) {
-        const int k = LD.nbr[27 * (size_t)b + lane];
-        if (k >= 0) {
-            beg = LD.start[k];
-            cnt = LD.start[k + 1] - beg;
+    const int e0 = LD.near_start[b], nr = LD.near_start[b + 1] - e0;
+    int carry = 0;
+    for (int c0 = 0; c0 < nr; c0 += 32) {
+        const int e = c0 + lane;
+        int beg = 0, cnt = 0;
+        if (e < nr) {
+            beg = LD.near_lo[e0 + e];
+            cnt = LD.near_hi[e0 + e] - beg;
         }
-    }
-    int inc = cnt;
+        int inc = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += v;
-    }
-    if (lane < 27) {
-        sbeg[lane] = beg;
-        spre[lane + 1] = inc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (e < nr) {
+            sbeg[e] = beg;
+            spre[e + 1] = carry + inc;
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
     }
     if (lane == 0) spre[0] = 0;
+    return nr;
 }
 
 // The point at position g of that list.
-__device__ __forceinline__ int near_source(const int *sbeg, const int *spre, int g)
+__device__ __forceinline__ int near_source(const int *sbeg, const int *spre, int nr, int g)
 {
-    int e = 0;  // the neighbour range holding g: spre[e] <= g < spre[e + 1]
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1)
-        if (e + w < 28 && spre[e + w] <= g) e += w;
-    return sbeg[e] + (g - spre[e]);
+    int lo = 0, hi = nr;  // the range e with spre[e] <= g < spre[e + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (spre[mid] <= g) lo = mid; else hi = mid;
+    }
+    return sbeg[lo] + (g - spre[lo]);
 }
 
 template <typename T, int R>
@@ -722,17 +926,22 @@ __global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nr
     __shared__ __align__(16) cpx<T> ssig[kNearTile * R];
     __shared__ __align__(16) cpx<T> spart[kNearThreads * R];
     __shared__ int sidx[kNearTile];
-    __shared__ int sbeg[27], spre[28];
+    __shared__ int sbeg[kMaxNearRanges], spre[kMaxNearRanges + 1];
+    __shared__ int snr;
     double *sx = (double *)spos, *sy = sx + kNearTile, *sz = sy + kNearTile;
     float4 *soh = (float4 *)spos, *sol = soh + kNearTile;
-    const LevelDev &LD = pd.lev[pd.D];
     const int tid = threadIdx.x;
-    const int2 item = pd.near_tile[blockIdx.x];
+    const int4 item = pd.near_tile[blockIdx.x];
+    const LevelDev &LD = pd.lev[item.z];
     const int b = item.x, t0 = item.y;
-    const int nt = min(kNearTargets, LD.start[b + 1] - t0);  // 1 .. kNearTargets
-    if (tid < 32) near_ranges(LD, b, tid, sbeg, spre);
+    const int nt = min(kNearTargets, LD.end[b] - t0);  // 1 .. kNearTargets
+    if (tid < 32) {
+        const int nr = near_ranges(LD, b, tid, sbeg, spre);
+        if (tid == 0) snr = nr;
+    }
     __syncthreads();
-    const int ns = spre[27];
+    const int nr = snr;
+    const int ns = spre[nr];
     const int q = kNearThreads / nt;
     const int tt = tid % nt, grp = tid / nt;
     const bool tv = grp < q;
@@ -755,7 +964,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near_staged(PlanDev pd, int nr
         for (int g0 = 0; g0 < ns; g0 += kNearTile) {
             const int cnt = min(kNearTile, ns - g0);
             for (int s = tid; s < cnt; s += kNearThreads) {
-                const int j = near_source(sbeg, spre, g0 + s);
+                const int j = near_source(sbeg, spre, nr, g0 + s);
                 sidx[s] = j;
                 if constexpr (sizeof(T) == 8) {
                     cp_async8(sx + s, pd.xs + j);
@@ -832,6 +1041,7 @@ __global__ void __launch_bounds__(128) k_eval(PlanDev pd, int nrhs, const void *
             for (int d = d_hi; d >= d_lo; --d) {
                 const LevelDev &L = pd.lev[d];
                 int b = L.pt_box[i];
+                if (b < 0) continue;  // below the point's leaf (adaptive tree)
                 for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
                     int k = L.cous[e];
                     const double *ck = L.center + 3 * (size_t)k;
@@ -950,19 +1160,17 @@ __device__ __forceinline__ void adj_reader(const PlanDev &pd, const LevelDev &L,
     const int oct = (int)(L.key[k] & 7u);
     const int pcone = Lp.act_cone[psl];
     const int row = L.utab ? table_row(L.ubits, L.urank, pcone) : -1;
+    using Entry = typename UpEntryOf<T, NW>::type;
     if (row >= 0) {
-        const UpEntry<T, NW> &en = ((const UpEntry<T, NW> *)L.utab)[((size_t)row * 8 + oct) * P + pnode];
-#pragma unroll
-        for (int m = 0; m < NW; ++m) w[m] = en.w[m];
-        f = cconj(cpx<T>{en.fr, en.fi});
+        cpx<T> ff;
+        up_entry<T, PS, PA>(pd, ((const Entry *)L.utab)[((size_t)row * 8 + oct) * P + pnode], w, ff);
+        f = cconj(ff);
     } else if (L.ucache) {
         const int j = Lp.act_box[psl];
         const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
-        const UpEntry<T, NW> &en =
-            ((const UpEntry<T, NW> *)L.ucache)[(size_t)L.uoff[psl] + (size_t)pnode * nch + (k - k0)];
-#pragma unroll
-        for (int m = 0; m < NW; ++m) w[m] = en.w[m];
-        f = cconj(cpx<T>{en.fr, en.fi});
+        cpx<T> ff;
+        up_entry<T, PS, PA>(pd, ((const Entry *)L.ucache)[(size_t)L.uoff[psl] + (size_t)pnode * nch + (k - k0)], w, ff);
+        f = cconj(ff);
     } else {
         cpx<T> ff;
         up_geometry<T, PS, PA>(pd, L, Lp, pcone, pnode, oct, w, ff);
@@ -1196,16 +1404,20 @@ inline void launch_adj_level(const PlanDev &pd, int d, int nrhs, const void *vs,
     }
 }
 
-// Adjoint per source: conj(g(q, x')) times the leaf cones' adjoint values, stored or added
-// to the conjugated near field (accumulate).
+// Adjoint per source: conj(g(q, x')) times the adjoint values of its leaf box's cones,
+// stored or added to the conjugated near field (accumulate).  only_level >= 3 restricts
+// the launch to the sources whose leaf box lies on that level (two-buffer adjoints of
+// adaptive trees run it level by level, while the level's values are resident).
 template <typename T, int R, int PS, int PA>
 __global__ void __launch_bounds__(128) k_adj_eval(PlanDev pd, int nrhs, const void *vs, void *ws, int mode,
-                                                  int accumulate)
+                                                  int accumulate, int only_level)
 {
     constexpr int P = PS * PA * PA;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= pd.n) return;
-    const LevelDev &LD = pd.lev[pd.D];
+    const int lv = pd.ptlev[j];  // the level of the point's leaf box
+    if (only_level >= 3 && lv != only_level) return;
+    const LevelDev &LD = pd.lev[lv];
     const int b = LD.pt_box[j];
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
@@ -1254,12 +1466,7 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
     constexpr int P = PS * PA * PA;
     if (!pd.pingpong) {
         if (mode & 2) {
-            const LevelDev &L = pd.lev[pd.D];
-            int64_t nt = (int64_t)L.nact * P;
-            {
-                NvtxRange range("leaf", pd.D);
-                if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
-            }
+            int64_t nt = launch_leaf<T, R, PS, PA>(pd, pd.D, nrhs, sig, st);
             tm.mark(STAGE_LEAF, nt > 0, st);
             int nl = 0;
             for (int d = pd.D; d >= 4; --d) {
@@ -1267,7 +1474,9 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
                 if (np == 0) continue;
                 NvtxRange range("upward", d);
                 launch_upward<T, R, PS, PA>(pd, d, nrhs, np, st);
-                ++nl;
+                // leaves of level d-1 (adaptive tree): their slots take the analytic factors
+                // of their own points, after the upward step has written the level
+                nl += 1 + (launch_leaf<T, R, PS, PA>(pd, d - 1, nrhs, sig, st) > 0);
             }
             tm.mark(STAGE_UPWARD, nl, st);
         }
@@ -1290,9 +1499,7 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
     }
     tm.mark(STAGE_EVAL, 1, st);
     if (mode & 2) {
-        const LevelDev &L = pd.lev[pd.D];
-        int64_t nt = (int64_t)L.nact * P;
-        if (nt > 0) k_leaf<T, R, PS, PA><<<grid_for(nt, 128), 128, 0, st>>>(pd, nrhs, sig);
+        int64_t nt = launch_leaf<T, R, PS, PA>(pd, pd.D, nrhs, sig, st);
         tm.mark(STAGE_LEAF, nt > 0, st);
         for (int d = pd.D; d >= 3; --d) {
             NvtxRange range("targets and upward", d);
@@ -1301,7 +1508,8 @@ cudaError_t launch_forward(const PlanDev &pd, int nrhs, const void *sig, void *u
             if (d > 3) {
                 int64_t np = (int64_t)pd.lev[d - 1].nact * P;
                 if (np > 0) launch_upward<T, R, PS, PA>(pd, d, nrhs, np, st);
-                tm.mark(STAGE_UPWARD, np > 0, st);
+                const int64_t nl = launch_leaf<T, R, PS, PA>(pd, d - 1, nrhs, sig, st);
+                tm.mark(STAGE_UPWARD, (np > 0) + (nl > 0), st);
             }
         }
     }
@@ -1326,7 +1534,7 @@ cudaError_t launch_adjoint(const PlanDev &pd, int nrhs, const void *vs, void *ws
         tm.mark(STAGE_ADJ_LEVEL, nl, st);
     }
     if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
-    if (mode & 2) k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1);
+    if (mode & 2) k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1, -1);
     tm.mark(STAGE_ADJ_EVAL, 1 + ((mode & 3) == 3), st);
     return cudaGetLastError();
 }
@@ -1344,10 +1552,17 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
     const PlanDev &pd = p->dev;
     JitLists tl, ul;
     ifgf_status s = IFGF_OK;
+    // the conjugated near field first (it stores), then per level the adjoint values and,
+    // in adaptive trees, the sources whose leaf box lies on that level (they add)
+    if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
     if (mode & 2) {
         for (int d = 3; d <= pd.D && s == IFGF_OK; ++d) {
             const int nact = pd.lev[d].nact;
-            if (nact == 0) continue;
+            if (nact == 0) {
+                if (pd.adaptive || d == pd.D)
+                    k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1, d);
+                continue;
+            }
             NvtxRange range("adjoint level (lists built here)", d);
             s = ifgf_jit_targets(p, d, &tl, st);
             if (s != IFGF_OK) break;
@@ -1369,14 +1584,15 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                     if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
                 }
             }
+            // the sources of this level's leaves, before level d + 2 reuses the buffer
+            if (pd.adaptive || d == pd.D)
+                k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1, d);
             if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
         }
     }
     ifgf_jit_release(&tl);
     ifgf_jit_release(&ul);
     if (s != IFGF_OK) return s;
-    if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
-    if (mode & 2) k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1);
     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint launch"; return IFGF_ECUDA; }
     return IFGF_OK;
 }
@@ -1437,8 +1653,9 @@ __global__ void __launch_bounds__(128) k_build_tcache(PlanDev pd, int d)
     const LevelDev &L = pd.lev[d];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
-    const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     const int b = L.pt_box[i];
+    if (b < 0) return;  // a point of a coarser leaf: no cousin evaluations at this level
+    const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     int o = L.toff[i];
     for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e, ++o) {
         const int k = L.cous[e];
@@ -1485,12 +1702,8 @@ __global__ void __launch_bounds__(128) k_build_ucache(PlanDev pd, int d)
     const int pcone = Lp.act_cone[slot];
     for (int k = k0; k < k1; ++k) {
         const int oct = (int)(L.key[k] & 7u);
-        UpEntry<T, PS + 2 * PA> e;
-        cpx<T> f;
-        e.cone = up_geometry<T, PS, PA>(pd, L, Lp, pcone, node, oct, e.w, f);
-        e.fr = f.x;
-        e.fi = f.y;
-        ((UpEntry<T, PS + 2 * PA> *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)] = e;
+        ((typename UpEntryOf<T, PS + 2 * PA>::type *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * (k1 - k0) + (k - k0)] =
+            make_up_entry<T, PS, PA>(pd, L, Lp, pcone, node, oct);
     }
 }
 
@@ -1517,9 +1730,9 @@ cudaError_t build_uptable(const PlanDev &pd, int d, void *tab, cudaStream_t st)
     int64_t n = (int64_t)pd.lev[d].urows * 8 * pd.P;
     if (n == 0) return cudaSuccess;
     if (pd.Ps == 3 && pd.Pang == 5)
-        k_build_uptable<T, 3, 5><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (UpEntry<T, 13> *)tab);
+        k_build_uptable<T, 3, 5><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (typename UpEntryOf<T, 13>::type *)tab);
     else if (pd.Ps == 4 && pd.Pang == 7)
-        k_build_uptable<T, 4, 7><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (UpEntry<T, 18> *)tab);
+        k_build_uptable<T, 4, 7><<<grid_for(n, 128), 128, 0, st>>>(pd, d, (typename UpEntryOf<T, 18>::type *)tab);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -171,10 +171,7 @@ __device__ __forceinline__ RowData row_geometry(const PlanDev &pd, const LevelDe
         const int oct = (int)(L.key[L.act_box[j.slot]] & 7u);
         const int trow = tab ? table_row(L.ubits, L.urank, pcone) : -1;
         if (trow >= 0) {
-            const UpEntry<float, 13> &en = ((const UpEntry<float, 13> *)L.utab)[((size_t)trow * 8 + oct) * kP + node];
-#pragma unroll
-            for (int m = 0; m < 13; ++m) w[m] = en.w[m];
-            f = {en.fr, en.fi};
+            up_entry<float, 3, 5>(pd, ((const UpEntry32 *)L.utab)[((size_t)trow * 8 + oct) * kP + node], w, f);
         } else {
             up_geometry<float, 3, 5>(pd, L, *Lp, pcone, node, oct, w, f);
         }
@@ -515,22 +512,27 @@ __global__ void __launch_bounds__(128) k_near_tiled(PlanDev pd, int nrhs, const 
     __shared__ float2 sG[kNearTargets][kNearKT + 1];
     __shared__ __align__(16) float2 ssig[kNearKT * TX * RPT];
     __shared__ int sj[kNearKT];                              // the chunk's point indices
-    __shared__ int sbeg[27], spre[28];
-    const LevelDev &LD = pd.lev[pd.D];
+    __shared__ int sbeg[kMaxNearRanges], spre[kMaxNearRanges + 1];
+    __shared__ int snr;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int2 item = pd.near_tile[blockIdx.x];
+    const int4 item = pd.near_tile[blockIdx.x];
+    const LevelDev &LD = pd.lev[item.z];
     const int b = item.x, t0 = item.y;
-    const int nt = min(kNearTargets, LD.start[b + 1] - t0);
+    const int nt = min(kNearTargets, LD.end[b] - t0);
     const double *cb = LD.center + 3 * (size_t)b;
     const float kf = (float)pd.kappa;
-    if (tid < 32) near_ranges(LD, b, tid, sbeg, spre);
+    if (tid < 32) {
+        const int nr = near_ranges(LD, b, tid, sbeg, spre);
+        if (tid == 0) snr = nr;
+    }
     if (tid < nt) {
         const Rel32 p = rel32(pd.xs[t0 + tid], pd.ys[t0 + tid], pd.zs[t0 + tid], cb);
         sth[tid] = make_float4(p.hx, p.hy, p.hz, 0.f);
         stl[tid] = make_float4(p.lx, p.ly, p.lz, 0.f);
     }
     __syncthreads();
-    const int ns = spre[27];
+    const int nr = snr;
+    const int ns = spre[nr];
     float2 acc[TPT][RPT];
 #pragma unroll
     for (int i = 0; i < TPT; ++i)
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(128) k_near_tiled(PlanDev pd, int nrhs, const 
     for (int g0 = 0; g0 < ns; g0 += kNearKT) {
         const int cnt = min(kNearKT, ns - g0);
         if (tid < cnt) {
-            const int j = near_source(sbeg, spre, g0 + tid);
+            const int j = near_source(sbeg, spre, nr, g0 + tid);
             sj[tid] = j;
             const Rel32 p = rel32(pd.xs[j], pd.ys[j], pd.zs[j], cb);
             ssh[tid] = make_float4(p.hx, p.hy, p.hz, 0.f);
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
     for (int i = 0; i < NPT; ++i)
 #pragma unroll
         for (int k = 0; k < RPT; ++k) acc[i][k] = make_float2(0.f, 0.f);
-    const int j0 = L.start[b], j1 = L.start[b + 1];
+    const int j0 = L.start[b], j1 = L.end[b];
     for (int jb = j0; jb < j1; jb += kLeafKT) {
         const int cnt = min(kLeafKT, j1 - jb);
         __syncthreads();  // the previous chunk is consumed (and the node constants are written)

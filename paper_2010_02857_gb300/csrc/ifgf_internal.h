@@ -45,13 +45,27 @@ struct LevelDev {
     int nact = 0;           // relevant cones at this level
     double H = 0, h = 0, ds = 0, dth = 0;
     const uint64_t *key = nullptr;
-    const int *start = nullptr;
-    const int *pt_box = nullptr;
+    const int *start = nullptr;        // [nbox+1] first point of each box (start[nbox] = N)
+    const int *end = nullptr;          // [nbox] one past the last point of each box (start[b+1] in a
+                                       // uniform tree; adaptive trees have points of coarser leaves
+                                       // between the boxes of a level)
+    const unsigned char *leaf = nullptr;  // [nbox] the box is a leaf (not subdivided)
+    const int *pt_box = nullptr;       // [N] box of every point at this level, -1 for points of
+                                       // coarser leaves (adaptive trees)
     const int *parent = nullptr;
     const int *child_start = nullptr;
     const int *nbr = nullptr;          // [nbox][27]
     const int *cous_start = nullptr;
     const int *cous = nullptr;
+    // near field of the leaf boxes of this level (d >= 3): CSR of point ranges [lo, hi),
+    // ascending; the uniform tree's level-D lists are the 27 neighbours' ranges
+    const int *near_start = nullptr;
+    const int *near_lo = nullptr;
+    const int *near_hi = nullptr;
+    // relevant cone slots of the leaf boxes of this level (their analytic factors come from
+    // their points); nullptr with nleaf_slots = nact: every slot
+    const int *leaf_slots = nullptr;
+    int nleaf_slots = 0;
     const double *center = nullptr;    // [nbox][3]
     const double *cosk = nullptr;      // [nc+1]
     const float *coskf = nullptr;      // [nc+1] the same in FP32 (cell decisions of the FP32 path)
@@ -97,6 +111,9 @@ struct LevelDev {
 };
 
 constexpr int kNearTargets = 32;  // targets per near-field block
+// most near-field point ranges of one leaf box (its 27 neighbours, and in an adaptive tree
+// the leaf neighbours of its ancestors); plans that need more are rejected
+constexpr int kMaxNearRanges = 27 * 8;
 
 struct PlanDev {
     int n = 0, D = 0, Ps = 0, Pang = 0, P = 0;
@@ -109,9 +126,11 @@ struct PlanDev {
     const double *xs = nullptr, *ys = nullptr, *zs = nullptr;
     const float4 *leaf_off = nullptr;  // [N] x_j - centre of its leaf box, and its squared norm (FP32)
     const int *perm = nullptr;
-    // near-field work items: (leaf box, first target) for each run of at most
-    // kNearTargets consecutive targets of a level-D box
-    const int2 *near_tile = nullptr;
+    const int *ptlev = nullptr;        // [N] level of every point's leaf box (all D in a uniform tree)
+    int adaptive = 0;                  // the tree has leaves above level D
+    // near-field work items: (leaf box, first target, level) for each run of at most
+    // kNearTargets consecutive targets of a leaf box
+    const int4 *near_tile = nullptr;
     int n_near_tile = 0;
     int *err = nullptr;                                  // device invariant-failure counter
     int *sched = nullptr;  // [IFGF_MAX_LEVELS + 1] work counters of the batched cone kernel
@@ -171,6 +190,7 @@ struct LevelHost {
     int64_t cousin_evals = 0, upward_evals = 0;
     int64_t words = 0;
     int64_t table_rows = 0;   // rows of the upward table of step d -> d-1 (0: none)
+    int64_t union_rows = 0;   // distinct relevant cone ids of level d-1 (the rows a table would have)
 };
 
 struct ifgf_plan {
@@ -180,6 +200,7 @@ struct ifgf_plan {
     int precision = IFGF_FP64;
     int max_nrhs = 1;
     int flags = 0;
+    int leaf_max = 0;          // adaptive tree: boxes of level >= 3 with at most leaf_max points are leaves
     int device = 0;            // the CUDA device current at ifgf_plan_create (owns every buffer)
     double timeout_s = 0;      // host-side wait limit of an evaluation (0: none)
     size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
@@ -239,6 +260,18 @@ template <typename T, int NW> struct UpEntry {
     T fr, fi;
     int cone;
 };
+
+// The entry of FP32 plans (24 bytes): the local coordinates of the node in its child cone
+// and the re-centring factor; the Lagrange weights are expanded from the coordinates by
+// the same FP32 operations that would have produced stored weights.
+struct UpEntry32 {
+    float t[3];
+    float fr, fi;
+    int cone;
+};
+
+template <typename T, int NW> struct UpEntryOf { using type = UpEntry<T, NW>; };
+template <int NW> struct UpEntryOf<float, NW> { using type = UpEntry32; };
 
 // Cached geometry of one cousin-target evaluation.  FP64 plans: the Lagrange weights
 // and the centred factor; float plans: the local coordinates and the factor.

@@ -126,27 +126,71 @@ __global__ void k_gather_points(const double *pts, const int *idx, int n, double
     perm[i] = j;
 }
 
-// box boundaries of level d: flag[i] = 1 where the level key changes
-__global__ void k_level_flags(const uint64_t *leafkey, int n, int shift, int *flag)
+// Box boundaries of level d among the points that still lie in boxes of level d (their
+// leaf level ptlev >= d; all points in a uniform tree): flag[i] = 1 where such a point
+// starts a box, i.e. where the level key changes or the previous point lies in a coarser
+// leaf.
+__device__ __forceinline__ bool level_start(const uint64_t *leafkey, const int *ptlev, int i, int d, int shift)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    flag[i] = (i == 0 || (leafkey[i] >> shift) != (leafkey[i - 1] >> shift)) ? 1 : 0;
+    return ptlev[i] >= d && (i == 0 || ptlev[i - 1] < d || (leafkey[i] >> shift) != (leafkey[i - 1] >> shift));
 }
 
-// pt_box = inclusive scan - 1; scatter box starts and keys
-__global__ void k_level_boxes(const uint64_t *leafkey, const int *incl, int n, int shift, int *pt_box,
-                              int *start, uint64_t *key)
+__global__ void k_level_flags(const uint64_t *leafkey, const int *ptlev, int n, int d, int shift, int *flag)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    flag[i] = level_start(leafkey, ptlev, i, d, shift) ? 1 : 0;
+}
+
+// pt_box = inclusive scan - 1 (-1 for points of coarser leaves); box starts, ends and keys
+__global__ void k_level_boxes(const uint64_t *leafkey, const int *ptlev, const int *incl, int n, int d, int shift,
+                              int nbox, int *pt_box, int *start, int *end, uint64_t *key)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i == 0) start[nbox] = n;
+    if (ptlev[i] < d) {
+        pt_box[i] = -1;
+        return;
+    }
     int b = incl[i] - 1;
     pt_box[i] = b;
-    if (i == 0 || incl[i - 1] != incl[i]) {
+    if (level_start(leafkey, ptlev, i, d, shift)) {
         start[b] = i;
         key[b] = leafkey[i] >> shift;
     }
-    if (i == n - 1) start[b + 1] = n;
+    if (i == n - 1 || ptlev[i + 1] < d || (leafkey[i + 1] >> shift) != (leafkey[i] >> shift)) end[b] = i + 1;
+}
+
+// Leaves of level d: every box of level D; with leaf_max > 0 (adaptive tree), also the
+// boxes of levels 3..D-1 that hold at most leaf_max points.  The points of a leaf above
+// level D take its level as their leaf level.
+__global__ void k_level_leaves(const int *start, const int *end, int nbox, int d, int D, int leaf_max,
+                               unsigned char *leaf)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    leaf[b] = (d == D || (leaf_max > 0 && d >= 3 && end[b] - start[b] <= leaf_max)) ? 1 : 0;
+}
+
+__global__ void k_max_int(const int *v, int n, int *mx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(mx, v[i]);
+}
+
+__global__ void k_any_leaf(const unsigned char *leaf, int nbox, int *any)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox && leaf[b]) atomicExch(any, 1);
+}
+
+__global__ void k_mark_leaf_points(const int *pt_box, const unsigned char *leaf, int n, int d, int *ptlev)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = pt_box[i];
+    if (b >= 0 && leaf[b]) ptlev[i] = d;
 }
 
 // offset of every point from the centre of its leaf box, and its squared norm: formed
@@ -156,39 +200,100 @@ __global__ void k_leaf_offsets(PlanDev pd, float4 *off)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
-    const LevelDev &L = pd.lev[pd.D];
+    const LevelDev &L = pd.lev[pd.ptlev[i]];
     const double *c = L.center + 3 * (size_t)L.pt_box[i];
     double dx = pd.xs[i] - c[0], dy = pd.ys[i] - c[1], dz = pd.zs[i] - c[2];
     off[i] = make_float4((float)dx, (float)dy, (float)dz, (float)(dx * dx + dy * dy + dz * dz));
 }
 
-// Near-field work items: the targets of each leaf box in runs of kNearTargets.
-__global__ void k_near_tile_count(const int *start, int nbox, int *cnt)
+// Near-field work items: the targets of each leaf box of level d in runs of kNearTargets.
+__global__ void k_near_tile_count(const int *start, const int *end, const unsigned char *leaf, int nbox, int *cnt)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nbox) return;
-    cnt[b] = b < nbox ? (start[b + 1] - start[b] + kNearTargets - 1) / kNearTargets : 0;
+    cnt[b] = b < nbox && leaf[b] ? (end[b] - start[b] + kNearTargets - 1) / kNearTargets : 0;
 }
 
-__global__ void k_near_tile_emit(const int *start, int nbox, const int *tstart, int2 *tile)
+__global__ void k_near_tile_emit(const int *start, int nbox, int d, const int *tstart, int4 *tile)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
     for (int t = tstart[b]; t < tstart[b + 1]; ++t)
-        tile[t] = make_int2(b, start[b] + (t - tstart[b]) * kNearTargets);
+        tile[t] = make_int4(b, start[b] + (t - tstart[b]) * kNearTargets, d, 0);
+}
+
+// Near-field ranges of the leaf boxes of level l (the near relation of adaptive trees):
+// the points of every neighbour of the box at level l, and for each level d = 3..l-1 the
+// points of the leaf neighbours of its ancestor at level d; ascending by first point.
+// With leaves on level D only these are the 27 neighbours' ranges.
+template <bool FILL>
+__global__ void k_near_ranges(PlanDev pd, int l, int *count, const int *nstart, int *lo, int *hi)
+{
+    const LevelDev &L = pd.lev[l];
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= L.nbox) return;
+    if (!L.leaf[b]) {
+        if (!FILL) count[b] = 0;
+        return;
+    }
+    int m = 0;
+    const int o = FILL ? nstart[b] : 0;
+    auto add = [&](int s, int e) {
+        if (FILL) {  // insertion by first point (the lists are short)
+            int j = m;
+            while (j > 0 && lo[o + j - 1] > s) {
+                lo[o + j] = lo[o + j - 1];
+                hi[o + j] = hi[o + j - 1];
+                --j;
+            }
+            lo[o + j] = s;
+            hi[o + j] = e;
+        }
+        ++m;
+    };
+    for (int e = 0; e < 27; ++e) {
+        const int q = L.nbr[27 * (size_t)b + e];
+        if (q < 0) break;
+        add(L.start[q], L.end[q]);
+    }
+    int a = b;
+    for (int d = l - 1; d >= 3; --d) {
+        a = pd.lev[d + 1].parent[a];
+        const LevelDev &La = pd.lev[d];
+        for (int e = 0; e < 27; ++e) {
+            const int q = La.nbr[27 * (size_t)a + e];
+            if (q < 0) break;
+            if (La.leaf[q]) add(La.start[q], La.end[q]);
+        }
+    }
+    if (!FILL) count[b] = m;
+}
+
+// relevant cone slots of the leaf boxes of level d
+__global__ void k_leaf_slot_count(const int *act_start, const unsigned char *leaf, int nbox, int *cnt)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbox) return;
+    cnt[b] = b < nbox && leaf[b] ? act_start[b + 1] - act_start[b] : 0;
+}
+
+__global__ void k_leaf_slot_emit(const int *act_start, const unsigned char *leaf, int nbox, const int *off,
+                                 int *slots)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox || !leaf[b]) return;
+    for (int s = act_start[b]; s < act_start[b + 1]; ++s) slots[off[b] + s - act_start[b]] = s;
 }
 
 // Points must be pairwise distinct (Eq. field1 sums over m != l; the method's
-// factorisation divides by |x_l - x_m|).  Equal points share their Morton key and hence
-// their leaf box, so each point is compared with the later points of its leaf.
-__global__ void k_duplicates(PlanDev pd, int *found)
+// factorisation divides by |x_l - x_m|).  Equal points share their level-D Morton key,
+// so each point is compared with the later points of its key run.
+__global__ void k_duplicates(PlanDev pd, const uint64_t *leafkey, int *found)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
-    const LevelDev &L = pd.lev[pd.D];
     const double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
-    const int j1 = L.start[L.pt_box[i] + 1];
-    for (int j = i + 1; j < j1; ++j)
+    for (int j = i + 1; j < pd.n && leafkey[j] == leafkey[i]; ++j)
         if (pd.xs[j] == x && pd.ys[j] == y && pd.zs[j] == z) {
             atomicExch(found, 1);
             return;
@@ -202,13 +307,18 @@ __global__ void k_parents(const int *start, int nbox, const int *pt_box_parent, 
     parent[b] = pt_box_parent[start[b]];
 }
 
-// children of parent box p (level d-1) are the contiguous level-d boxes with parent p
+// children of parent box p (level d-1) are the contiguous level-d boxes with parent p:
+// child_start[p] = the first level-d box whose parent is >= p (leaves have none)
 __global__ void k_child_start(const int *parent, int nbox, int nparent, int *child_start)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    if (b == 0 || parent[b] != parent[b - 1]) child_start[parent[b]] = b;
-    if (b == nbox - 1) child_start[nparent] = nbox;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > nparent) return;
+    int lo = 0, hi = nbox;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (parent[mid] < p) lo = mid + 1; else hi = mid;
+    }
+    child_start[p] = lo;
 }
 
 // x_k^d = corner + (k + 1/2) H_d   (Eq. defboxsizesandcenters, 0-based k)
@@ -306,18 +416,21 @@ __global__ void k_activate_cousins(PlanDev pd, int d, uint64_t *bits)
     const LevelDev &L = pd.lev[d];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
-    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     int b = L.pt_box[i];
+    if (b < 0) return;  // a point of a coarser leaf (adaptive tree)
+    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e) {
         int k = L.cous[e];
         const double *c = L.center + 3 * (size_t)k;
-        ConeGeom g = cone_of(L, __dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2]));
+        ConeGeom g = cone_of_mixed(L, __dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2]));
         set_bit(bits, L.words, k, g.cone);
     }
 }
 
 // rule (ii): every interpolation point of a relevant parent cone marks its cone
-// around each child centre.
+// around each child centre.  Both activation kernels take cells from cone_of_mixed,
+// which equals the correctly rounded cone_of bit for bit (FP32 decisions only outside a
+// margin around the cell boundaries, cone_of inside it) at a fraction of its FP64 cost.
 __global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
 {
     const LevelDev &L = pd.lev[d];
@@ -330,7 +443,7 @@ __global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
     for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k) {
         double v[3];
         node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
-        ConeGeom g = cone_of(L, v[0], v[1], v[2]);
+        ConeGeom g = cone_of_mixed(L, v[0], v[1], v[2]);
         set_bit(bits, L.words, k, g.cone);
     }
 }
@@ -383,7 +496,7 @@ __global__ void k_count_cousin_evals(PlanDev pd, int d, unsigned long long *acc)
     unsigned long long v = 0;
     if (i < pd.n) {
         int b = L.pt_box[i];
-        v = (unsigned long long)(L.cous_start[b + 1] - L.cous_start[b]);
+        if (b >= 0) v = (unsigned long long)(L.cous_start[b + 1] - L.cous_start[b]);
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
@@ -391,16 +504,13 @@ __global__ void k_count_cousin_evals(PlanDev pd, int d, unsigned long long *acc)
 
 __global__ void k_count_near(PlanDev pd, unsigned long long *acc)
 {
-    const LevelDev &L = pd.lev[pd.D];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
     if (i < pd.n) {
+        const LevelDev &L = pd.lev[pd.ptlev[i]];
         int b = L.pt_box[i];
-        for (int e = 0; e < 27; ++e) {
-            int k = L.nbr[27 * (size_t)b + e];
-            if (k < 0) break;
-            v += (unsigned long long)(L.start[k + 1] - L.start[k]);
-        }
+        for (int e = L.near_start[b]; e < L.near_start[b + 1]; ++e)
+            v += (unsigned long long)(L.near_hi[e] - L.near_lo[e]);
         v -= 1;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -420,14 +530,14 @@ __global__ void k_count_upward(PlanDev pd, int d, unsigned long long *acc)
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
 }
 
-__global__ void k_count_leaf(PlanDev pd, unsigned long long *acc)
+__global__ void k_count_leaf(PlanDev pd, int d, unsigned long long *acc)
 {
-    const LevelDev &L = pd.lev[pd.D];
+    const LevelDev &L = pd.lev[d];
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
-    if (s < L.nact) {
+    if (s < L.nact && L.leaf[L.act_box[s]]) {
         int b = L.act_box[s];
-        v = (unsigned long long)(L.start[b + 1] - L.start[b]) * pd.P;
+        v = (unsigned long long)(L.end[b] - L.start[b]) * pd.P;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(acc, v);
@@ -444,8 +554,9 @@ __global__ void k_emit_tlist(PlanDev pd, int d, const int *off, int *keys, int *
     const LevelDev &L = pd.lev[d];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
-    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     int b = L.pt_box[i];
+    if (b < 0) return;  // a point of a coarser leaf
+    double x = pd.xs[i], y = pd.ys[i], z = pd.zs[i];
     int o = off[i];
     for (int e = L.cous_start[b]; e < L.cous_start[b + 1]; ++e, ++o) {
         int k = L.cous[e];
@@ -477,7 +588,7 @@ __global__ void k_point_cousin_count(PlanDev pd, int d, int *cnt)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.n) return;
     int b = L.pt_box[i];
-    cnt[i] = L.cous_start[b + 1] - L.cous_start[b];
+    cnt[i] = b < 0 ? 0 : L.cous_start[b + 1] - L.cous_start[b];
 }
 
 __global__ void k_parent_slot_count(PlanDev pd, int d, int *cnt)
@@ -640,6 +751,9 @@ static inline double cheb_node(int k, int n)
     return cos(((double)(2 * k + 1) * M_PI) / (double)(2 * n));
 }
 
+// device memory kept free at plan time for the adjoint's transpose lists and workspace
+constexpr size_t kReserveBytes = (size_t)24 << 30;
+
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
 {
     auto t0 = std::chrono::steady_clock::now();
@@ -731,13 +845,23 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
     k_gather_points<<<nblocks(n), kThreads, 0, st>>>(dpts, (int *)idxB.ptr, n, xs, ys, zs, perm);
     CK(cudaGetLastError());
 
-    // relevant boxes of every level
+    // relevant boxes of every level.  A box exists when its parent exists and is not a
+    // leaf (every box of levels 1..D-1 in a uniform tree); the points of a leaf above
+    // level D lie in no box of the finer levels (ptlev < d there).
+    DALLOC(ptlev, int, n);
+    {
+        std::vector<int> hD(n, D);
+        CK(cudaMemcpyAsync(ptlev, hD.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    pd.ptlev = ptlev;
+    pd.adaptive = 0;
     Scratch flag, incl;
     if (!flag.alloc((size_t)n * 4) || !incl.alloc((size_t)n * 4)) return IFGF_ENOMEM;
     for (int d = 1; d <= D; ++d) {
         LevelDev &L = pd.lev[d];
         int shift = 3 * (D - d);
-        k_level_flags<<<nblocks(n), kThreads, 0, st>>>(leafkey, n, shift, (int *)flag.ptr);
+        k_level_flags<<<nblocks(n), kThreads, 0, st>>>(leafkey, ptlev, n, d, shift, (int *)flag.ptr);
         CK(cudaGetLastError());
         ifgf_status s = cub_inclusive_sum(p, (int *)flag.ptr, (int *)incl.ptr, n, st);
         if (s != IFGF_OK) return s;
@@ -747,10 +871,16 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         p->lh[d].nbox = nbox;
         DALLOC(pt_box, int, n);
         DALLOC(start, int, nbox + 1);
-        DALLOC(key, uint64_t, nbox);
-        k_level_boxes<<<nblocks(n), kThreads, 0, st>>>(leafkey, (int *)incl.ptr, n, shift, pt_box, start, key);
+        DALLOC(bend, int, nbox + 1);
+        DALLOC(key, uint64_t, nbox + 1);
+        DALLOC(leaf, unsigned char, nbox + 1);
+        k_level_boxes<<<nblocks(n), kThreads, 0, st>>>(leafkey, ptlev, (int *)incl.ptr, n, d, shift, nbox, pt_box,
+                                                       start, bend, key);
+        k_level_leaves<<<nblocks(nbox), kThreads, 0, st>>>(start, bend, nbox, d, D, p->leaf_max, leaf);
+        if (d < D && d >= 3 && p->leaf_max > 0)
+            k_mark_leaf_points<<<nblocks(n), kThreads, 0, st>>>(pt_box, leaf, n, d, ptlev);
         CK(cudaGetLastError());
-        L.pt_box = pt_box; L.start = start; L.key = key;
+        L.pt_box = pt_box; L.start = start; L.end = bend; L.key = key; L.leaf = leaf;
         L.H = Hd[d];
         DALLOC(center, double, 3 * (size_t)nbox);
         k_centers<<<nblocks(nbox), kThreads, 0, st>>>(key, nbox, p->corner[0], p->corner[1], p->corner[2],
@@ -764,7 +894,7 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
     }
     {
         CK(cudaMemsetAsync(flag.ptr, 0, sizeof(int), st));
-        k_duplicates<<<nblocks(n), kThreads, 0, st>>>(pd, (int *)flag.ptr);
+        k_duplicates<<<nblocks(n), kThreads, 0, st>>>(pd, leafkey, (int *)flag.ptr);
         CK(cudaGetLastError());
         int dup = 0;
         CK(cudaMemcpy(&dup, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
@@ -779,7 +909,7 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         DALLOC(parent, int, L.nbox);
         k_parents<<<nblocks(L.nbox), kThreads, 0, st>>>(L.start, L.nbox, Lp.pt_box, parent);
         DALLOC(cstart, int, Lp.nbox + 1);
-        k_child_start<<<nblocks(L.nbox), kThreads, 0, st>>>(parent, L.nbox, Lp.nbox, cstart);
+        k_child_start<<<nblocks(Lp.nbox + 1), kThreads, 0, st>>>(parent, L.nbox, Lp.nbox, cstart);
         CK(cudaGetLastError());
         L.parent = parent;
         Lp.child_start = cstart;
@@ -790,19 +920,76 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaGetLastError());
         pd.leaf_off = off;
     }
+    // leaves above level D make the tree adaptive
+    for (int d = 3; d < D; ++d) {
+        int any = 0;
+        if (p->leaf_max > 0 && pd.lev[d].nbox > 0) {
+            Scratch c;
+            if (!c.alloc(sizeof(int))) return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(c.ptr, 0, sizeof(int), st));
+            k_any_leaf<<<nblocks(pd.lev[d].nbox), kThreads, 0, st>>>(pd.lev[d].leaf, pd.lev[d].nbox, (int *)c.ptr);
+            CK(cudaMemcpy(&any, c.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        }
+        if (any) pd.adaptive = 1;
+    }
+    // near-field ranges of the leaf boxes of every level, and the work items: runs of at
+    // most kNearTargets targets of a leaf box
     {
-        const LevelDev &L = pd.lev[D];
-        Scratch cnt, tstart;
-        if (!cnt.alloc((size_t)(L.nbox + 1) * 4) || !tstart.alloc((size_t)(L.nbox + 1) * 4)) return IFGF_ENOMEM;
-        k_near_tile_count<<<nblocks(L.nbox + 1), kThreads, 0, st>>>(L.start, L.nbox, (int *)cnt.ptr);
-        CK(cudaGetLastError());
-        ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)tstart.ptr, L.nbox + 1, st);
-        if (s != IFGF_OK) return s;
         int ntile = 0;
-        CK(cudaMemcpy(&ntile, (int *)tstart.ptr + L.nbox, sizeof(int), cudaMemcpyDeviceToHost));
-        DALLOC(tile, int2, ntile);
-        k_near_tile_emit<<<nblocks(L.nbox), kThreads, 0, st>>>(L.start, L.nbox, (int *)tstart.ptr, tile);
-        CK(cudaGetLastError());
+        Scratch tstarts[IFGF_MAX_LEVELS + 1];
+        int nt_level[IFGF_MAX_LEVELS + 1] = {};
+        for (int d = 3; d <= D; ++d) {
+            LevelDev &L = pd.lev[d];
+            const int nb = L.nbox;
+            Scratch cnt;
+            if (!cnt.alloc((size_t)(nb + 1) * 4)) return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nb + 1) * 4, st));
+            if (nb > 0) k_near_ranges<false><<<nblocks(nb), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr, nullptr, nullptr, nullptr);
+            CK(cudaGetLastError());
+            {
+                Scratch mx;
+                if (!mx.alloc(sizeof(int))) return IFGF_ENOMEM;
+                CK(cudaMemsetAsync(mx.ptr, 0, sizeof(int), st));
+                if (nb > 0) k_max_int<<<nblocks(nb), kThreads, 0, st>>>((int *)cnt.ptr, nb, (int *)mx.ptr);
+                int hmax = 0;
+                CK(cudaMemcpy(&hmax, mx.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+                if (hmax > kMaxNearRanges) {
+                    p->last_error = "a leaf box has more than " + std::to_string(kMaxNearRanges) +
+                                    " near-field ranges (use fewer levels or a smaller leaf_max)";
+                    return IFGF_EINVAL;
+                }
+            }
+            DALLOC(nstart, int, nb + 1);
+            ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, nstart, nb + 1, st);
+            if (s != IFGF_OK) return s;
+            int m = 0;
+            CK(cudaMemcpy(&m, nstart + nb, sizeof(int), cudaMemcpyDeviceToHost));
+            DALLOC(nlo, int, m + 1);
+            DALLOC(nhi, int, m + 1);
+            L.near_start = nstart;
+            L.near_lo = nlo;
+            L.near_hi = nhi;
+            if (nb > 0) k_near_ranges<true><<<nblocks(nb), kThreads, 0, st>>>(pd, d, nullptr, nstart, nlo, nhi);
+            CK(cudaGetLastError());
+            if (!tstarts[d].alloc((size_t)(nb + 1) * 4)) return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nb + 1) * 4, st));
+            k_near_tile_count<<<nblocks(nb + 1), kThreads, 0, st>>>(L.start, L.end, L.leaf, nb, (int *)cnt.ptr);
+            CK(cudaGetLastError());
+            s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)tstarts[d].ptr, nb + 1, st);
+            if (s != IFGF_OK) return s;
+            CK(cudaMemcpy(&nt_level[d], (int *)tstarts[d].ptr + nb, sizeof(int), cudaMemcpyDeviceToHost));
+            ntile += nt_level[d];
+        }
+        DALLOC(tile, int4, ntile + 1);
+        int o = 0;
+        for (int d = D; d >= 3; --d) {  // finest leaves first (the uniform tree: level D only)
+            if (nt_level[d] == 0) continue;
+            k_near_tile_emit<<<nblocks(pd.lev[d].nbox), kThreads, 0, st>>>(pd.lev[d].start, pd.lev[d].nbox, d,
+                                                                         (int *)tstarts[d].ptr, tile + o);
+            CK(cudaGetLastError());
+            o += nt_level[d];
+        }
+        CK(cudaStreamSynchronize(st));
         pd.near_tile = tile;
         pd.n_near_tile = ntile;
     }
@@ -931,6 +1118,26 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         k_act_start<<<nblocks(L.nbox + 1), kThreads, 0, st>>>(rank, L.nbox, L.words, nact, act_start);
         CK(cudaGetLastError());
         L.act_cone = act_cone; L.act_box = act_box; L.act_start = act_start;
+        // relevant cones of the leaf boxes (every slot of level D in a uniform tree)
+        if (!pd.adaptive) {
+            L.leaf_slots = nullptr;
+            L.nleaf_slots = d == D ? nact : 0;
+        } else {
+            Scratch lc;
+            if (!lc.alloc((size_t)(L.nbox + 1) * 4)) return IFGF_ENOMEM;
+            k_leaf_slot_count<<<nblocks(L.nbox + 1), kThreads, 0, st>>>(act_start, L.leaf, L.nbox, (int *)lc.ptr);
+            CK(cudaGetLastError());
+            DALLOC(loff, int, L.nbox + 1);
+            s = cub_exclusive_sum(p, (int *)lc.ptr, loff, L.nbox + 1, st);
+            if (s != IFGF_OK) return s;
+            int nls = 0;
+            CK(cudaMemcpy(&nls, loff + L.nbox, sizeof(int), cudaMemcpyDeviceToHost));
+            DALLOC(lslots, int, nls + 1);
+            if (L.nbox > 0) k_leaf_slot_emit<<<nblocks(L.nbox), kThreads, 0, st>>>(act_start, L.leaf, L.nbox, loff, lslots);
+            CK(cudaGetLastError());
+            L.leaf_slots = lslots;
+            L.nleaf_slots = nls;
+        }
     }
 
     // statistics of one apply
@@ -941,7 +1148,8 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         CK(cudaMemsetAsync(a, 0, sizeof(unsigned long long) * (IFGF_MAX_LEVELS + 4), st));
         for (int d = 3; d <= D; ++d) k_count_cousin_evals<<<nblocks(n), kThreads, 0, st>>>(pd, d, a + d);
         k_count_near<<<nblocks(n), kThreads, 0, st>>>(pd, a + 0);
-        k_count_leaf<<<nblocks(pd.lev[D].nact), kThreads, 0, st>>>(pd, a + 1);
+        for (int d = 3; d <= D; ++d)
+            if (pd.lev[d].nact > 0) k_count_leaf<<<nblocks(pd.lev[d].nact), kThreads, 0, st>>>(pd, d, a + 1);
         CK(cudaGetLastError());
         unsigned long long h[IFGF_MAX_LEVELS + 4];
         CK(cudaMemcpyAsync(h, a, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -958,11 +1166,74 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         for (int d = 4; d <= D; ++d) p->lh[d].upward_evals = (int64_t)h[d];
     }
 
+    // Value buffers.  All levels stay resident when that fits the budget; otherwise
+    // two buffers alternate between levels d and d-1 (the only two an evaluation
+    // step reads and writes), and right-hand sides are processed in chunks.
+    const size_t eb = ifgf_elem_bytes(p->precision);
+    size_t all_levels = 0, max_pair = 0, max_level = 0;
+    for (int d = 3; d <= D; ++d) {
+        size_t b = (size_t)pd.lev[d].nact * P * eb;
+        all_levels += b;
+        max_level = std::max(max_level, b);
+        if (d > 3) max_pair = std::max(max_pair, b + (size_t)pd.lev[d - 1].nact * P * eb);
+    }
+    if (D == 3) max_pair = max_level;
+    size_t budget = p->value_budget;
+    if (budget == 0) {
+        // 85% of the free memory less the sorted density and field buffers and a reserve
+        // for the adjoint's transpose lists and workspace; the upward tables and
+        // evaluation caches come after the values, from what is left
+        size_t freeb = 0, totalb = 0;
+        CK(cudaMemGetInfo(&freeb, &totalb));
+        const size_t sorted = (size_t)2 * n * p->max_nrhs * eb + std::min(kReserveBytes, totalb / 10);
+        budget = freeb > sorted ? (size_t)((freeb - sorted) * 0.85) : 0;
+    }
+    if (all_levels * p->max_nrhs <= budget) {
+        p->pingpong = false;
+        p->rhs_chunk = p->max_nrhs;
+    } else {
+        p->pingpong = true;
+        int64_t c = max_pair ? (int64_t)(budget / max_pair) : p->max_nrhs;
+        if (c < 1) { p->last_error = "cone values of two levels do not fit in device memory"; return IFGF_ENOMEM; }
+        // the fewest passes, then chunks as equal as possible (8 right-hand sides that fit
+        // 5 at a time run as 4 + 4)
+        const int64_t passes = (p->max_nrhs + std::min<int64_t>(c, p->max_nrhs) - 1) / std::min<int64_t>(c, p->max_nrhs);
+        p->rhs_chunk = (int)((p->max_nrhs + passes - 1) / passes);
+    }
+    if (p->flags & 8) {  // force ping-pong buffers (tests)
+        p->pingpong = true;
+        p->rhs_chunk = p->max_nrhs;
+    }
+    if (p->flags & 16) p->rhs_chunk = std::min(p->rhs_chunk, 2);  // force small chunks (tests)
+    pd.pingpong = p->pingpong ? 1 : 0;
+    size_t value_bytes = 0;  // forward cone values of all levels (plans that keep every level)
+    if (!p->pingpong) {
+        for (int d = 3; d <= D; ++d) {
+            LevelDev &L = pd.lev[d];
+            value_bytes += (size_t)L.nact * P * p->rhs_chunk * eb;
+            L.F = ifgf_dalloc(p, (size_t)L.nact * P * p->rhs_chunk * eb);
+            if (!L.F) { p->last_error = "cone value buffer"; return IFGF_ENOMEM; }
+        }
+    } else {
+        size_t even = 0, odd = 0;
+        for (int d = 3; d <= D; ++d) {
+            size_t b = (size_t)pd.lev[d].nact * P * p->rhs_chunk * eb;
+            if (d & 1) odd = std::max(odd, b); else even = std::max(even, b);
+        }
+        void *bufs[2] = {ifgf_dalloc(p, even), ifgf_dalloc(p, odd)};
+        if (!bufs[0] || !bufs[1]) { p->last_error = "cone value buffers"; return IFGF_ENOMEM; }
+        for (int d = 3; d <= D; ++d) pd.lev[d].F = bufs[d & 1];
+    }
+    p->sig_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
+    p->u_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
+    if (!p->sig_sorted || !p->u_sorted) { p->last_error = "sorted density buffers"; return IFGF_ENOMEM; }
+
     // Upward tables: the geometry of the step d -> d-1 depends only on (parent cone id,
     // child octant, node).  Tabulate it where the table has at most half as many
-    // entries as the level has upward evaluations per apply.
+    // entries as the level has upward evaluations per apply and takes at most half of
+    // the memory left after the value buffers (finest levels first).
     const size_t entry_bytes = ifgf_uptable_entry_bytes(p->precision, Ps, Pang);
-    for (int d = 4; d <= D; ++d) {
+    for (int d = D; d >= 4; --d) {
         LevelDev &L = pd.lev[d];
         LevelDev &Lp = pd.lev[d - 1];
         int64_t nw = Lp.words;
@@ -981,9 +1252,16 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         if (s != IFGF_OK) return s;
         int rows = 0;
         CK(cudaMemcpy(&rows, urank + nw, sizeof(int), cudaMemcpyDeviceToHost));
+        p->lh[d].union_rows = rows;
         int64_t entries = (int64_t)rows * 8 * P;
         size_t bytes = (size_t)entries * entry_bytes;
-        if ((p->flags & 2) || rows == 0 || 2 * entries > p->lh[d].upward_evals || bytes > ((size_t)8 << 30)) continue;
+        size_t freeb = 0, totalb = 0;
+        CK(cudaMemGetInfo(&freeb, &totalb));
+        // keep room for the adjoint's cone values, allocated on the first adjoint call
+        // (as large as the forward values of a plan that keeps every level)
+        const size_t reserve = std::min(kReserveBytes, totalb / 10) + (p->pingpong ? 0 : value_bytes);
+        const size_t room = freeb > reserve ? (freeb - reserve) / 2 : 0;
+        if ((p->flags & 2) || rows == 0 || 2 * entries > p->lh[d].upward_evals || bytes > room) continue;
         DALLOC(uids, int, rows);
         Scratch dummy;
         if (!dummy.alloc((size_t)rows * 4)) return IFGF_ENOMEM;
@@ -1062,59 +1340,6 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         }
     }
 
-    // Value buffers.  All levels stay resident when that fits the budget; otherwise
-    // two buffers alternate between levels d and d-1 (the only two an evaluation
-    // step reads and writes), and right-hand sides are processed in chunks.
-    const size_t eb = ifgf_elem_bytes(p->precision);
-    size_t all_levels = 0, max_pair = 0, max_level = 0;
-    for (int d = 3; d <= D; ++d) {
-        size_t b = (size_t)pd.lev[d].nact * P * eb;
-        all_levels += b;
-        max_level = std::max(max_level, b);
-        if (d > 3) max_pair = std::max(max_pair, b + (size_t)pd.lev[d - 1].nact * P * eb);
-    }
-    if (D == 3) max_pair = max_level;
-    size_t budget = p->value_budget;
-    if (budget == 0) {
-        size_t freeb = 0, totalb = 0;
-        CK(cudaMemGetInfo(&freeb, &totalb));
-        size_t sorted = (size_t)2 * n * p->max_nrhs * eb;
-        budget = freeb > sorted ? (size_t)((freeb - sorted) * 0.6) : 0;
-    }
-    if (all_levels * p->max_nrhs <= budget) {
-        p->pingpong = false;
-        p->rhs_chunk = p->max_nrhs;
-    } else {
-        p->pingpong = true;
-        int64_t c = max_pair ? (int64_t)(budget / max_pair) : p->max_nrhs;
-        if (c < 1) { p->last_error = "cone values of two levels do not fit in device memory"; return IFGF_ENOMEM; }
-        p->rhs_chunk = (int)std::min<int64_t>(c, p->max_nrhs);
-    }
-    if (p->flags & 8) {  // force ping-pong buffers (tests)
-        p->pingpong = true;
-        p->rhs_chunk = p->max_nrhs;
-    }
-    if (p->flags & 16) p->rhs_chunk = std::min(p->rhs_chunk, 2);  // force small chunks (tests)
-    pd.pingpong = p->pingpong ? 1 : 0;
-    if (!p->pingpong) {
-        for (int d = 3; d <= D; ++d) {
-            LevelDev &L = pd.lev[d];
-            L.F = ifgf_dalloc(p, (size_t)L.nact * P * p->rhs_chunk * eb);
-            if (!L.F) { p->last_error = "cone value buffer"; return IFGF_ENOMEM; }
-        }
-    } else {
-        size_t even = 0, odd = 0;
-        for (int d = 3; d <= D; ++d) {
-            size_t b = (size_t)pd.lev[d].nact * P * p->rhs_chunk * eb;
-            if (d & 1) odd = std::max(odd, b); else even = std::max(even, b);
-        }
-        void *bufs[2] = {ifgf_dalloc(p, even), ifgf_dalloc(p, odd)};
-        if (!bufs[0] || !bufs[1]) { p->last_error = "cone value buffers"; return IFGF_ENOMEM; }
-        for (int d = 3; d <= D; ++d) pd.lev[d].F = bufs[d & 1];
-    }
-    p->sig_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
-    p->u_sorted = ifgf_dalloc(p, (size_t)n * p->rhs_chunk * eb);
-    if (!p->sig_sorted || !p->u_sorted) { p->last_error = "sorted density buffers"; return IFGF_ENOMEM; }
     CK(cudaStreamSynchronize(st));
     int herr = 0;
     CK(cudaMemcpy(&herr, pd.err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -15,6 +15,9 @@ outputs the oracle computes one by one:
     (2e-5: FP32 values and accumulation).
   * cubes_64rhs (N = 1,572,864, 64 plane-wave right-hand sides, tensor cores): 2,048
     sampled targets per right-hand side against the direct sum (1e-3).
+  * prolate_128lambda_adaptive (the same spheroid on an adaptive octree, mixed): 4,096
+    sampled targets against the direct sum (1e-3), the adjoint on 256 sampled sources
+    against the direct adjoint (1e-3), and the adjoint identity on the GPU operator.
   * sphere_256lambda (N = 25,165,824, 8 right-hand sides, mixed; two-level buffers and
     right-hand-side chunks): 1,024 sampled targets per right-hand side against the
     direct sum (1e-3); 256 sampled sources of the adjoint per right-hand side against
@@ -46,7 +49,7 @@ def rel(a, b):
 
 def _plan(pkg, torch, wl, precision, **kw):
     g = pkg.Plan(torch.from_numpy(wl.points()).cuda(), wl.kappa, wl.levels, wl.p_radial, wl.p_angular,
-                 wl.leaf_ns, wl.leaf_nc, precision=precision, **kw)
+                 wl.leaf_ns, wl.leaf_nc, precision=precision, leaf_max=wl.leaf_max, **kw)
     if precision == "batched":
         g.autotune(wl.nrhs)
     g.set_graphs(True)
@@ -173,3 +176,25 @@ def test_sphere_256lambda_mixed_sampled_forward_adjoint(env):
     exa = oracle.direct_adjoint(pts, wl.kappa, v.astype(np.complex128), src)
     for r in range(wl.nrhs):
         assert rel(w[r, src], exa[r]) < 1e-3, (r, rel(w[r, src], exa[r]))
+
+
+def test_prolate_128lambda_adaptive_sampled(env):
+    torch, pkg = env
+    wl = wi.WORKLOADS["prolate_128lambda_adaptive"]
+    pts, sig = wl.points(), wl.densities()
+    g = _plan(pkg, torch, wl, "mixed")
+    st = g.stats()
+    assert st["adaptive"] == 1
+    s = torch.from_numpy(sig.astype(np.complex64)).cuda()
+    u = g.apply(s).cpu().numpy()
+    v = wi.complex_normal(wl.seed + 400, (1, wl.n)).astype(np.complex64)
+    w = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert g.check() == 0
+    lhs = np.vdot(v.astype(np.complex128), u.astype(np.complex128))
+    rhs = np.vdot(w.astype(np.complex128), sig)
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    del g
+    tg = wl.target_indices()
+    assert rel(u[:, tg], oracle.direct(pts, wl.kappa, sig, tg)) < 1e-3
+    src = tg[:256]
+    assert rel(w[:, src], oracle.direct_adjoint(pts, wl.kappa, v.astype(np.complex128), src)) < 1e-3

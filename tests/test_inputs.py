@@ -123,3 +123,16 @@ def test_named_workloads_are_deterministic(name):
     a, b = wl.points(), wl.points()
     assert a.shape == (wl.n, 3) and np.array_equal(a, b)
     assert np.all(np.isfinite(a))
+
+
+def test_row_blocks_of_a_batch_are_the_batch_rows():
+    # the densities a rank generates for its right-hand sides are exactly those rows of
+    # the whole batch, and the first nrhs rows of a larger batch are the workload's own
+    full = wi.complex_normal(41, (6, 1000))
+    assert np.array_equal(wi.complex_normal_rows(41, 6, 1000, 0, 6), full)
+    assert np.array_equal(wi.complex_normal_rows(41, 6, 1000, 2, 5), full[2:5])
+    wl = wi.small_sphere(500, 2, 3, nrhs=2)
+    assert np.array_equal(wl.densities((0, 2, 8)), wl.densities())
+    assert np.array_equal(wl.densities((3, 5, 8)), wi.complex_normal(wl.seed + 100, (8, 500))[3:5])
+    cubes = wi.Workload("c", 400, 1.0, 3, nrhs=4, surface="cubes", seed=4)
+    assert np.allclose(cubes.densities((1, 3, 4)), cubes.densities()[1:3], rtol=0, atol=0)
