@@ -293,7 +293,7 @@ def main():
                          "oracle's serial IFGF (Algorithm 1): plan build and full applies, one "
                          "right-hand side (OMP_NUM_THREADS sets its threads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed", "batched", "batched_fp16"],
                     help="override the workload's precision")
     ap.add_argument("--nrhs", type=int, default=None,
                     help="override the workload's number of right-hand sides (same generator)")
@@ -339,7 +339,7 @@ def main():
     evaluate = plan.apply if args.op == "apply" else plan.apply_adjoint
     # batched plans: the tile shapes come from the autotuner, timed on this plan
     tiles = None
-    if precision == "batched" and wl.nrhs % 2 == 0 and wl.nrhs <= 64:
+    if precision.startswith("batched") and wl.nrhs % 2 == 0 and wl.nrhs <= 64:
         t0 = time.perf_counter()
         tiles = plan.autotune(wl.nrhs)
         tiles["tune_s"] = time.perf_counter() - t0
@@ -410,7 +410,7 @@ def main():
                     "work": f"{up_evals + cousin_evals} transposed evaluations x {ADJOINT_FLOPS_PER_EVAL} flops "
                             f"per RHS, {ad_launches:.0f} launches, {ad_ms:.3f} ms"}
         up_ms = ad_ms
-    elif precision == "batched":
+    elif precision.startswith("batched"):
         # tcgen05 cone kernels: every cousin and upward evaluation is one GEMM row of
         # 75 weights x 2 nrhs real columns (useful flops; the BF16 hi/lo split and
         # the padding of K to 80 are not counted)
@@ -438,7 +438,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "mixed": "f32+f64", "batched": "bf16x3+f32+f64"}[precision],
+                "dtype": {"fp64": "f64", "mixed": "f32+f64", "batched": "bf16x3+f32+f64",
+                          "batched_fp16": "f16x3+f32+f64"}[precision],
                 "data": "synthetic",
                 "config": {"workload": wl.name, "op": args.op, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
                            "p_radial": wl.p_radial, "p_angular": wl.p_angular,

@@ -302,6 +302,17 @@ WORKLOADS = {
     "sphere_32lambda": Workload("sphere_32lambda", 393_216, wavelengths_to_kappa(2.0, 32), 8,
                                 leaf_ns=1, leaf_nc=2, targets=2_000, seed=2, surface="sphere",
                                 description="Fibonacci sphere N=393216, 32 lambda, D=8, FP64 + adjoint"),
+    # higher order (P_s, P_ang) = (4, 7), 196 points per cone, for the 1e-5..1e-6 accuracy
+    # range (the oracle gives 5.5e-5 with (1, 2) leaf cones and 3.6e-6 with (2, 4) on the
+    # 8-wavelength sphere)
+    "sphere_32lambda_p47": Workload("sphere_32lambda_p47", 393_216, wavelengths_to_kappa(2.0, 32), 8,
+                                    p_radial=4, p_angular=7, leaf_ns=1, leaf_nc=2, targets=2_000, seed=2,
+                                    surface="sphere",
+                                    description="Fibonacci sphere N=393216, 32 lambda, D=8, order (4,7), FP64"),
+    "sphere_8lambda_p47": Workload("sphere_8lambda_p47", 98_304, wavelengths_to_kappa(2.0, 8), 6,
+                                   p_radial=4, p_angular=7, leaf_ns=2, leaf_nc=4, targets=2_000, seed=6,
+                                   surface="sphere",
+                                   description="Fibonacci sphere N=98304, 8 lambda, D=6, order (4,7), (2,4) leaf cones, FP64"),
     # prolate spheroid 10:1:1, long axis 128 wavelengths, D = 10
     "prolate_128lambda": Workload("prolate_128lambda", 3_145_728, wavelengths_to_kappa(2.0, 128), 10,
                                   leaf_ns=1, leaf_nc=2, targets=4_096, seed=3, surface="prolate",

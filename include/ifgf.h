@@ -63,7 +63,12 @@ typedef enum {
      * nrhs and the adjoint run the IFGF_MIXED kernels); requires (P_s, P_ang) =
      * (3, 5).  Contributions are added to their destinations with FP32 atomic
      * reductions, so the last bits of the result vary from run to run. */
-    IFGF_BATCHED_BF16 = 2
+    IFGF_BATCHED_BF16 = 2,
+    /* IFGF_BATCHED_BF16 with FP16 operands: the hi + lo split keeps ~22 significant bits
+     * (~16 for BF16); each cone's values are scaled by a power of two into [-1, 1] before
+     * the split (FP16's exponent range is narrow) and the rows of the cone carry the
+     * inverse power. */
+    IFGF_BATCHED_FP16 = 3
 } ifgf_precision;
 
 typedef struct {
@@ -101,9 +106,12 @@ typedef struct {
                        issues no MMA, so its bounded waits for them run out (after a
                        shortened limit) and the device error counter records it
                        (testing; see ifgf_plan_check);
-                       bit 9: FP32 upward steps read the child cone values from L1
-                       instead of staging them in shared memory (testing: the two
-                       kernels sum in the same order). */
+                       bit 9: FP32 upward steps run one thread per parent node, reading
+                       the child cone values from L1, instead of one warp per parent cone
+                       in runs of nodes that share a child cone (testing: the two kernels
+                       sum in the same order);
+                       bit 10: the run kernel takes at most 8 runs per pass (testing:
+                       exercises its multi-pass path). */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels

@@ -26,9 +26,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libifgf.so")
 
-IFGF_FP64, IFGF_MIXED, IFGF_BATCHED_BF16 = 0, 1, 2
+IFGF_FP64, IFGF_MIXED, IFGF_BATCHED_BF16, IFGF_BATCHED_FP16 = 0, 1, 2, 3
 PRECISIONS = {"fp64": IFGF_FP64, "mixed": IFGF_MIXED, "batched": IFGF_BATCHED_BF16,
-              "batched_bf16": IFGF_BATCHED_BF16}
+              "batched_bf16": IFGF_BATCHED_BF16, "batched_fp16": IFGF_BATCHED_FP16}
 STATUS = {0: "IFGF_OK", 1: "IFGF_EINVAL", 2: "IFGF_ENOMEM", 3: "IFGF_ECUDA", 4: "IFGF_ETIMEOUT",
           5: "IFGF_EINTERNAL"}
 

@@ -85,8 +85,8 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         g_create_error = "supported (P_s, P_ang): (3, 5) and (4, 7)";
         return IFGF_EINVAL;
     }
-    if (opt && opt->precision == IFGF_BATCHED_BF16 && !(p_radial == 3 && p_angular == 5)) {
-        g_create_error = "IFGF_BATCHED_BF16 plans support (P_s, P_ang) = (3, 5)";
+    if (opt && ifgf_is_batched(opt->precision) && !(p_radial == 3 && p_angular == 5)) {
+        g_create_error = "batched (tensor-core) plans support (P_s, P_ang) = (3, 5)";
         return IFGF_EINVAL;
     }
     ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0, 0.0, 0};
@@ -95,7 +95,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     if (!(o.timeout_s >= 0.0)) { g_create_error = "timeout_s must be >= 0"; return IFGF_EINVAL; }
     if (o.max_nrhs <= 0) o.max_nrhs = 1;
     if (o.max_nrhs > 1024) { g_create_error = "max_nrhs must be <= 1024"; return IFGF_EINVAL; }
-    if (o.precision != IFGF_FP64 && o.precision != IFGF_MIXED && o.precision != IFGF_BATCHED_BF16) {
+    if (o.precision != IFGF_FP64 && o.precision != IFGF_MIXED && !ifgf_is_batched(o.precision)) {
         g_create_error = "unknown precision";
         return IFGF_EINVAL;
     }
@@ -104,7 +104,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         return IFGF_EINVAL;
     }
     if (o.leaf_max < 0) { g_create_error = "leaf_max must be >= 0"; return IFGF_EINVAL; }
-    if (o.leaf_max > 0 && o.precision == IFGF_BATCHED_BF16) {
+    if (o.leaf_max > 0 && ifgf_is_batched(o.precision)) {
         g_create_error = "adaptive trees (leaf_max > 0) are supported by IFGF_FP64 and IFGF_MIXED plans";
         return IFGF_EINVAL;
     }
@@ -121,6 +121,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     p->flags = o.flags;
     p->dev.flags = o.flags;
     p->leaf_max = o.leaf_max;
+    p->dev.batched_f16 = o.precision == IFGF_BATCHED_FP16 ? 1 : 0;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         cudaGetLastError();
         delete p;
@@ -163,8 +164,8 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     }
     ifgf_status s = ifgf_build_plan(p, points, st);
     // batched plans group evaluations by source cone with the transpose lists
-    if (s == IFGF_OK && ((o.flags & 1) || o.precision == IFGF_BATCHED_BF16)) s = ifgf_build_adjoint_lists(p, st);
-    if (s == IFGF_OK && o.precision == IFGF_BATCHED_BF16 && ifgf_batched_prepare() != cudaSuccess) {
+    if (s == IFGF_OK && ((o.flags & 1) || ifgf_is_batched(o.precision))) s = ifgf_build_adjoint_lists(p, st);
+    if (s == IFGF_OK && ifgf_is_batched(o.precision) && ifgf_batched_prepare() != cudaSuccess) {
         cudaGetLastError();
         p->last_error = "shared-memory limit of the tensor-core kernel";
         s = IFGF_ECUDA;
@@ -236,7 +237,7 @@ static cudaError_t launch_evaluation(ifgf_plan *p, const void *din, void *dout, 
         void *cout = (char *)dout + (size_t)c0 * p->n * eb;
         if (p->precision == IFGF_FP64)
             e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
-        else if (p->precision == IFGF_BATCHED_BF16 && !adjoint && nc % 2 == 0 && nc <= 64)
+        else if (ifgf_is_batched(p->precision) && !adjoint && nc % 2 == 0 && nc <= 64)
             e = ifgf_run_batched(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
         else
             e = ifgf_run_typed_f32(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
@@ -676,7 +677,7 @@ extern "C" ifgf_status ifgf_plan_autotune(ifgf_plan *plan, int nrhs, int reps, d
                                           void *stream)
 {
     if (!plan) return IFGF_EINVAL;
-    if (plan->precision != IFGF_BATCHED_BF16 || nrhs < 2 || nrhs > 64 || nrhs % 2 || nrhs > plan->max_nrhs ||
+    if (!ifgf_is_batched(plan->precision) || nrhs < 2 || nrhs > 64 || nrhs % 2 || nrhs > plan->max_nrhs ||
         reps < 1) {
         plan->last_error = "autotune: batched plan, even nrhs in [2, min(64, max_nrhs)] and reps >= 1";
         return IFGF_EINVAL;

@@ -491,6 +491,184 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
     }
 }
 
+// 8- and 16-byte asynchronous copies global -> shared (cp.async), and their wait
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"((uint64_t)__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// FP32 upward step with the children's cone values staged in shared memory (used where
+// the geometry is computed on the fly: one node per lane keeps the FP64 work of the
+// geometry dense in every warp).
+//
+// The thread layout and the arithmetic are those of k_upward (one thread per (parent
+// slot, node); children in order; the same sum-factorised contraction), but a warp
+// reads cone values from shared memory instead of from L1.  In k_upward the 32 lanes of
+// a warp interpolate, at each child step, from the 2-3 child cones their nodes fall in,
+// so every value load costs 2-3 L1 wavefronts and the kernel is bound by L1 throughput.
+// Here, at each child step, the warp finds the distinct child slots of its lanes
+// (__match_any_sync), copies the values of up to kUpStage of them into its shared-memory
+// stage (coalesced 16-byte or 8-byte loads), and each lane contracts from its cone's
+// copy.  A staged cone takes P * nrhs complex values; the copies follow one another
+// without padding, so the copies start 600 * nrhs (mod 32) banks apart: for nrhs = 1..4
+// the same node of up to four cones lies in disjoint banks, and a warp's load is one
+// shared-memory wavefront whichever of the staged cones its lanes read.  Lanes whose
+// cone is beyond the first kUpStage distinct ones (rare) read from global memory.  Every
+// lane sums its children in the same order with the same operations as k_upward.
+// nrhs <= R <= 4.
+constexpr int kUpStage = 4;
+constexpr int kUpWarps = 4;
+
+template <int R, int PS, int PA>
+__device__ __forceinline__ void contract_staged(const float2 *s, int nrhs, const float *ws, const float *wt,
+                                                const float *wp, cpx<float> *out)
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[r] = {0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < PS; ++a) {
+        cpx<float> mid[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) mid[r] = {0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < PA; ++b) {
+            cpx<float> in[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) in[r] = {0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < PA; ++c) {
+                const int idx = (a * PA + b) * PA + c;
+                if (R == 4 && nrhs == 4) {
+                    const float4 v01 = reinterpret_cast<const float4 *>(s)[idx * 2];
+                    const float4 v23 = reinterpret_cast<const float4 *>(s)[idx * 2 + 1];
+                    const float v[8] = {v01.x, v01.y, v01.z, v01.w, v23.x, v23.y, v23.z, v23.w};
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        in[r].x += wp[c] * v[2 * r];
+                        in[r].y += wp[c] * v[2 * r + 1];
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (R == 1 || r < nrhs) {
+                            const float2 v = s[idx * nrhs + r];
+                            in[r].x += wp[c] * v.x;
+                            in[r].y += wp[c] * v.y;
+                        }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) { mid[r].x += wt[b] * in[r].x; mid[r].y += wt[b] * in[r].y; }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) { out[r].x += ws[a] * mid[r].x; out[r].y += ws[a] * mid[r].y; }
+    }
+}
+
+template <int R, int PS, int PA, bool TAB>
+__global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int d, int nrhs)
+{
+    constexpr int P = PS * PA * PA;
+    constexpr int NW = PS + 2 * PA;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) float2 s_up_stage[];
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = t < (int64_t)Lp.nact * P;
+    if (__all_sync(kFull, !valid)) return;  // whole warps past the end
+    const int slot = valid ? (int)(t / P) : 0, node = valid ? (int)(t % P) : 0;
+    const int j = valid ? Lp.act_box[slot] : 0;
+    const int pcone = valid ? Lp.act_cone[slot] : 0;
+    const UpEntry32 *tab = nullptr;
+    if constexpr (TAB) {
+        if (valid) {
+            const int row = table_row(L.ubits, L.urank, pcone);
+            if (row < 0) { atomicAdd(pd.err, 1); valid = false; }
+            else tab = (const UpEntry32 *)L.utab + (size_t)row * 8 * P + node;
+        }
+    }
+    const int k0 = valid ? Lp.child_start[j] : 0;
+    const int nch = valid ? Lp.child_start[j + 1] - k0 : 0;
+    const int maxch = __reduce_max_sync(kFull, nch);
+    const int vals = P * nrhs;  // complex values per staged cone
+    float2 *stg = s_up_stage + (size_t)warp * kUpStage * vals;
+    cpx<float> acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = {0.f, 0.f};
+    for (int kk = 0; kk < maxch; ++kk) {
+        int sl = -1;
+        float w[NW];
+        cpx<float> f = {0.f, 0.f};
+        if (kk < nch) {
+            const int k = k0 + kk;
+            const int oct = (int)(L.key[k] & 7u);
+            int cone;
+            if constexpr (TAB) {
+                cone = up_entry<float, PS, PA>(pd, tab[(size_t)oct * P], w, f);
+            } else if (L.ucache) {
+                cone = up_entry<float, PS, PA>(
+                    pd, ((const UpEntry32 *)L.ucache)[(size_t)L.uoff[slot] + (size_t)node * nch + kk], w, f);
+            } else {
+                cone = up_geometry<float, PS, PA>(pd, L, Lp, pcone, node, oct, w, f);
+            }
+            sl = cone_slot(L, k, cone);
+            if (sl < 0) atomicAdd(pd.err, 1);
+        }
+        // the warp's distinct child slots; the first kUpStage are staged
+        const unsigned same = __match_any_sync(kFull, sl);
+        const int leader = __ffs(same) - 1;
+        const unsigned leaders = __ballot_sync(kFull, lane == leader && sl >= 0);
+        const int mine = sl >= 0 ? __popc(leaders & ((1u << leader) - 1u)) : -1;
+        const int nst = min(__popc(leaders), kUpStage);
+        unsigned rem = leaders;
+        for (int g = 0; g < nst; ++g) {
+            const int src = __ffs(rem) - 1;
+            rem &= rem - 1u;
+            const int gsl = __shfl_sync(kFull, sl, src);
+            const float2 *from = (const float2 *)L.F + (size_t)gsl * vals;
+            float2 *to = stg + (size_t)g * vals;
+            if ((vals & 1) == 0) {
+                for (int e = lane; e < vals / 2; e += 32)
+                    reinterpret_cast<float4 *>(to)[e] = __ldg(reinterpret_cast<const float4 *>(from) + e);
+            } else {
+                for (int e = lane; e < vals; e += 32) to[e] = __ldg(from + e);
+            }
+        }
+        __syncwarp();
+        if (sl >= 0) {
+            cpx<float> val[R];
+            if (mine < kUpStage) contract_staged<R, PS, PA>(stg + (size_t)mine * vals, nrhs, w, w + PS, w + PS + PA, val);
+            else contract<float, R, PS, PA>(L.F, (size_t)sl * P, nrhs, 0, w, w + PS, w + PS + PA, val);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cpx<float> m = cmul(f, val[r]);
+                acc[r].x += m.x;
+                acc[r].y += m.y;
+            }
+        }
+        __syncwarp();  // the stage is read before the next child step overwrites it
+    }
+    if (valid) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (R == 1 || r < nrhs) st<float>(Lp.F, ((size_t)slot * P + node) * nrhs + r, acc[r]);
+    }
+}
+
 // FP32 upward step, one warp per parent cone slot, in runs of nodes that share a child cone.
 //
 // k_upward gives each thread one (parent slot, node) and interpolates, child by child, from
@@ -512,7 +690,7 @@ __global__ void __launch_bounds__(128) k_upward(PlanDev pd, int d, int nrhs)
 // from global memory; more than 32 runs (rare) take a second pass.
 constexpr int kRunK = 3;
 constexpr int kRunStage = 4;
-constexpr int kRunWarps = 4;
+constexpr int kRunWarps = 2;  // 2 x 14.3 KB of shared memory per CTA (4 right-hand sides), under the 48 KB default
 
 // the run's evaluations: values src[node][r] (r < nrhs) of one child cone, per evaluation e
 // the weights ws[e] (PS), wt[e] (PA), wp[e] (PA); out[e][r]
@@ -587,16 +765,22 @@ __device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)
     }
 }
 
-// Shared memory of one warp of k_upward_runs for P nodes and nrhs right-hand sides.
+// Shared memory of one warp of k_upward_runs for P nodes and nrhs right-hand sides, in this
+// order (each array starts on a boundary of its element type; 8-byte arrays first):
+//   stage [kRunStage][P][nrhs] complex   (16-byte aligned: the 16-byte copies)
+//   acc   [P][R] complex, f [P] complex  (8 bytes)
+//   t     [P][3] float, slot [P], runs [32][kRunK], run group [32]  (4 bytes)
+// The warp's block is a multiple of 16 bytes, so every warp's stage stays 16-byte aligned.
 __host__ __device__ constexpr size_t run_stage_floats(int P, int nrhs) { return (size_t)kRunStage * P * nrhs * 2; }
 __host__ __device__ constexpr size_t run_warp_bytes(int P, int R, int nrhs)
 {
-    // stage, accumulators [P][R] complex, geometry t[P][3] + f[P][2] floats, slots [P], runs [32][kRunK]
-    return (run_stage_floats(P, nrhs) + (size_t)P * R * 2 + (size_t)P * 5) * 4 + (size_t)P * 4 + 32 * kRunK * 4 + 32 * 4;
+    // ... plus two buffers of the next child's P table entries (24 bytes each, prefetched)
+    return ((run_stage_floats(P, nrhs) + (size_t)P * R * 2 + (size_t)P * 2 + (size_t)P * 3) * 4 + (size_t)P * 4 +
+            32 * kRunK * 4 + 32 * 4 + 2 * (size_t)P * sizeof(UpEntry32) + 15) / 16 * 16;
 }
 
 template <int R, int PS, int PA, bool TAB>
-__global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, int d, int nrhs)
+__global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, int d, int nrhs)
 {
     constexpr int P = PS * PA * PA;
     constexpr int NW = PS + 2 * PA;
@@ -612,11 +796,12 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
     float *base = (float *)((unsigned char *)s_runs_raw + (size_t)warp * run_warp_bytes(P, R, nrhs));
     float2 *stage = (float2 *)base;
     float2 *acc = (float2 *)(base + run_stage_floats(P, nrhs));  // [P][R]
-    float *gt = (float *)(acc + (size_t)P * R);                 // [P][3]
-    float2 *gf = (float2 *)(gt + (size_t)P * 3);               // [P]
-    int *gsl = (int *)(gf + P);                                 // [P]
+    float2 *gf = acc + (size_t)P * R;                           // [P]
+    float *gt = (float *)(gf + P);                              // [P][3]
+    int *gsl = (int *)(gt + (size_t)P * 3);                     // [P]
     int *runs = gsl + P;                                        // [32][kRunK]
     int *rgrp = runs + 32 * kRunK;                              // [32] group of each run
+    UpEntry32 *graw = (UpEntry32 *)(rgrp + 32);                 // [2][P] table entries of a child
     const int j = Lp.act_box[slot];
     const int pcone = Lp.act_cone[slot];
     const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
@@ -630,9 +815,27 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
         tab = (const UpEntry32 *)L.utab + (size_t)row * 8 * P;
     }
     for (int q = lane; q < P * R; q += 32) acc[q] = make_float2(0.f, 0.f);
+    const int rmax = (pd.flags & 1024) ? 8 : 32;  // runs per pass (flags bit 10: 8, testing)
+    // the table entries of child kk + 1 are copied (asynchronously, 8 bytes at a time: an
+    // entry block starts on an 8-byte boundary) while child kk is contracted
+    auto prefetch_entries = [&](int kk2) {
+        if constexpr (TAB) {
+            if (kk2 < nch) {
+                const int oct2 = (int)(L.key[k0 + kk2] & 7u);
+                const uint2 *from = (const uint2 *)(tab + (size_t)oct2 * P);
+                uint2 *to = (uint2 *)(graw + (size_t)(kk2 & 1) * P);
+                for (int q = lane; q < P * 3; q += 32) cp_async8(to + q, from + q);
+            }
+        }
+    };
+    prefetch_entries(0);
     for (int kk = 0; kk < nch; ++kk) {
         const int k = k0 + kk;
         const int oct = (int)(L.key[k] & 7u);
+        if constexpr (TAB) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
         // A. geometry of the P nodes
         int sl_c[NCH];
 #pragma unroll
@@ -644,7 +847,7 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
                 cpx<float> f;
                 int cone;
                 if constexpr (TAB) {
-                    const UpEntry32 en = tab[(size_t)oct * P + node];
+                    const UpEntry32 en = graw[(size_t)(kk & 1) * P + node];
                     tl[0] = en.t[0]; tl[1] = en.t[1]; tl[2] = en.t[2];
                     f = {en.fr, en.fi};
                     cone = en.cone;
@@ -694,35 +897,37 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
                 if (mem) {
                     const int rank = before + __popc(m & ((1u << lane) - 1u));
                     const int run = nruns + rank / kRunK;
-                    if (run < 32) runs[run * kRunK + rank % kRunK] = lane + 32 * c;
+                    if (run < rmax) runs[run * kRunK + rank % kRunK] = lane + 32 * c;
                 }
                 before += __popc(m);
                 pend[c] &= ~m;
             }
             const int nr = (before + kRunK - 1) / kRunK;
-            for (int q = nruns + lane; q < nruns + nr && q < 32; q += 32) rgrp[q] = g;
-            // C. stage this group's cone values
+            for (int q = nruns + lane; q < nruns + nr && q < rmax; q += 32) rgrp[q] = g;
+            // C. stage this group's cone values (asynchronous copies: the groups' loads
+            // overlap, and all complete at the wait below)
             if (g < kRunStage) {
                 const int vals = P * nrhs;
                 const float2 *from = (const float2 *)L.F + (size_t)g_sl * vals;
                 float2 *to = stage + (size_t)g * vals;
                 if ((vals & 1) == 0) {
-                    for (int q = lane; q < vals / 2; q += 32)
-                        reinterpret_cast<float4 *>(to)[q] = __ldg(reinterpret_cast<const float4 *>(from) + q);
+                    for (int q = lane; q < vals / 2; q += 32) cp_async16(to + 2 * q, from + 2 * q);
                 } else {
-                    for (int q = lane; q < vals; q += 32) to[q] = __ldg(from + q);
+                    for (int q = lane; q < vals; q += 32) cp_async8(to + q, from + q);
                 }
             }
             nruns += nr;
         }
+        cp_async_wait_all();
         __syncwarp();
-        // D. the runs (a second pass when a child step has more than 32)
-        for (int pass = 0; pass * 32 < nruns; ++pass) {
+        prefetch_entries(kk + 1);
+        // D. the runs (more passes when a child step has more than rmax)
+        for (int pass = 0; pass * rmax < nruns; ++pass) {
             if (pass > 0) {  // rebuild the runs beyond the first 32 from the groups
                 __syncwarp();
                 for (int q = lane; q < 32 * kRunK; q += 32) runs[q] = -1;
                 __syncwarp();
-                int cnt = 0, g = 0, prev = -1;
+                int cnt = 0, g = 0;
                 if (lane == 0) {
                     // nodes in group order, node order within a group: run index r counts on
                     for (int gg = 0; gg < ngroups; ++gg) {
@@ -742,8 +947,8 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
                         int rank = 0;
                         for (int node = 0; node < P; ++node) {
                             if (gsl[node] != sl0) continue;
-                            const int run = cnt + rank / kRunK - 32 * pass;
-                            if (run >= 0 && run < 32) {
+                            const int run = cnt + rank / kRunK - rmax * pass;
+                            if (run >= 0 && run < rmax) {
                                 runs[run * kRunK + rank % kRunK] = node;
                                 rgrp[run] = gg;
                             }
@@ -751,12 +956,11 @@ __global__ void __launch_bounds__(32 * kRunWarps, 4) k_upward_runs(PlanDev pd, i
                         }
                         cnt += (rank + kRunK - 1) / kRunK;
                     }
-                    (void)prev;
                 }
                 __syncwarp();
             }
             const int r = lane;
-            if (pass * 32 + r < nruns) {
+            if (r < rmax && pass * rmax + r < nruns) {
                 int nodes[kRunK];
                 float w[kRunK][NW];
 #pragma unroll
@@ -808,15 +1012,22 @@ template <typename T, int R, int PS, int PA>
 inline void launch_upward(const PlanDev &pd, int d, int nrhs, int64_t np, cudaStream_t st)
 {
     if constexpr (sizeof(T) == 4 && R <= 4) {
-        if (nrhs <= R && !(pd.flags & 512)) {
-            constexpr int P = PS * PA * PA;
+        constexpr int P = PS * PA * PA;
+        const size_t smem = (size_t)kRunWarps * run_warp_bytes(P, R, nrhs);
+        // within the default 48 KB of dynamic shared memory (all of (3, 5); (4, 7) up to 2
+        // right-hand sides); larger configurations run k_upward
+        if (nrhs <= R && !(pd.flags & 512) && smem <= 48 * 1024) {
             const int nslot = pd.lev[d - 1].nact;
-            const size_t smem = (size_t)kRunWarps * run_warp_bytes(P, R, nrhs);
             const int grid = (nslot + kRunWarps - 1) / kRunWarps;
-            if (pd.lev[d].utab)
+            if (pd.lev[d].utab) {
                 k_upward_runs<R, PS, PA, true><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
-            else
+            } else if (pd.lev[d].ucache) {
                 k_upward_runs<R, PS, PA, false><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
+            } else {
+                // geometry on the fly: the staged kernel (one node per lane)
+                const size_t ssmem = (size_t)kUpWarps * kUpStage * P * nrhs * sizeof(float2);
+                k_upward_staged<R, PS, PA, false><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, ssmem, st>>>(pd, d, nrhs);
+            }
             return;
         }
     }
@@ -855,23 +1066,6 @@ inline int64_t launch_leaf(const PlanDev &pd, int d, int nrhs, const void *sig, 
 constexpr int kNearTile = 128;
 constexpr int kNearThreads = 128;
 static_assert(kNearThreads >= kNearTargets, "every target of a work item needs a thread");
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"((uint64_t)__cvta_generic_to_global(src))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"((uint64_t)__cvta_generic_to_global(src))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-}
 
 // The sources of the near field of leaf box b of level LD as one list (one warp, the
 // first of the block): the box's near ranges [near_lo, near_hi) (its neighbours'

@@ -1,4 +1,4 @@
-// Batched right-hand sides on tensor cores (IFGF_BATCHED_BF16 plans).
+// Batched right-hand sides on tensor cores (IFGF_BATCHED_BF16 and IFGF_BATCHED_FP16 plans).
 //
 // With many right-hand sides the interpolation of Algorithm 1 is a set of small
 // dense contractions that share their cone values: every evaluation that reads
@@ -16,7 +16,10 @@
 // chunks of 128 rows.  For each cone B goes to shared memory as BF16 hi + lo parts;
 // for each chunk A (hi + lo) is written and one thread issues tcgen05.mma
 // (kind::f16, BF16 inputs, FP32 accumulation in tensor memory): Ahi Bhi + Ahi Blo +
-// Alo Bhi per K block of 16, which keeps ~16 significant bits of both operands.
+// Alo Bhi per K block of 16, which keeps ~16 significant bits of both operands.  With
+// FP16 operands (IFGF_BATCHED_FP16) the hi + lo split keeps ~22 bits; the values of
+// each cone are scaled by a power of two into [-1, 1] (FP16's range is narrow) and the
+// row factors of its chunks carry the inverse power.
 // While the tensor cores run, the threads compute the rows of the CTA's next chunk.
 // The epilogue reads the accumulator with tcgen05.ld, multiplies each row by its
 // complex factor, transposes 32 rows through shared memory and adds them to their
@@ -30,6 +33,7 @@
 // computed once per pair and broadcast; the leaf factors by blocks that stage a chunk
 // of sources' densities and factors in shared memory and contract them from there.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ifgf_apply_impl.cuh"
 
@@ -58,21 +62,27 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: FP32 accumulate, BF16 A and B, A K-major, B MN-major
-__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
+// instruction descriptor: FP32 accumulate, A and B both BF16 (F16 = false) or both FP16
+// (F16 = true), A K-major, B MN-major
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N, bool f16 = false)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void bf16_split(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+// x = hi + lo + O(2^-16 |x|) in BF16 (F16 = false), or + O(2^-22 |x|) in FP16 (F16 = true,
+// for |x| within the FP16 range: the cone values are scaled into [-1, 1] per cone)
+template <bool F16> __device__ __forceinline__ uint32_t split_hi_lo(float x, uint16_t &lo)
 {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
-{
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    if constexpr (F16) {
+        const __half h = __float2half_rn(x);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+        return __half_as_ushort(h);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+        return __bfloat16_as_ushort(h);
+    }
 }
 
 // A (kM x kK, K-major): element (m, k) at (m/8)*SBO_A + (k/8)*128 + (m%8)*16 + (k%8)*2
@@ -182,8 +192,9 @@ __device__ __forceinline__ RowData row_geometry(const PlanDev &pd, const LevelDe
     return rd;
 }
 
-// A row `row` from its weights: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c, as BF16
-// hi and lo parts; zero for an empty row and for the padding columns p >= 75
+// A row `row` from its weights: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c, as hi and
+// lo parts (BF16 or FP16); zero for an empty row and for the padding columns p >= 75
+template <bool F16>
 __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row, unsigned char *A_hi,
                                             unsigned char *A_lo)
 {
@@ -192,7 +203,7 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
         uint32_t hv[4], lv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            float x2[2];
+            uint32_t h2[2], l2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int p = kc * 8 + q * 2 + h;
@@ -201,13 +212,12 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
                     const int ia = p / 25, ib = (p / 5) % 5, ic = p % 5;
                     x = w[ia] * w[3 + ib] * w[8 + ic];
                 }
-                x2[h] = x;
+                uint16_t lo;
+                h2[h] = split_hi_lo<F16>(x, lo);
+                l2[h] = lo;
             }
-            __nv_bfloat16 h0, l0, h1, l1;
-            bf16_split(x2[0], h0, l0);
-            bf16_split(x2[1], h1, l1);
-            hv[q] = pack2(h0, h1);
-            lv[q] = pack2(l0, l1);
+            hv[q] = h2[0] | (h2[1] << 16);
+            lv[q] = l2[0] | (l2[1] << 16);
         }
         const uint32_t off = a_off(row, kc * 8);
         *(uint4 *)(A_hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
@@ -215,13 +225,14 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
     }
 }
 
-// The cone's values as B (hi, lo): complex -> (re, im) columns 2r, 2r+1.  Lane l of a
-// warp converts (p, r) = (8 pb + l / 4, 4 rb + l % 4) of a tile (pb, rb), so that its
-// 32 four-byte stores fill one core matrix (no bank conflicts) and its loads read
+// The cone's values as B (hi, lo), times `scale`: complex -> (re, im) columns 2r, 2r+1.
+// Lane l of a warp converts (p, r) = (8 pb + l / 4, 4 rb + l % 4) of a tile (pb, rb), so
+// that its 32 four-byte stores fill one core matrix (no bank conflicts) and its loads read
 // eight 32-byte runs.  Batches of kBatch independent loads per thread before any
 // conversion; nt threads (a multiple of 32) take part, t is this thread's index.
+template <bool F16>
 __device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrhs, int npad, uint32_t lbo_b,
-                                            unsigned char *B_hi, unsigned char *B_lo, int t, int nt)
+                                            unsigned char *B_hi, unsigned char *B_lo, int t, int nt, float scale)
 {
     const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
     const int ntr = npad / 8;               // r tiles of 4: npad / 2 columns pairs
@@ -239,15 +250,29 @@ __device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrh
             const int idx = base + u * nt, tile = idx >> 5, l = idx & 31;
             const int p = (tile / ntr) * 8 + (l >> 2), r = (tile % ntr) * 4 + (l & 3);
             if (idx < tot && p < kP) {
-                __nv_bfloat16 h0, l0, h1, l1;
-                bf16_split(v[u].x, h0, l0);
-                bf16_split(v[u].y, h1, l1);
+                uint16_t l0, l1;
+                const uint32_t h0 = split_hi_lo<F16>(v[u].x * scale, l0);
+                const uint32_t h1 = split_hi_lo<F16>(v[u].y * scale, l1);
                 const uint32_t off = b_off(p, 2 * r, lbo_b);
-                *(uint32_t *)(B_hi + off) = pack2(h0, h1);
-                *(uint32_t *)(B_lo + off) = pack2(l0, l1);
+                *(uint32_t *)(B_hi + off) = h0 | (h1 << 16);
+                *(uint32_t *)(B_lo + off) = (uint32_t)l0 | ((uint32_t)l1 << 16);
             }
         }
     }
+}
+
+// Largest |value| (as its non-negative float bits) of the cone's values, over the block.
+__device__ __forceinline__ void cone_max_abs(const LevelDev &L, int slot, int nrhs, int t, int nt, unsigned *smax)
+{
+    const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
+    float m = 0.f;
+    for (int q = t; q < kP * nrhs; q += nt) {
+        const float2 v = __ldg(F + q);
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0 && m > 0.f) atomicMax(smax, __float_as_uint(m));
 }
 
 // 15 MMAs (5 K blocks x {hi.hi, hi.lo, lo.hi}) into the accumulator, then a commit
@@ -360,12 +385,14 @@ __device__ __forceinline__ void cone_epilogue(uint32_t tmem, int tid, int nrhs, 
 // one thread issues the MMAs, and while the tensor cores run, every thread computes
 // its row of the next job (weights, factor, destination: the global loads of the
 // row), then drains this job's accumulator.
+template <bool F16>
 __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernelArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tbase;
     __shared__ int sq[2];  // slots of the CTA's cones q and q + 1 (entry q % 2)
+    __shared__ unsigned smax;  // FP16 operands: the cone's largest |value| (float bits)
     const int tid = threadIdx.x, warp = tid >> 5;
     const LevelDev &L = pd.lev[a.d];
     const int npad = a.npad, nrhs = a.nrhs;
@@ -399,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tbase;
-    const uint32_t idesc = umma_idesc(kM, npad);
+    const uint32_t idesc = umma_idesc(kM, npad, F16);
     const LevelDev *Lp = a.d > 3 ? &pd.lev[a.d - 1] : nullptr;
     const bool tab = a.do_upward && a.d > 3 && L.utab != nullptr;
     uint32_t phase = 0;
@@ -412,10 +439,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     float w[13];
     RowData rd = {nullptr, 0.f, 0.f};
     if (have) rd = row_geometry(pd, L, Lp, a, cur, tab, tid, w);
+    float unscale = 1.f;  // FP16 operands: the cone's values are scaled by 1 / unscale (a power of two)
     while (have) {
         // the previous job's MMAs have completed: B and A may be rewritten
-        if (cur.c0 == 0) load_cone_B(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid, kThreads);
-        write_A_row(w, rd.dest != nullptr, tid, A_hi, A_lo);
+        if (cur.c0 == 0) {
+            float scale = 1.f;
+            if constexpr (F16) {
+                if (tid == 0) smax = 0u;
+                __syncthreads();
+                cone_max_abs(L, cur.slot, nrhs, tid, kThreads, &smax);
+                __syncthreads();
+                const float mx = __uint_as_float(smax);
+                int e = 0;
+                if (mx > 0.f) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+                scale = ldexpf(1.f, -e);
+                unscale = ldexpf(1.f, e);
+            }
+            load_cone_B<F16>(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid, kThreads, scale);
+        }
+        if constexpr (F16) {
+            rd.fr *= unscale;
+            rd.fi *= unscale;
+        }
+        write_A_row<F16>(w, rd.dest != nullptr, tid, A_hi, A_lo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0 && !a.skip_mma) {
@@ -754,7 +800,10 @@ static size_t cone_mma_smem(int npad)
 cudaError_t ifgf_batched_prepare()
 {
     using namespace ifgf::batched;
-    return cudaFuncSetAttribute(k_cone_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cone_mma_smem(128));
+    cudaError_t e = cudaFuncSetAttribute(k_cone_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cone_mma_smem(128));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_cone_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cone_mma_smem(128));
 }
 
 // The tensor-core cone kernels of levels D..3 (targets of every level, parent
@@ -790,7 +839,8 @@ static cudaError_t launch_cones(const PlanDev &pd, int nrhs, float2 *us, int cta
         const cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
         const int grid = std::min(L.nact, (ctas == 1 ? 1 : 2) * 152);
-        k_cone_mma<<<grid, kThreads, smem, st>>>(pd, a);
+        if (pd.batched_f16) k_cone_mma<true><<<grid, kThreads, smem, st>>>(pd, a);
+        else k_cone_mma<false><<<grid, kThreads, smem, st>>>(pd, a);
         ++*launches;
     }
     return cudaGetLastError();

@@ -140,6 +140,7 @@ struct PlanDev {
     // and the tensor-core cone kernel's persistent CTAs per SM (1 or 2)
     int tune_leaf = 0;
     int tune_cone_ctas = 2;
+    int batched_f16 = 0;   // IFGF_BATCHED_FP16: the tensor-core contraction takes FP16 operands
     LevelDev lev[IFGF_MAX_LEVELS + 1];
 };
 
@@ -253,6 +254,9 @@ struct ifgf_plan {
 
 // complex element size of the plan's data type
 inline size_t ifgf_elem_bytes(int precision) { return precision == IFGF_FP64 ? 16 : 8; }
+
+// plans whose interpolation contractions run on the tensor cores
+inline bool ifgf_is_batched(int precision) { return precision == IFGF_BATCHED_BF16 || precision == IFGF_BATCHED_FP16; }
 
 // Upward-table entry for value type T and NW = P_s + 2 P_ang weights.
 template <typename T, int NW> struct UpEntry {

@@ -1284,7 +1284,7 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
     // the geometry of untabled upward levels, computed once here instead of at every
     // apply.  Built when they take at most a quarter of the free memory (flags bit 5
     // turns them off; batched plans have their own target cache).
-    if (!(p->flags & 32) && p->precision != IFGF_BATCHED_BF16) {
+    if (!(p->flags & 32) && !ifgf_is_batched(p->precision)) {
         const bool f64 = p->precision == IFGF_FP64;
         const size_t te = Ps == 3 && Pang == 5 ? (f64 ? sizeof(TEntry64) : sizeof(TEntry32)) : 0;
         const size_t ue = ifgf_uptable_entry_bytes(p->precision, Ps, Pang);
@@ -1443,7 +1443,7 @@ ifgf_status ifgf_build_adjoint_lists(ifgf_plan *p, cudaStream_t st)
                 L.tl_start = start;
                 L.tl = list;
             }
-            if (p->precision == IFGF_BATCHED_BF16 && !(p->flags & 4) && m > 0) {
+            if (ifgf_is_batched(p->precision) && !(p->flags & 4) && m > 0) {
                 DALLOC(tloc, float4, m);
                 DALLOC(tfac, float2, m);
                 CK(ifgf_cache_target_geometry(pd, d, tloc, tfac, m, st));
