@@ -111,7 +111,10 @@ typedef struct {
                        in runs of nodes that share a child cone (testing: the two kernels
                        sum in the same order);
                        bit 10: the run kernel takes at most 8 runs per pass (testing:
-                       exercises its multi-pass path). */
+                       exercises its multi-pass path);
+                       bit 11: FP32 upward steps whose geometry is computed on the fly use
+                       the run kernel too (by default they use one node per lane, which
+                       keeps the FP64 geometry work dense; testing and measurement). */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
                        memory at plan time.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels

@@ -683,17 +683,21 @@ __global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int
 //   C. copies the values of the first kRunStage cones into the warp's shared-memory stage
 //      (coalesced 16-byte loads);
 //   D. gives each lane one run: it reads each value of its cone once and applies it to the
-//      run's kRunK evaluations (same FMAs as k_upward, in the same order, per evaluation),
-//      and adds factor times value to the node's accumulator in shared memory.
-// Every node sums its children in order with the same operations as k_upward, so the
-// results are equal.  Cones beyond the first kRunStage of a child step (rare) are read
-// from global memory; more than 32 runs (rare) take a second pass.
+//      run's kRunK evaluations (the weight products (ws wt) wp per node, so that only
+//      accumulators and weights stay live), and adds factor times value to the node's
+//      accumulator in shared memory.
+// Every node sums its children in the same order as k_upward; the contraction associates
+// its products differently (the same polynomial, equal to FP32 rounding).  Cones beyond
+// the first kRunStage of a child step (rare) are read from global memory; more than 32 runs
+// (rare) take a second pass.
 constexpr int kRunK = 3;
 constexpr int kRunStage = 4;
 constexpr int kRunWarps = 2;  // 2 x 14.3 KB of shared memory per CTA (4 right-hand sides), under the 48 KB default
 
 // the run's evaluations: values src[node][r] (r < nrhs) of one child cone, per evaluation e
-// the weights ws[e] (PS), wt[e] (PA), wp[e] (PA); out[e][r]
+// the weights w[e] = (ws (PS), wt (PA), wp (PA)); out[e][r] = sum over the nodes (a, b, c) of
+// (ws[a] wt[b]) wp[c] src[(a PA + b) PA + c][r].  Each value is read once and applied to the
+// run's kRunK evaluations; per evaluation only the accumulators and the weights are live.
 template <int R, int PS, int PA, typename Src>
 __device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)[PS + 2 * PA], cpx<float> (*out)[R])
 {
@@ -702,64 +706,47 @@ __device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)
 #pragma unroll
         for (int r = 0; r < R; ++r) out[e][r] = {0.f, 0.f};
 #pragma unroll 1
-    for (int a = 0; a < PS; ++a) {
-        cpx<float> mid[kRunK][R];
-#pragma unroll
-        for (int e = 0; e < kRunK; ++e)
-#pragma unroll
-            for (int r = 0; r < R; ++r) mid[e][r] = {0.f, 0.f};
-#pragma unroll
-        for (int b = 0; b < PA; ++b) {
-            cpx<float> in[kRunK][R];
-#pragma unroll
-            for (int e = 0; e < kRunK; ++e)
-#pragma unroll
-                for (int r = 0; r < R; ++r) in[e][r] = {0.f, 0.f};
-#pragma unroll
-            for (int c = 0; c < PA; ++c) {
-                const int idx = (a * PA + b) * PA + c;
-                float v[2 * R];
-                if (R == 4 && nrhs == 4) {
-                    const float4 v01 = reinterpret_cast<const float4 *>(src)[idx * 2];
-                    const float4 v23 = reinterpret_cast<const float4 *>(src)[idx * 2 + 1];
-                    v[0] = v01.x; v[1] = v01.y; v[2] = v01.z; v[3] = v01.w;
-                    v[4] = v23.x; v[5] = v23.y; v[6] = v23.z; v[7] = v23.w;
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        float2 x = make_float2(0.f, 0.f);
-                        if (R == 1 || r < nrhs) x = src[idx * nrhs + r];
-                        v[2 * r] = x.x;
-                        v[2 * r + 1] = x.y;
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < kRunK; ++e)
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        in[e][r].x += w[e][PS + PA + c] * v[2 * r];
-                        in[e][r].y += w[e][PS + PA + c] * v[2 * r + 1];
-                    }
-            }
-#pragma unroll
-            for (int e = 0; e < kRunK; ++e)
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    mid[e][r].x += w[e][PS + b] * in[e][r].x;
-                    mid[e][r].y += w[e][PS + b] * in[e][r].y;
-                }
-        }
+    for (int ab = 0; ab < PS * PA; ++ab) {
+        const int a = ab / PA, b = ab - a * PA;
+        float wab[kRunK];
 #pragma unroll
         for (int e = 0; e < kRunK; ++e) {
-            // w[e][a] with the rolled loop index a, by selects (keeps w in registers)
-            float wa = w[e][0];
+            // w[e][a] and w[e][PS + b] with the rolled index, by selects (w stays in registers)
+            float wa = w[e][0], wb = w[e][PS];
 #pragma unroll
             for (int m = 1; m < PS; ++m)
                 if (a == m) wa = w[e][m];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                out[e][r].x += wa * mid[e][r].x;
-                out[e][r].y += wa * mid[e][r].y;
+            for (int m = 1; m < PA; ++m)
+                if (b == m) wb = w[e][PS + m];
+            wab[e] = wa * wb;
+        }
+#pragma unroll
+        for (int c = 0; c < PA; ++c) {
+            const int idx = ab * PA + c;
+            float v[2 * R];
+            if (R == 4 && nrhs == 4) {
+                const float4 v01 = reinterpret_cast<const float4 *>(src)[idx * 2];
+                const float4 v23 = reinterpret_cast<const float4 *>(src)[idx * 2 + 1];
+                v[0] = v01.x; v[1] = v01.y; v[2] = v01.z; v[3] = v01.w;
+                v[4] = v23.x; v[5] = v23.y; v[6] = v23.z; v[7] = v23.w;
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float2 x = make_float2(0.f, 0.f);
+                    if (R == 1 || r < nrhs) x = src[idx * nrhs + r];
+                    v[2 * r] = x.x;
+                    v[2 * r + 1] = x.y;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < kRunK; ++e) {
+                const float wn = wab[e] * w[e][PS + PA + c];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    out[e][r].x += wn * v[2 * r];
+                    out[e][r].y += wn * v[2 * r + 1];
+                }
             }
         }
     }
@@ -774,9 +761,8 @@ __device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)
 __host__ __device__ constexpr size_t run_stage_floats(int P, int nrhs) { return (size_t)kRunStage * P * nrhs * 2; }
 __host__ __device__ constexpr size_t run_warp_bytes(int P, int R, int nrhs)
 {
-    // ... plus two buffers of the next child's P table entries (24 bytes each, prefetched)
     return ((run_stage_floats(P, nrhs) + (size_t)P * R * 2 + (size_t)P * 2 + (size_t)P * 3) * 4 + (size_t)P * 4 +
-            32 * kRunK * 4 + 32 * 4 + 2 * (size_t)P * sizeof(UpEntry32) + 15) / 16 * 16;
+            32 * kRunK * 4 + 32 * 4 + 15) / 16 * 16;
 }
 
 template <int R, int PS, int PA, bool TAB>
@@ -801,7 +787,6 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
     int *gsl = (int *)(gt + (size_t)P * 3);                     // [P]
     int *runs = gsl + P;                                        // [32][kRunK]
     int *rgrp = runs + 32 * kRunK;                              // [32] group of each run
-    UpEntry32 *graw = (UpEntry32 *)(rgrp + 32);                 // [2][P] table entries of a child
     const int j = Lp.act_box[slot];
     const int pcone = Lp.act_cone[slot];
     const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
@@ -816,26 +801,9 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
     }
     for (int q = lane; q < P * R; q += 32) acc[q] = make_float2(0.f, 0.f);
     const int rmax = (pd.flags & 1024) ? 8 : 32;  // runs per pass (flags bit 10: 8, testing)
-    // the table entries of child kk + 1 are copied (asynchronously, 8 bytes at a time: an
-    // entry block starts on an 8-byte boundary) while child kk is contracted
-    auto prefetch_entries = [&](int kk2) {
-        if constexpr (TAB) {
-            if (kk2 < nch) {
-                const int oct2 = (int)(L.key[k0 + kk2] & 7u);
-                const uint2 *from = (const uint2 *)(tab + (size_t)oct2 * P);
-                uint2 *to = (uint2 *)(graw + (size_t)(kk2 & 1) * P);
-                for (int q = lane; q < P * 3; q += 32) cp_async8(to + q, from + q);
-            }
-        }
-    };
-    prefetch_entries(0);
     for (int kk = 0; kk < nch; ++kk) {
         const int k = k0 + kk;
         const int oct = (int)(L.key[k] & 7u);
-        if constexpr (TAB) {
-            cp_async_wait_all();
-            __syncwarp();
-        }
         // A. geometry of the P nodes
         int sl_c[NCH];
 #pragma unroll
@@ -847,7 +815,7 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
                 cpx<float> f;
                 int cone;
                 if constexpr (TAB) {
-                    const UpEntry32 en = graw[(size_t)(kk & 1) * P + node];
+                    const UpEntry32 en = tab[(size_t)oct * P + node];
                     tl[0] = en.t[0]; tl[1] = en.t[1]; tl[2] = en.t[2];
                     f = {en.fr, en.fi};
                     cone = en.cone;
@@ -920,7 +888,6 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
         }
         cp_async_wait_all();
         __syncwarp();
-        prefetch_entries(kk + 1);
         // D. the runs (more passes when a child step has more than rmax)
         for (int pass = 0; pass * rmax < nruns; ++pass) {
             if (pass > 0) {  // rebuild the runs beyond the first 32 from the groups
@@ -1021,7 +988,7 @@ inline void launch_upward(const PlanDev &pd, int d, int nrhs, int64_t np, cudaSt
             const int grid = (nslot + kRunWarps - 1) / kRunWarps;
             if (pd.lev[d].utab) {
                 k_upward_runs<R, PS, PA, true><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
-            } else if (pd.lev[d].ucache) {
+            } else if (pd.lev[d].ucache || (pd.flags & 2048)) {
                 k_upward_runs<R, PS, PA, false><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
             } else {
                 // geometry on the fly: the staged kernel (one node per lane)

@@ -423,7 +423,11 @@ __global__ void k_activate_cousins(PlanDev pd, int d, uint64_t *bits)
         int k = L.cous[e];
         const double *c = L.center + 3 * (size_t)k;
         ConeGeom g = cone_of_mixed(L, __dsub_rn(x, c[0]), __dsub_rn(y, c[1]), __dsub_rn(z, c[2]));
-        set_bit(bits, L.words, k, g.cone);
+        // neighbouring points of a leaf mostly mark the same cone of the same cousin
+        const unsigned grp = __activemask();
+        const unsigned long long key = ((unsigned long long)(unsigned)k << 32) | (unsigned)g.cone;
+        const unsigned same = __match_any_sync(grp, key);
+        if ((threadIdx.x & 31) == __ffs(same) - 1) set_bit(bits, L.words, k, g.cone);
     }
 }
 
@@ -431,20 +435,32 @@ __global__ void k_activate_cousins(PlanDev pd, int d, uint64_t *bits)
 // around each child centre.  Both activation kernels take cells from cone_of_mixed,
 // which equals the correctly rounded cone_of bit for bit (FP32 decisions only outside a
 // margin around the cell boundaries, cone_of inside it) at a fraction of its FP64 cost.
+// The lanes of a warp hold consecutive nodes of one or two parent cones and mostly mark the
+// same few child cones: only one lane per distinct (child, cone) pair issues the atomic OR.
 __global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
 {
     const LevelDev &L = pd.lev[d];
     const LevelDev &Lp = pd.lev[d - 1];
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)Lp.nact * pd.P) return;
-    int slot = (int)(t / pd.P), node = (int)(t % pd.P);
-    int j = Lp.act_box[slot];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < (int64_t)Lp.nact * pd.P;
+    if (__all_sync(0xffffffffu, !valid)) return;  // whole warps past the end
+    const int slot = valid ? (int)(t / pd.P) : 0, node = valid ? (int)(t % pd.P) : 0;
+    const int j = valid ? Lp.act_box[slot] : 0;
+    const int k0 = valid ? Lp.child_start[j] : 0, nch = valid ? Lp.child_start[j + 1] - k0 : 0;
+    const int maxch = __reduce_max_sync(0xffffffffu, nch);
     const double hh = L.H * 0.5;
-    for (int k = Lp.child_start[j]; k < Lp.child_start[j + 1]; ++k) {
-        double v[3];
-        node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
-        ConeGeom g = cone_of_mixed(L, v[0], v[1], v[2]);
-        set_bit(bits, L.words, k, g.cone);
+    for (int kk = 0; kk < maxch; ++kk) {
+        unsigned long long key = ~0ull;  // (child box, cone) of this lane, or none
+        if (kk < nch) {
+            const int k = k0 + kk;
+            double v[3];
+            node_rel(Lp, pd.Ps, pd.Pang, Lp.act_cone[slot], node, hh, (int)(L.key[k] & 7u), v, nullptr);
+            ConeGeom g = cone_of_mixed(L, v[0], v[1], v[2]);
+            key = ((unsigned long long)(unsigned)k << 32) | (unsigned)g.cone;
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        if (key != ~0ull && (threadIdx.x & 31) == __ffs(same) - 1)
+            set_bit(bits, L.words, (int)(key >> 32), (int)(key & 0xffffffffu));
     }
 }
 

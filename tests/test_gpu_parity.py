@@ -669,14 +669,15 @@ def test_batched_every_rhs_elementwise_vs_oracle(pkg, torch_cuda, nrhs, precisio
 
 
 @pytest.mark.parametrize("nrhs,flags", [(1, 0), (2, 0), (3, 0), (4, 0), (4, 2), (4, 8 | 32), (4, 1024),
-                                        (1, 2 | 1024)])
+                                        (1, 2 | 1024), (4, 2 | 2048), (3, 8 | 32 | 2048)])
 def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
     # the FP32 upward step in runs of nodes that share a child cone (default) and the
     # kernel with one thread per parent node reading the values from L1 (flags bit 9) sum
-    # every parent node over the same children in the same order with the same
-    # operations: equal cone values at every level; tabled (default) and on-the-fly
-    # geometry (bit 1); two-level buffers without caches (bits 3 and 5); at most 8 runs
-    # per pass (bit 10, the multi-pass path)
+    # every parent node over the same children in the same order; the run kernel
+    # associates each 75-term contraction differently (weight products), so the cone
+    # values agree to FP32 rounding carried over the levels (1e-5, a tenth of the mixed
+    # path's element-wise bound); tabled (default) and on-the-fly geometry (bit 1);
+    # two-level buffers without caches (bits 3 and 5); at most 8 runs per pass (bit 10)
     torch = torch_cuda
     wl, pts, _ = _make((6000, 6, 6, 1, 2))
     sig = wi.complex_normal(200 + nrhs, (nrhs, wl.n))
@@ -685,11 +686,11 @@ def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
     b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 6, 3, 5, 1, 2, flags=flags | 512, **kw)
     s = torch.from_numpy(sig).cuda().to(torch.complex64)
     ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
-    assert maxrel(ua, ub) < 1e-6, maxrel(ua, ub)
+    assert maxrel(ua, ub) < 1e-5, maxrel(ua, ub)
     if not flags & 8:
         for d in range(3, 7):
             va, vb = a.values(d, nrhs), b.values(d, nrhs)
-            assert maxrel(va, vb) < 1e-6, (d, maxrel(va, vb))
+            assert maxrel(va, vb) < 1e-5, (d, maxrel(va, vb))
     o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
     uo = o.apply(sig)
     for r in range(nrhs):
