@@ -59,10 +59,11 @@ typedef enum {
     IFGF_MIXED = 1,
     /* IFGF_MIXED with the per-cone interpolation contraction on tensor cores
      * (tcgen05, BF16 hi+lo operand split, FP32 accumulate), grouped by source cone;
-     * for many right-hand sides.  Used by ifgf_apply for even nrhs <= 64 (other
-     * nrhs and the adjoint run the IFGF_MIXED kernels); requires (P_s, P_ang) =
-     * (3, 5).  Contributions are added to their destinations with FP32 atomic
-     * reductions, so the last bits of the result vary from run to run. */
+     * for many right-hand sides.  Used by ifgf_apply for even nrhs up to 64 at
+     * (P_s, P_ang) = (3, 5) (contraction length 80) and up to 48 at (4, 7) (length 208,
+     * one CTA per SM); other nrhs and the adjoint run the IFGF_MIXED kernels.
+     * Contributions are added to their destinations with FP32 atomic reductions, so the
+     * last bits of the result vary from run to run. */
     IFGF_BATCHED_BF16 = 2,
     /* IFGF_BATCHED_BF16 with FP16 operands: the hi + lo split keeps ~22 significant bits
      * (~16 for BF16); each cone's values are scaled by a power of two into [-1, 1] before
@@ -297,13 +298,15 @@ ifgf_status ifgf_plan_check(ifgf_plan *plan, int *device_errors);
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int on);
 
 /*
- * Autotuner of the batched tensor-core path (IFGF_BATCHED_BF16 plans).  On this plan's
- * relevant cones with nrhs right-hand sides (even, 2..min(64, max_nrhs)) it times:
+ * Autotuner of the batched tensor-core path (IFGF_BATCHED_BF16 and IFGF_BATCHED_FP16
+ * plans).  On this plan's relevant cones with nrhs right-hand sides (even, 2..the order's
+ * maximum (64 at (3, 5), 48 at (4, 7)) and max_nrhs) it times:
  *   - each register-tile shape of the leaf analytic-factor kernel, written as threads
  *     along the right-hand sides x thread groups along the 75 nodes of a cone:
- *     0 = 16 x 8 (the default), 1 = 32 x 4, 2 = 8 x 16;
+ *     0 = 16 x 8 (the default), 1 = 32 x 4, 2 = 8 x 16 (order (4, 7) plans run one leaf
+ *     kernel, so the three times are of the same kernel);
  *   - each grid of the persistent tensor-core cone kernel: 1 or 2 CTAs per SM (2 is
- *     the default);
+ *     the default; order (4, 7) fits one);
  * reps runs of each after one warm-up run, and keeps the fastest of each for the
  * plan's later evaluations.  ms (NULL or [5]) receives the candidates' mean times in
  * milliseconds in the order above (the 3 leaf shapes, then 1 and 2 CTAs per SM);

@@ -21,6 +21,7 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
 cudaError_t ifgf_batched_prepare();
+int ifgf_batched_max_nrhs(int Ps);
 cudaError_t ifgf_batched_autotune(PlanDev &pd, int nrhs, const void *sig, void *us, cudaStream_t st, int reps,
                                   float *ms);
 
@@ -85,10 +86,7 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
         g_create_error = "supported (P_s, P_ang): (3, 5) and (4, 7)";
         return IFGF_EINVAL;
     }
-    if (opt && ifgf_is_batched(opt->precision) && !(p_radial == 3 && p_angular == 5)) {
-        g_create_error = "batched (tensor-core) plans support (P_s, P_ang) = (3, 5)";
-        return IFGF_EINVAL;
-    }
+
     ifgf_options o = {0, 0, 1, IFGF_FP64, 0, 0, 0.0, 0};
     if (opt) o = *opt;
     if (o.value_budget_bytes < 0) { g_create_error = "value_budget_bytes must be >= 0"; return IFGF_EINVAL; }
@@ -237,7 +235,7 @@ static cudaError_t launch_evaluation(ifgf_plan *p, const void *din, void *dout, 
         void *cout = (char *)dout + (size_t)c0 * p->n * eb;
         if (p->precision == IFGF_FP64)
             e = ifgf_run_typed_f64(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
-        else if (ifgf_is_batched(p->precision) && !adjoint && nc % 2 == 0 && nc <= 64)
+        else if (ifgf_is_batched(p->precision) && !adjoint && nc % 2 == 0 && nc <= ifgf_batched_max_nrhs(p->Ps))
             e = ifgf_run_batched(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, st, p->timer);
         else
             e = ifgf_run_typed_f32(p->dev, nc, cin, cout, p->sig_sorted, p->u_sorted, mode, adjoint, st, p->timer);
@@ -677,7 +675,8 @@ extern "C" ifgf_status ifgf_plan_autotune(ifgf_plan *plan, int nrhs, int reps, d
                                           void *stream)
 {
     if (!plan) return IFGF_EINVAL;
-    if (!ifgf_is_batched(plan->precision) || nrhs < 2 || nrhs > 64 || nrhs % 2 || nrhs > plan->max_nrhs ||
+    if (!ifgf_is_batched(plan->precision) || nrhs < 2 || nrhs > ifgf_batched_max_nrhs(plan->Ps) || nrhs % 2 ||
+        nrhs > plan->max_nrhs ||
         reps < 1) {
         plan->last_error = "autotune: batched plan, even nrhs in [2, min(64, max_nrhs)] and reps >= 1";
         return IFGF_EINVAL;

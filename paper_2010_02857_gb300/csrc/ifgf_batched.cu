@@ -40,8 +40,19 @@
 namespace ifgf {
 namespace batched {
 
-constexpr int kP = 75;        // nodes per cone (P_s = 3, P_ang = 5)
-constexpr int kK = 80;        // K padded to 5 blocks of 16
+// Interpolation order of a batched plan: P = P_s P_ang^2 nodes per cone, the contraction
+// length K (P padded to a multiple of 16, the K of one kind::f16 MMA), NW Lagrange weights.
+template <int PS_, int PA_> struct Ord {
+    static constexpr int PS = PS_, PA = PA_;
+    static constexpr int P = PS * PA * PA;
+    static constexpr int K = (P + 15) / 16 * 16;
+    static constexpr int NW = PS + 2 * PA;
+    static constexpr uint32_t SBO_A = (K / 8) * 128;  // byte stride of 8-row groups of A
+};
+using Ord35 = Ord<3, 5>;  // 75 nodes, K = 80
+using Ord47 = Ord<4, 7>;  // 196 nodes, K = 208
+// largest even nrhs of the tensor-core path per order (shared memory: A and B hi + lo)
+constexpr int kMaxBatched35 = 64, kMaxBatched47 = 48;
 constexpr int kM = 128;       // rows per MMA
 constexpr int kThreads = 128;
 constexpr int kWaitLimit = 1 << 22;
@@ -85,10 +96,12 @@ template <bool F16> __device__ __forceinline__ uint32_t split_hi_lo(float x, uin
     }
 }
 
-// A (kM x kK, K-major): element (m, k) at (m/8)*SBO_A + (k/8)*128 + (m%8)*16 + (k%8)*2
-constexpr uint32_t SBO_A = (kK / 8) * 128;
-__device__ __forceinline__ uint32_t a_off(int m, int k) { return (m >> 3) * SBO_A + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2; }
-// B (kK x Npad, MN-major): element (k, n) at (k/8)*LBO_B + (n/8)*128 + (k%8)*16 + (n%8)*2, LBO_B = Npad/8*128
+// A (kM x K, K-major): element (m, k) at (m/8)*SBO_A + (k/8)*128 + (m%8)*16 + (k%8)*2
+template <class O> __device__ __forceinline__ uint32_t a_off(int m, int k)
+{
+    return (m >> 3) * O::SBO_A + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2;
+}
+// B (K x Npad, MN-major): element (k, n) at (k/8)*LBO_B + (n/8)*128 + (k%8)*16 + (n%8)*2, LBO_B = Npad/8*128
 __device__ __forceinline__ uint32_t b_off(int k, int n, uint32_t lbo_b)
 {
     return (k >> 3) * lbo_b + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;
@@ -147,8 +160,9 @@ struct RowData {
     float fr, fi;   // complex factor of the row
 };
 
-// Lagrange weights w[13] and factor of row `row` of job j: a cousin target (centred
+// Lagrange weights w[NW] and factor of row `row` of job j: a cousin target (centred
 // factor G(x, x_k^d)) or a parent interpolation point (re-centring factor)
+template <class O>
 __device__ __forceinline__ RowData row_geometry(const PlanDev &pd, const LevelDev &L, const LevelDev *Lp,
                                                 const ConeKernelArgs &a, const ConeJob &j, bool tab, int row,
                                                 float *w)
@@ -163,43 +177,43 @@ __device__ __forceinline__ RowData row_geometry(const PlanDev &pd, const LevelDe
         if (L.tl_loc) {
             float4 t = L.tl_loc[e];
             float2 G = L.tl_fac[e];
-            lagrange(3, pd.tsf, pd.itsf, t.x, w);
-            lagrange(5, pd.taf, pd.itaf, t.y, w + 3);
-            lagrange(5, pd.taf, pd.itaf, t.z, w + 8);
+            lagrange(O::PS, pd.tsf, pd.itsf, t.x, w);
+            lagrange(O::PA, pd.taf, pd.itaf, t.y, w + O::PS);
+            lagrange(O::PA, pd.taf, pd.itaf, t.z, w + O::PS + O::PA);
             f = {G.x, G.y};
         } else {
             const double *ck = L.center + 3 * (size_t)L.act_box[j.slot];
             double vx = __dsub_rn(pd.xs[i], ck[0]), vy = __dsub_rn(pd.ys[i], ck[1]), vz = __dsub_rn(pd.zs[i], ck[2]);
-            ConeGeom g = geom_weights<float, 3, 5>(pd, L, vx, vy, vz, w);
+            ConeGeom g = geom_weights<float, O::PS, O::PA>(pd, L, vx, vy, vz, w);
             f = green_r<float>(pd.kappa, g.r);
         }
         rd.dest = a.u + (size_t)i * a.nrhs;
     } else {
         const int e = L.ul[j.u0 + r - j.rows_t];
-        const int psl = e / kP, node = e % kP;
+        const int psl = e / O::P, node = e % O::P;
         const int pcone = Lp->act_cone[psl];
         const int oct = (int)(L.key[L.act_box[j.slot]] & 7u);
         const int trow = tab ? table_row(L.ubits, L.urank, pcone) : -1;
         if (trow >= 0) {
-            up_entry<float, 3, 5>(pd, ((const UpEntry32 *)L.utab)[((size_t)trow * 8 + oct) * kP + node], w, f);
+            up_entry<float, O::PS, O::PA>(pd, ((const UpEntry32 *)L.utab)[((size_t)trow * 8 + oct) * O::P + node], w, f);
         } else {
-            up_geometry<float, 3, 5>(pd, L, *Lp, pcone, node, oct, w, f);
+            up_geometry<float, O::PS, O::PA>(pd, L, *Lp, pcone, node, oct, w, f);
         }
-        rd.dest = (float2 *)Lp->F + ((size_t)psl * kP + node) * a.nrhs;
+        rd.dest = (float2 *)Lp->F + ((size_t)psl * O::P + node) * a.nrhs;
     }
     rd.fr = f.x;
     rd.fi = f.y;
     return rd;
 }
 
-// A row `row` from its weights: W[p] = ws[a] wt[b] wp[c], p = (a*5 + b)*5 + c, as hi and
-// lo parts (BF16 or FP16); zero for an empty row and for the padding columns p >= 75
-template <bool F16>
+// A row `row` from its weights: W[p] = ws[a] wt[b] wp[c], p = (a P_ang + b) P_ang + c, as
+// hi and lo parts (BF16 or FP16); zero for an empty row and for the padding columns p >= P
+template <bool F16, class O>
 __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row, unsigned char *A_hi,
                                             unsigned char *A_lo)
 {
 #pragma unroll
-    for (int kc = 0; kc < kK / 8; ++kc) {
+    for (int kc = 0; kc < O::K / 8; ++kc) {
         uint32_t hv[4], lv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -208,9 +222,9 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
             for (int h = 0; h < 2; ++h) {
                 const int p = kc * 8 + q * 2 + h;
                 float x = 0.f;
-                if (valid && p < kP) {
-                    const int ia = p / 25, ib = (p / 5) % 5, ic = p % 5;
-                    x = w[ia] * w[3 + ib] * w[8 + ic];
+                if (valid && p < O::P) {
+                    const int ia = p / (O::PA * O::PA), ib = (p / O::PA) % O::PA, ic = p % O::PA;
+                    x = w[ia] * w[O::PS + ib] * w[O::PS + O::PA + ic];
                 }
                 uint16_t lo;
                 h2[h] = split_hi_lo<F16>(x, lo);
@@ -219,7 +233,7 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
             hv[q] = h2[0] | (h2[1] << 16);
             lv[q] = l2[0] | (l2[1] << 16);
         }
-        const uint32_t off = a_off(row, kc * 8);
+        const uint32_t off = a_off<O>(row, kc * 8);
         *(uint4 *)(A_hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
         *(uint4 *)(A_lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
     }
@@ -230,26 +244,26 @@ __device__ __forceinline__ void write_A_row(const float *w, bool valid, int row,
 // that its 32 four-byte stores fill one core matrix (no bank conflicts) and its loads read
 // eight 32-byte runs.  Batches of kBatch independent loads per thread before any
 // conversion; nt threads (a multiple of 32) take part, t is this thread's index.
-template <bool F16>
+template <bool F16, class O>
 __device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrhs, int npad, uint32_t lbo_b,
                                             unsigned char *B_hi, unsigned char *B_lo, int t, int nt, float scale)
 {
-    const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
+    const float2 *F = (const float2 *)L.F + (size_t)slot * O::P * nrhs;
     const int ntr = npad / 8;               // r tiles of 4: npad / 2 columns pairs
-    const int tot = (kK / 8) * ntr * 32;    // (p tiles) x (r tiles) x 32 lanes
+    const int tot = (O::K / 8) * ntr * 32;  // (p tiles) x (r tiles) x 32 lanes
     for (int base = t; base < tot; base += kBatch * nt) {
         float2 v[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int idx = base + u * nt, tile = idx >> 5, l = idx & 31;
             const int p = (tile / ntr) * 8 + (l >> 2), r = (tile % ntr) * 4 + (l & 3);
-            v[u] = (idx < tot && p < kP && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
+            v[u] = (idx < tot && p < O::P && r < nrhs) ? __ldg(F + (size_t)p * nrhs + r) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int idx = base + u * nt, tile = idx >> 5, l = idx & 31;
             const int p = (tile / ntr) * 8 + (l >> 2), r = (tile % ntr) * 4 + (l & 3);
-            if (idx < tot && p < kP) {
+            if (idx < tot && p < O::P) {
                 uint16_t l0, l1;
                 const uint32_t h0 = split_hi_lo<F16>(v[u].x * scale, l0);
                 const uint32_t h1 = split_hi_lo<F16>(v[u].y * scale, l1);
@@ -262,11 +276,12 @@ __device__ __forceinline__ void load_cone_B(const LevelDev &L, int slot, int nrh
 }
 
 // Largest |value| (as its non-negative float bits) of the cone's values, over the block.
+template <class O>
 __device__ __forceinline__ void cone_max_abs(const LevelDev &L, int slot, int nrhs, int t, int nt, unsigned *smax)
 {
-    const float2 *F = (const float2 *)L.F + (size_t)slot * kP * nrhs;
+    const float2 *F = (const float2 *)L.F + (size_t)slot * O::P * nrhs;
     float m = 0.f;
-    for (int q = t; q < kP * nrhs; q += nt) {
+    for (int q = t; q < O::P * nrhs; q += nt) {
         const float2 v = __ldg(F + q);
         m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
@@ -275,15 +290,16 @@ __device__ __forceinline__ void cone_max_abs(const LevelDev &L, int slot, int nr
     if ((t & 31) == 0 && m > 0.f) atomicMax(smax, __float_as_uint(m));
 }
 
-// 15 MMAs (5 K blocks x {hi.hi, hi.lo, lo.hi}) into the accumulator, then a commit
+// 3 K / 16 MMAs (the K blocks x {hi.hi, hi.lo, lo.hi}) into the accumulator, then a commit
 // that arrives on mbar when they have completed
+template <class O>
 __device__ __forceinline__ void issue_cone_mma(uint32_t tmem, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
                                                uint32_t lbo_b, uint32_t idesc, uint32_t mbar)
 {
 #pragma unroll
-    for (int kb = 0; kb < kK / 16; ++kb) {
-        const uint64_t dah = umma_desc(ah + kb * 256, 128, SBO_A);
-        const uint64_t dal = umma_desc(al + kb * 256, 128, SBO_A);
+    for (int kb = 0; kb < O::K / 16; ++kb) {
+        const uint64_t dah = umma_desc(ah + kb * 256, 128, O::SBO_A);
+        const uint64_t dal = umma_desc(al + kb * 256, 128, O::SBO_A);
         const uint64_t dbh = umma_desc(bh + kb * 2 * lbo_b, lbo_b, 128);
         const uint64_t dbl = umma_desc(bl + kb * 2 * lbo_b, lbo_b, 128);
         const uint32_t acc0 = kb > 0 ? 1u : 0u;
@@ -385,7 +401,7 @@ __device__ __forceinline__ void cone_epilogue(uint32_t tmem, int tid, int nrhs, 
 // one thread issues the MMAs, and while the tensor cores run, every thread computes
 // its row of the next job (weights, factor, destination: the global loads of the
 // row), then drains this job's accumulator.
-template <bool F16>
+template <bool F16, class O>
 __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernelArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -398,10 +414,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     const int npad = a.npad, nrhs = a.nrhs;
     const uint32_t lbo_b = (uint32_t)(npad / 8) * 128;
     unsigned char *A_hi = sm;
-    unsigned char *A_lo = A_hi + kM * kK * 2;
-    unsigned char *B_hi = A_lo + kM * kK * 2;
-    unsigned char *B_lo = B_hi + kK * npad * 2;
-    unsigned char *stage = B_lo + kK * npad * 2;
+    unsigned char *A_lo = A_hi + kM * O::K * 2;
+    unsigned char *B_hi = A_lo + kM * O::K * 2;
+    unsigned char *B_lo = B_hi + O::K * npad * 2;
+    unsigned char *stage = B_lo + O::K * npad * 2;
 
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
@@ -416,9 +432,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // padding rows p = 75..79 of B stay zero for the whole kernel
-    for (int idx = tid; idx < (kK - kP) * npad; idx += kThreads) {
-        const int p = kP + idx / npad, n = idx % npad;
+    // padding rows p = P..K-1 of B stay zero for the whole kernel
+    for (int idx = tid; idx < (O::K - O::P) * npad; idx += kThreads) {
+        const int p = O::P + idx / npad, n = idx % npad;
         *(__nv_bfloat16 *)(B_hi + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
         *(__nv_bfloat16 *)(B_lo + b_off(p, n, lbo_b)) = __float2bfloat16_rn(0.f);
     }
@@ -436,9 +452,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
     cur.c0 = 0;
     cur.rows = 0;
     bool have = next_job(L, a, sq, cur);
-    float w[13];
+    float w[O::NW];
     RowData rd = {nullptr, 0.f, 0.f};
-    if (have) rd = row_geometry(pd, L, Lp, a, cur, tab, tid, w);
+    if (have) rd = row_geometry<O>(pd, L, Lp, a, cur, tab, tid, w);
     float unscale = 1.f;  // FP16 operands: the cone's values are scaled by 1 / unscale (a power of two)
     while (have) {
         // the previous job's MMAs have completed: B and A may be rewritten
@@ -447,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
             if constexpr (F16) {
                 if (tid == 0) smax = 0u;
                 __syncthreads();
-                cone_max_abs(L, cur.slot, nrhs, tid, kThreads, &smax);
+                cone_max_abs<O>(L, cur.slot, nrhs, tid, kThreads, &smax);
                 __syncthreads();
                 const float mx = __uint_as_float(smax);
                 int e = 0;
@@ -455,19 +471,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
                 scale = ldexpf(1.f, -e);
                 unscale = ldexpf(1.f, e);
             }
-            load_cone_B<F16>(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid, kThreads, scale);
+            load_cone_B<F16, O>(L, cur.slot, nrhs, npad, lbo_b, B_hi, B_lo, tid, kThreads, scale);
         }
         if constexpr (F16) {
             rd.fr *= unscale;
             rd.fi *= unscale;
         }
-        write_A_row<F16>(w, rd.dest != nullptr, tid, A_hi, A_lo);
+        write_A_row<F16, O>(w, rd.dest != nullptr, tid, A_hi, A_lo);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0 && !a.skip_mma) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            issue_cone_mma(tmem, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), lbo_b, idesc,
-                           smem_u32(&mbar));
+            issue_cone_mma<O>(tmem, smem_u32(A_hi), smem_u32(A_lo), smem_u32(B_hi), smem_u32(B_lo), lbo_b, idesc,
+                              smem_u32(&mbar));
         }
         // the next job's row while the tensor cores run this one
         ConeJob nxt = cur;
@@ -475,9 +491,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
         // entering cone q: the entry of cone q - 1 takes cone q + 1 (read from the next
         // iteration on, after the barriers below)
         if (tid == 0 && have_n && nxt.c0 == 0) sq[(nxt.q + 1) & 1] = take_cone(a);
-        float wn[13];
+        float wn[O::NW];
         RowData rn = {nullptr, 0.f, 0.f};
-        if (have_n) rn = row_geometry(pd, L, Lp, a, nxt, tab, tid, wn);
+        if (have_n) rn = row_geometry<O>(pd, L, Lp, a, nxt, tab, tid, wn);
         uint32_t done = 0;
         for (int it = 0; it < a.wait_limit && !done; ++it) {
             asm volatile(
@@ -499,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_cone_mma(PlanDev pd, ConeKernel
         cur = nxt;
         rd = rn;
 #pragma unroll
-        for (int m = 0; m < 13; ++m) w[m] = wn[m];
+        for (int m = 0; m < O::NW; ++m) w[m] = wn[m];
         have = have_n;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -659,23 +675,23 @@ __global__ void __launch_bounds__(128) k_near_tiled(PlanDev pd, int nrhs, const 
 // autotuner chooses (8, 16 or 32).  Every output is one thread's sum over the sources
 // in order, so the result does not depend on the shape.
 constexpr int kLeafKT = 32;
-constexpr int kLeafShapes = 3;  // TX = 16, 32, 8 (launch_leaf)
+constexpr int kLeafShapes = 3;  // TX = 16, 32, 8 (launch_leaf); order (3, 5)
 
 template <int TX, int RPT>
 __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const float2 *sig)
 {
     constexpr int NG = 128 / TX;
-    constexpr int NPT = (kP + NG - 1) / NG;  // nodes per thread
-    __shared__ float4 snode[kP];              // R and dir of each node (FP32)
+    constexpr int NPT = (Ord35::P + NG - 1) / NG;  // nodes per thread
+    __shared__ float4 snode[Ord35::P];              // R and dir of each node (FP32)
     __shared__ float4 soff[kLeafKT];          // the chunk's source offsets (delta, |delta|^2)
-    __shared__ float2 sg[kP][kLeafKT + 1];    // g(q_n, x_j); padded against bank conflicts
+    __shared__ float2 sg[Ord35::P][kLeafKT + 1];    // g(q_n, x_j); padded against bank conflicts
     __shared__ __align__(16) float2 ssig[kLeafKT * TX * RPT];
     const LevelDev &L = pd.lev[pd.D];
     const int slot = blockIdx.x;
     const int b = L.act_box[slot];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const float kf = (float)pd.kappa;
-    if (tid < kP) {
+    if (tid < Ord35::P) {
         const double *c = L.center + 3 * (size_t)b;
         double q[3], dir[3];
         const double R0 = node_pos(L, 3, 5, L.act_cone[slot], tid, c[0], c[1], c[2], q, dir);
@@ -696,7 +712,7 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
         if (tid < cnt) soff[tid] = pd.leaf_off[jb + tid];
         cp_async_wait_all();
         __syncthreads();
-        for (int e = tid; e < kP * cnt; e += blockDim.x) {
+        for (int e = tid; e < Ord35::P * cnt; e += blockDim.x) {
             const int n = e / cnt, t = e - n * cnt;
             const float4 nd = snode[n];
             const cpx<float> g = leaf_factor32(nd.x, nd.y, nd.z, nd.w, kf, soff[t]);
@@ -713,7 +729,7 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
 #pragma unroll
             for (int i = 0; i < NPT; ++i) {
                 const int n = ty + NG * i;
-                if (n < kP) {
+                if (n < Ord35::P) {
                     const float2 g = sg[n][t];
 #pragma unroll
                     for (int k = 0; k < RPT; ++k) {
@@ -724,11 +740,11 @@ __global__ void __launch_bounds__(128) k_leaf_tiled(PlanDev pd, int nrhs, const 
             }
         }
     }
-    float2 *F = (float2 *)L.F + (size_t)slot * kP * nrhs;
+    float2 *F = (float2 *)L.F + (size_t)slot * Ord35::P * nrhs;
 #pragma unroll
     for (int i = 0; i < NPT; ++i) {
         const int n = ty + NG * i;
-        if (n >= kP) continue;
+        if (n >= Ord35::P) continue;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
             const int r = tx + TX * k;
@@ -754,11 +770,17 @@ void launch_leaf_shape(const PlanDev &pd, int nrhs, const float2 *sig, int nact,
     }
 }
 
-// leaf factors of all relevant leaf cones with tile shape `shape` (an index of kLeafTX)
+// leaf factors of all relevant leaf cones with tile shape `shape` (an index of kLeafTX);
+// order (4, 7) plans run the mixed path's leaf kernel (one thread per node, right-hand
+// sides in blocks of 8)
 inline void launch_leaf(const PlanDev &pd, int nrhs, const float2 *sig, int shape, cudaStream_t st)
 {
     const int nact = pd.lev[pd.D].nact;
     if (nact == 0) return;
+    if (pd.Ps == 4) {
+        ifgf::launch_leaf<float, 8, 4, 7>(pd, pd.D, nrhs, sig, st);
+        return;
+    }
     if (shape == 1) launch_leaf_shape<32>(pd, nrhs, sig, nact, st);
     else if (shape == 2) launch_leaf_shape<8>(pd, nrhs, sig, nact, st);
     else launch_leaf_shape<16>(pd, nrhs, sig, nact, st);
@@ -787,24 +809,34 @@ inline cudaError_t launch_cuda_core(const PlanDev &pd, int nrhs, const float2 *s
 }  // namespace batched
 }  // namespace ifgf
 
-// Shared memory of k_cone_mma for npad columns.
-static size_t cone_mma_smem(int npad)
+// Shared memory of k_cone_mma for npad columns and contraction length K.
+static size_t cone_mma_smem(int npad, int K)
 {
     using namespace ifgf::batched;
-    return (size_t)2 * kM * kK * 2 + (size_t)2 * kK * npad * 2 + (size_t)kM * kStageStride;
+    return (size_t)2 * kM * K * 2 + (size_t)2 * K * npad * 2 + (size_t)kM * kStageStride;
 }
 
-// Raises k_cone_mma's dynamic shared-memory limit to what 64 right-hand sides (128
-// columns) need.  Called once per batched plan, so that evaluations queue only
-// stream-ordered work (and can be captured into CUDA graphs).
+// Raises k_cone_mma's dynamic shared-memory limit to what the largest batch of each order
+// needs (64 right-hand sides, 128 columns, at order (3, 5): 98 KB, two CTAs per SM; 48, 96
+// columns, at order (4, 7): 205 KB, one CTA per SM).  Called once per batched plan, so
+// that evaluations queue only stream-ordered work (and can be captured into CUDA graphs).
 cudaError_t ifgf_batched_prepare()
 {
     using namespace ifgf::batched;
-    cudaError_t e = cudaFuncSetAttribute(k_cone_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)cone_mma_smem(128));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_cone_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cone_mma_smem(128));
+    const int s35 = (int)cone_mma_smem(2 * kMaxBatched35, Ord35::K);
+    const int s47 = (int)cone_mma_smem(2 * kMaxBatched47, Ord47::K);
+    cudaError_t e = cudaFuncSetAttribute(k_cone_mma<false, Ord35>, cudaFuncAttributeMaxDynamicSharedMemorySize, s35);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cone_mma<true, Ord35>, cudaFuncAttributeMaxDynamicSharedMemorySize, s35);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cone_mma<false, Ord47>, cudaFuncAttributeMaxDynamicSharedMemorySize, s47);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cone_mma<true, Ord47>, cudaFuncAttributeMaxDynamicSharedMemorySize, s47);
+    return e;
 }
+
+// the largest nrhs the tensor-core path takes for a plan's order
+int ifgf_batched_max_nrhs(int Ps) { return Ps == 4 ? ifgf::batched::kMaxBatched47 : ifgf::batched::kMaxBatched35; }
 
 // The tensor-core cone kernels of levels D..3 (targets of every level, parent
 // interpolation points above level 3), ctas persistent CTAs per SM.
@@ -815,12 +847,15 @@ static cudaError_t launch_cones(const PlanDev &pd, int nrhs, float2 *us, int cta
     const int npad = ((2 * nrhs + 15) / 16) * 16;
     int tcols = 32;
     while (tcols < npad) tcols *= 2;
-    const size_t smem = cone_mma_smem(npad);  // within the limit ifgf_batched_prepare set
+    const bool o47 = pd.Ps == 4;
+    // within the limit ifgf_batched_prepare set
+    const size_t smem = cone_mma_smem(npad, o47 ? Ord47::K : Ord35::K);
+    const int P = o47 ? Ord47::P : Ord35::P;
     for (int d = pd.D; d >= 3; --d) {
         const LevelDev &L = pd.lev[d];
         if (d > 3) {
             const LevelDev &Lp = pd.lev[d - 1];
-            const cudaError_t e = cudaMemsetAsync(Lp.F, 0, (size_t)Lp.nact * kP * nrhs * sizeof(float2), st);
+            const cudaError_t e = cudaMemsetAsync(Lp.F, 0, (size_t)Lp.nact * P * nrhs * sizeof(float2), st);
             if (e != cudaSuccess) return e;
         }
         if (L.nact == 0) continue;
@@ -838,9 +873,16 @@ static cudaError_t launch_cones(const PlanDev &pd, int nrhs, float2 *us, int cta
         a.wait_limit = a.skip_mma ? (1 << 10) : kWaitLimit;
         const cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
-        const int grid = std::min(L.nact, (ctas == 1 ? 1 : 2) * 152);
-        if (pd.batched_f16) k_cone_mma<true><<<grid, kThreads, smem, st>>>(pd, a);
-        else k_cone_mma<false><<<grid, kThreads, smem, st>>>(pd, a);
+        // one CTA per SM when two do not fit (order (4, 7))
+        const int per_sm = (ctas == 1 || 2 * smem > 227 * 1024) ? 1 : 2;
+        const int grid = std::min(L.nact, per_sm * 152);
+        if (o47) {
+            if (pd.batched_f16) k_cone_mma<true, Ord47><<<grid, kThreads, smem, st>>>(pd, a);
+            else k_cone_mma<false, Ord47><<<grid, kThreads, smem, st>>>(pd, a);
+        } else {
+            if (pd.batched_f16) k_cone_mma<true, Ord35><<<grid, kThreads, smem, st>>>(pd, a);
+            else k_cone_mma<false, Ord35><<<grid, kThreads, smem, st>>>(pd, a);
+        }
         ++*launches;
     }
     return cudaGetLastError();

@@ -696,3 +696,27 @@ def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
     for r in range(nrhs):
         assert maxrel(ua[r], uo[r]) < ELEM_MIXED, (r, maxrel(ua[r], uo[r]))
     assert a.check() == 0 and b.check() == 0
+
+
+@pytest.mark.parametrize("precision,elem,l2", [("batched", ELEM_BATCHED, 2e-4), ("batched_fp16", ELEM_MIXED, 2e-5)])
+@pytest.mark.parametrize("nrhs", [2, 16, 48])
+def test_batched_order_4_7_vs_oracle(pkg, torch_cuda, nrhs, precision, elem, l2):
+    # (P_s, P_ang) = (4, 7) on the tensor cores: 196 nodes per cone, contraction length 208
+    # (13 K blocks), one CTA per SM at 48 right-hand sides; every right-hand side against
+    # the oracle's order-(4, 7) IFGF element-wise, and the first against the direct sum
+    torch = torch_cuda
+    wl, pts, _ = _make((3000, 3, 4, 2, 4))
+    sig = wi.complex_normal(300 + nrhs, (nrhs, wl.n))
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 4, 4, 7, 2, 4, max_nrhs=nrhs, precision=precision)
+    o = oracle.Plan(pts, wl.kappa, 4, 4, 7, 2, 4)
+    s = torch.from_numpy(sig).cuda()
+    ub, uo = b.apply(s).cpu().numpy(), o.apply(sig)
+    for r in range(nrhs):
+        assert maxrel(ub[r], uo[r]) < elem, (r, maxrel(ub[r], uo[r]))
+        assert rel(ub[r], uo[r]) < l2, (r, rel(ub[r], uo[r]))
+    ex = oracle.direct(pts, wl.kappa, sig[:1])
+    assert rel(ub[:1], ex) < 1e-3
+    tune = b.autotune(nrhs, reps=1)
+    assert tune["cone_ctas_per_sm"] in (1, 2)
+    assert rel(b.apply(s).cpu().numpy(), ub) < 1e-5
+    assert b.check() == 0
