@@ -299,6 +299,8 @@ def main():
                     help="override the workload's number of right-hand sides (same generator)")
     ap.add_argument("--op", default="apply", choices=["apply", "adjoint"],
                     help="time ifgf_apply (default) or ifgf_apply_adjoint")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tune-cache file of batched plans: reuse a stored tile-shape choice, else time and store one")
     args = ap.parse_args()
     wl = wi.WORKLOADS[args.workload]
     if args.nrhs is not None:
@@ -339,9 +341,9 @@ def main():
     evaluate = plan.apply if args.op == "apply" else plan.apply_adjoint
     # batched plans: the tile shapes come from the autotuner, timed on this plan
     tiles = None
-    if precision.startswith("batched") and wl.nrhs % 2 == 0 and wl.nrhs <= 64:
+    if precision.startswith("batched") and wl.nrhs % 2 == 0 and wl.nrhs <= (64 if wl.p_radial == 3 else 48):
         t0 = time.perf_counter()
-        tiles = plan.autotune(wl.nrhs)
+        tiles = plan.autotune(wl.nrhs, cache=args.tune_cache)
         tiles["tune_s"] = time.perf_counter() - t0
     # every evaluation below replays a CUDA graph of the apply's launches; the graphs
     # (with and without the stage events) are captured during the warm-up

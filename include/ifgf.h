@@ -329,6 +329,42 @@ ifgf_status ifgf_plan_autotune(ifgf_plan *plan, int nrhs, int reps, double *ms, 
 ifgf_status ifgf_plan_set_tiles(ifgf_plan *plan, int leaf_shape, int cone_ctas_per_sm);
 
 /*
+ * Persistent tune cache.  The shapes ifgf_plan_autotune chooses depend on the device and
+ * on the workload's sizes, not on the densities, so they can be kept in a text file and
+ * reused by later plans and processes.  The file holds one line per workload,
+ *     <key> <leaf_shape> <cone_ctas_per_sm>
+ * with the values of ifgf_plan_set_tiles; lines are appended whole, the last valid line
+ * for a key wins and malformed or out-of-range lines are skipped (so the file may be
+ * shared by processes and edited by hand).  Host code only: no device work.
+ *
+ * ifgf_plan_tune_key writes the plan's key for nrhs right-hand sides into buf (cap
+ * bytes, at most 481 used): the device's name, SM count and compute capability, the
+ * precision, (P_s, P_ang), nrhs, N, the depth, the leaf factor count and the rows of the
+ * cone contraction (cousin plus upward evaluations), as one token without whitespace.
+ * Errors: IFGF_EINVAL (cap too small), IFGF_ECUDA (device query failed).
+ *
+ * ifgf_tune_cache_lookup sets *found to 1 and choice[2] to {leaf_shape,
+ * cone_ctas_per_sm} when path holds a valid line for key, else *found = 0 (also when the
+ * file does not exist).  Errors: IFGF_EINVAL for a NULL argument or a key that is empty,
+ * longer than 480 bytes or contains whitespace.
+ *
+ * ifgf_tune_cache_store appends the line for key and choice[2] to path (creating it).
+ * Errors: IFGF_EINVAL for a bad key, values out of range, or a file that cannot be
+ * written.
+ *
+ * ifgf_plan_autotune_cached looks the plan's key up in path: on a hit it sets the cached
+ * shapes (ifgf_plan_set_tiles) and sets *hit = 1 without any device work; otherwise it
+ * runs ifgf_plan_autotune(plan, nrhs, reps, ...) and appends the choice.  choice (NULL or
+ * [2]) receives the shapes in use.  Errors: those of ifgf_plan_autotune (checked on a hit
+ * too), and IFGF_EINVAL when the file cannot be written.
+ */
+ifgf_status ifgf_plan_tune_key(const ifgf_plan *plan, int nrhs, char *buf, int cap);
+ifgf_status ifgf_tune_cache_lookup(const char *path, const char *key, int *found, int *choice);
+ifgf_status ifgf_tune_cache_store(const char *path, const char *key, const int *choice);
+ifgf_status ifgf_plan_autotune_cached(ifgf_plan *plan, int nrhs, int reps, const char *path, int *choice, int *hit,
+                                      void *stream);
+
+/*
  * CUDA-graph replay of evaluations.  With on != 0, the launches of an evaluation
  * (ifgf_apply, ifgf_apply_adjoint, ifgf_apply_partial) are captured into a CUDA graph
  * the first time the plan evaluates with a given input buffer, output buffer, nrhs,

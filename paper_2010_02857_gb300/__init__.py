@@ -39,8 +39,10 @@ EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_p
            "ifgf_plan_get_cousins", "ifgf_plan_get_active", "ifgf_plan_get_values", "ifgf_plan_cone_ids",
            "ifgf_plan_geometry",
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_autotune", "ifgf_plan_set_tiles", "ifgf_plan_timings",
+           "ifgf_plan_tune_key", "ifgf_tune_cache_lookup", "ifgf_tune_cache_store", "ifgf_plan_autotune_cached",
            "ifgf_device_peak", "ifgf_last_error"]
 STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
+LEAF_SHAPES = ["16x8", "32x4", "8x16"]
 
 
 class IFGFError(RuntimeError):
@@ -89,6 +91,10 @@ def lib():
         L.ifgf_plan_set_graphs.argtypes = [P, i]
         L.ifgf_plan_autotune.argtypes = [P, i, i, P, P, P]
         L.ifgf_plan_set_tiles.argtypes = [P, i, i]
+        L.ifgf_plan_tune_key.argtypes = [P, i, ctypes.c_char_p, i]
+        L.ifgf_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P, P]
+        L.ifgf_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, P]
+        L.ifgf_plan_autotune_cached.argtypes = [P, i, i, ctypes.c_char_p, P, P, P]
         L.ifgf_plan_timings.argtypes = [P, P, P, P, i]
         L.ifgf_device_peak.argtypes = [i, P, P]
         L.ifgf_last_error.argtypes = [P]
@@ -187,6 +193,21 @@ def device_peak(which: str, stream=None) -> float:
 
 def plan_destroy(handle):
     _check(lib().ifgf_plan_destroy(handle))
+
+
+def tune_cache_lookup(path: str, key: str):
+    """ifgf_tune_cache_lookup: (leaf_shape, cone_ctas_per_sm) stored for key in the tune
+    cache file, or None."""
+    found = ctypes.c_int(0)
+    choice = (ctypes.c_int * 2)()
+    _check(lib().ifgf_tune_cache_lookup(os.fsencode(path), key.encode(), ctypes.byref(found), choice))
+    return (int(choice[0]), int(choice[1])) if found.value else None
+
+
+def tune_cache_store(path: str, key: str, leaf_shape: int, cone_ctas_per_sm: int):
+    """ifgf_tune_cache_store: append a tile-shape choice for key to the tune cache file."""
+    choice = (ctypes.c_int * 2)(int(leaf_shape), int(cone_ctas_per_sm))
+    _check(lib().ifgf_tune_cache_store(os.fsencode(path), key.encode(), choice))
 
 
 # ------------------------------------------------------------------------------------
@@ -348,14 +369,30 @@ class Plan:
     def set_profiling(self, on: bool):
         _check(lib().ifgf_plan_set_profiling(self.handle, int(bool(on))), self.handle)
 
-    def autotune(self, nrhs: int, reps: int = 3) -> dict:
-        """Time the batched path's tile shapes on this plan and keep the fastest."""
-        ms = np.zeros(5)
+    def autotune(self, nrhs: int, reps: int = 3, cache: str | None = None) -> dict:
+        """Time the batched path's tile shapes on this plan and keep the fastest.
+
+        With ``cache`` (a file path), a shape choice stored there for this plan's key is
+        taken without timing (``"cached": True``), and a new choice is appended to it.
+        """
         choice = np.zeros(2, dtype=np.int32)
+        if cache is not None:
+            hit = np.zeros(1, dtype=np.int32)
+            _check(lib().ifgf_plan_autotune_cached(self.handle, int(nrhs), int(reps), os.fsencode(cache),
+                                                   _ptr(choice), _ptr(hit), _stream()), self.handle)
+            return {"leaf_shape": LEAF_SHAPES[int(choice[0])], "cone_ctas_per_sm": int(choice[1]),
+                    "cached": bool(hit[0]), "key": self.tune_key(nrhs)}
+        ms = np.zeros(5)
         _check(lib().ifgf_plan_autotune(self.handle, int(nrhs), int(reps), _ptr(ms), _ptr(choice), _stream()),
                self.handle)
-        return {"leaf_shape": ["16x8", "32x4", "8x16"][int(choice[0])], "cone_ctas_per_sm": int(choice[1]),
+        return {"leaf_shape": LEAF_SHAPES[int(choice[0])], "cone_ctas_per_sm": int(choice[1]),
                 "leaf_ms": [float(x) for x in ms[:3]], "cone_ms": [float(x) for x in ms[3:]]}
+
+    def tune_key(self, nrhs: int) -> str:
+        """The tune-cache key of this plan for nrhs right-hand sides."""
+        buf = ctypes.create_string_buffer(512)
+        _check(lib().ifgf_plan_tune_key(self.handle, int(nrhs), buf, len(buf)), self.handle)
+        return buf.value.decode()
 
     def set_tiles(self, leaf_shape: int, cone_ctas_per_sm: int):
         """Set the batched path's tile shapes (leaf shape 0..2, 1 or 2 CTAs per SM)."""

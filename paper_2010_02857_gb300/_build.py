@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libifgf.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["ifgf_plan.cu", "ifgf_apply_f64.cu", "ifgf_apply_f32.cu", "ifgf_apply_f32_r4.cu", "ifgf_api.cu", "ifgf_noalloc.cu",
-           "ifgf_batched.cu", "ifgf_peak.cu"]
+           "ifgf_batched.cu", "ifgf_peak.cu", "ifgf_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,7 +21,6 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
 cudaError_t ifgf_batched_prepare();
-int ifgf_batched_max_nrhs(int Ps);
 cudaError_t ifgf_batched_autotune(PlanDev &pd, int nrhs, const void *sig, void *us, cudaStream_t st, int reps,
                                   float *ms);
 

@@ -257,6 +257,8 @@ inline size_t ifgf_elem_bytes(int precision) { return precision == IFGF_FP64 ? 1
 
 // plans whose interpolation contractions run on the tensor cores
 inline bool ifgf_is_batched(int precision) { return precision == IFGF_BATCHED_BF16 || precision == IFGF_BATCHED_FP16; }
+// largest nrhs of one tensor-core pass at the given radial order (defined with the kernels)
+int ifgf_batched_max_nrhs(int Ps);
 
 // Upward-table entry for value type T and NW = P_s + 2 P_ang weights.
 template <typename T, int NW> struct UpEntry {

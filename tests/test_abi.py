@@ -69,6 +69,8 @@ def test_plan_entry_points_reject_a_null_plan(libifgf):
         ("ifgf_plan_set_graphs", [P, i], (None, 1)),
         ("ifgf_plan_set_tiles", [P, i, i], (None, 0, 2)),
         ("ifgf_plan_autotune", [P, i, i, P, P, P], (None, 4, 1, None, None, None)),
+        ("ifgf_plan_autotune_cached", [P, i, i, ctypes.c_char_p, P, P, P], (None, 4, 1, b"x", None, None, None)),
+        ("ifgf_plan_tune_key", [P, i, ctypes.c_char_p, i], (None, 4, None, 0)),
         ("ifgf_plan_set_profiling", [P, i], (None, 1)),
         ("ifgf_apply", [P, P, P, i, P], (None, None, None, 1, None)),
         ("ifgf_apply_adjoint", [P, P, P, i, P], (None, None, None, 1, None)),

@@ -342,6 +342,9 @@ def test_host_pointer_path_matches_device_path(pkg, torch_cuda):
     assert np.array_equal(g.apply_adjoint(sigma), w1)
 
 
+LEAF = ["16x8", "32x4", "8x16"]
+
+
 @pytest.mark.parametrize("nrhs", [2, 24, 64])
 def test_autotuned_tile_shapes_give_the_same_result(pkg, torch_cuda, nrhs):
     # every leaf tile shape sums each output over the sources in the same order, and the
@@ -376,6 +379,35 @@ def test_autotuned_tile_shapes_give_the_same_result(pkg, torch_cuda, nrhs):
     with pytest.raises(pkg.IFGFError):
         b.set_tiles(3, 1)
     assert b.check() == 0
+
+
+def test_tune_cache_reuses_a_choice_across_plans(pkg, torch_cuda, tmp_path):
+    # the first plan of a workload is timed and its choice appended to the cache file; a
+    # second plan of the same workload takes the choice from the file without timing; a
+    # plan of another nrhs is a different key
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    path = str(tmp_path / "tune.txt")
+    x = torch.from_numpy(pts).cuda()
+    b1 = pkg.Plan(x, wl.kappa, 5, 3, 5, 1, 2, max_nrhs=16, precision="batched")
+    t1 = b1.autotune(16, reps=1, cache=path)
+    assert not t1["cached"] and " " not in t1["key"]
+    assert open(path).read().split() == [t1["key"], str(LEAF.index(t1["leaf_shape"])), str(t1["cone_ctas_per_sm"])]
+    b2 = pkg.Plan(x, wl.kappa, 5, 3, 5, 1, 2, max_nrhs=16, precision="batched")
+    assert b2.tune_key(16) == t1["key"]
+    b2.set_tiles((LEAF.index(t1["leaf_shape"]) + 1) % 3, 3 - t1["cone_ctas_per_sm"])  # not the cached shapes
+    t2 = b2.autotune(16, reps=1, cache=path)
+    assert t2["cached"] and t2["leaf_shape"] == t1["leaf_shape"] and t2["cone_ctas_per_sm"] == t1["cone_ctas_per_sm"]
+    st = b2.stats()
+    assert LEAF[st["tune_leaf"]] == t1["leaf_shape"] and st["tune_cone_ctas"] == t1["cone_ctas_per_sm"]
+    assert b2.tune_key(8) != t1["key"]
+    t3 = b2.autotune(8, reps=1, cache=path)
+    assert not t3["cached"] and len(open(path).read().splitlines()) == 2
+    with pytest.raises(pkg.IFGFError):
+        b2.autotune(3, cache=path)  # odd nrhs: rejected even though nothing is cached for it
+    s = torch.from_numpy(wi.complex_normal(7, (16, wl.n))).cuda().to(torch.complex64)
+    assert rel(b2.apply(s).cpu().numpy(), b1.apply(s).cpu().numpy()) < 1e-5
+    assert b1.check() == 0 and b2.check() == 0
 
 
 @pytest.mark.parametrize("precision,nrhs,flags", [("fp64", 1, 0), ("mixed", 3, 0), ("batched", 4, 0),

@@ -55,7 +55,7 @@ def test_rhs_sharded_apply_equals_single_process(nrhs):
     import ifgf_inputs as wi
     import paper_2010_02857_gb300 as pkg
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may hold a CUDA context
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), nrhs, out), nprocs=world, join=True)
         got = [out[r] for r in range(world)]

@@ -37,7 +37,7 @@ def test_max_over_ranks_takes_the_slowest_rank():
     import torch.multiprocessing as mp
     world = 2
     values = [12.5, 40.25]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may hold a CUDA context
         out = m.dict()
         mp.spawn(_rank_main, args=(world, _free_port(), values, out), nprocs=world, join=True)
         assert [out[r] for r in range(world)] == [max(values)] * world
@@ -101,7 +101,7 @@ def test_rhs_sharded_apply_gathers_the_single_rank_result():
     import ifgf_inputs as wi
     import oracle
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may hold a CUDA context
         out = m.dict()
         mp.spawn(_shard_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         got = [out[r] for r in range(world)]
