@@ -49,17 +49,23 @@ METRIC = "IFGF apply time and equivalent interactions/s (N^2/t) at rel.err<=1e-3
 UNIT = "interactions/s"
 
 # Algorithmic work of one upward evaluation (one parent interpolation point
-# interpolated from one child cone and re-centred): the sum-factorised 75-term
-# contraction, 2 * (75 + 15 + 3) = 186 real FMAs = 372 flops, plus the complex
-# multiply-accumulate by the re-centring factor, 8 flops.  The geometry (child cone,
-# Lagrange weights, factor) is box-independent and tabulated per level where that
+# interpolated from one child cone and re-centred), for P = P_s * P_ang^2 nodes: the
+# sum-factorised contraction over the azimuthal, polar and radial node indices,
+# 2 * (P + P_s * P_ang + P_s) real FMAs (186 FMAs = 372 flops at (3, 5)), plus the
+# complex multiply-accumulate by the re-centring factor, 8 flops.  The geometry (child
+# cone, Lagrange weights, factor) is box-independent and tabulated per level where that
 # pays, so it is not counted.
-UPWARD_FLOPS_PER_EVAL = 372 + 8
-# Adjoint: every cousin or upward evaluation, transposed, is a rank-1 update of the 75
+def upward_flops_per_eval(ps: int, pa: int) -> int:
+    return 4 * (ps * pa * pa + ps * pa + ps) + 8
+
+
+# Adjoint: every cousin or upward evaluation, transposed, is a rank-1 update of the P
 # values of its cone's adjoint by the Lagrange weight product times the conjugated factor
-# times the reader's value: 75 real-by-complex multiply-adds (300 flops) plus the complex
+# times the reader's value: P real-by-complex multiply-adds (4 P flops) plus the complex
 # product of factor and value (8 flops) per RHS.
-ADJOINT_FLOPS_PER_EVAL = 300 + 8
+def adjoint_flops_per_eval(ps: int, pa: int) -> int:
+    return 4 * ps * pa * pa + 8
+
 
 NUM_SMS = 152
 
@@ -299,6 +305,8 @@ def main():
                     help="override the workload's number of right-hand sides (same generator)")
     ap.add_argument("--op", default="apply", choices=["apply", "adjoint"],
                     help="time ifgf_apply (default) or ifgf_apply_adjoint")
+    ap.add_argument("--plan-flags", type=int, default=0,
+                    help="ifgf_options.flags of the plan (e.g. 32: no evaluation caches, as in plans too large for them)")
     ap.add_argument("--tune-cache", default=None,
                     help="tune-cache file of batched plans: reuse a stored tile-shape choice, else time and store one")
     args = ap.parse_args()
@@ -322,7 +330,7 @@ def main():
     pts = torch.from_numpy(wl.points()).to(dev)
     t0 = time.perf_counter()
     plan = pkg.Plan(pts, wl.kappa, wl.levels, wl.p_radial, wl.p_angular, wl.leaf_ns, wl.leaf_nc,
-                    max_nrhs=wl.nrhs, precision=precision, leaf_max=wl.leaf_max)
+                    max_nrhs=wl.nrhs, precision=precision, leaf_max=wl.leaf_max, flags=args.plan_flags)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
     stats = plan.stats()
@@ -406,27 +414,31 @@ def main():
         # k_adj_level: the transposed cousin-target and upward evaluations of every level
         ad_ms = st["adj_level"]["ms"] / calls
         ad_launches = st["adj_level"]["launches"] / calls
-        flops = (up_evals + cousin_evals) * ADJOINT_FLOPS_PER_EVAL * nrhs
+        adj_flops = adjoint_flops_per_eval(wl.p_radial, wl.p_angular)
+        flops = (up_evals + cousin_evals) * adj_flops * nrhs
         peak = fp64_peak if precision == "fp64" else fp32_peak
         roofline = {"bound": "alu", "kernel": "k_adj_level", "peak_source": peak_src,
-                    "work": f"{up_evals + cousin_evals} transposed evaluations x {ADJOINT_FLOPS_PER_EVAL} flops "
+                    "work": f"{up_evals + cousin_evals} transposed evaluations x {adj_flops} flops "
                             f"per RHS, {ad_launches:.0f} launches, {ad_ms:.3f} ms"}
         up_ms = ad_ms
     elif precision.startswith("batched"):
         # tcgen05 cone kernels: every cousin and upward evaluation is one GEMM row of
-        # 75 weights x 2 nrhs real columns (useful flops; the BF16 hi/lo split and
-        # the padding of K to 80 are not counted)
+        # P weights x 2 nrhs real columns (useful flops; the hi/lo operand split and
+        # the padding of K to a multiple of 16 are not counted)
         rows = up_evals + cousin_evals
-        flops = rows * 2 * 75 * 2 * nrhs
+        npts = wl.p_radial * wl.p_angular ** 2
+        flops = rows * 2 * npts * 2 * nrhs
         peak = float(measured_peaks().get("bf16_tflops", 1900.0))
         roofline = {"bound": "tensor", "kernel": "k_cone_mma", "peak_source": "measured bf16 dense (burst)",
-                    "work": f"{rows} GEMM rows x {2 * 75 * 2 * nrhs} flops per apply, "
+                    "work": f"{rows} GEMM rows x {2 * npts * 2 * nrhs} flops per apply, "
                             f"{up_launches:.0f} launches, {up_ms:.3f} ms"}
     else:
-        flops = up_evals * UPWARD_FLOPS_PER_EVAL * nrhs
+        up_flops = upward_flops_per_eval(wl.p_radial, wl.p_angular)
+        flops = up_evals * up_flops * nrhs
         peak = fp64_peak if precision == "fp64" else fp32_peak
-        roofline = {"bound": "alu", "kernel": "k_upward", "peak_source": peak_src,
-                    "work": f"{up_evals} upward evaluations x {UPWARD_FLOPS_PER_EVAL} {pipe} flops per RHS, "
+        kname = "k_upward" if precision == "fp64" else "k_upward_runs + k_upward_staged"
+        roofline = {"bound": "alu", "kernel": kname, "peak_source": peak_src,
+                    "work": f"{up_evals} upward evaluations x {up_flops} {pipe} flops per RHS, "
                             f"{nrhs} RHS, {up_launches:.0f} launches, {up_ms:.3f} ms"}
     achieved = flops / (up_ms * 1e-3) / 1e12 if up_ms > 0 else None
     traffic = (traffic_per_launch(wl.name, precision)
@@ -446,7 +458,7 @@ def main():
                 "config": {"workload": wl.name, "op": args.op, "n": n, "nrhs": nrhs, "kappa": wl.kappa, "levels": wl.levels,
                            "p_radial": wl.p_radial, "p_angular": wl.p_angular,
                            "leaf_cones": [wl.leaf_ns, wl.leaf_nc], "precision": precision,
-                           "leaf_max": wl.leaf_max,
+                           "leaf_max": wl.leaf_max, "plan_flags": args.plan_flags,
                            "l2": "flushed between steps (256 MB write)", "launch": "CUDA graph replay",
                            "parallelism": f"rhs-sharded x{world}", "batch_nrhs": batch},
                 "t_plan_ms": t_plan * 1e3, "tiles": tiles,

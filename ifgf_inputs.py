@@ -349,6 +349,13 @@ WORKLOADS = {
                                  leaf_ns=3, leaf_nc=6, nrhs=8, targets=1_024, seed=5, surface="sphere",
                                  precision="mixed",
                                  description="Fibonacci sphere N=25165824, 256 lambda, D=9, 8 RHS"),
+    # the 256-wavelength sphere scaled down 16x (same leaf box width of one wavelength,
+    # same leaf cones, same points per leaf): its kernels see the same per-box geometry
+    # with level arrays of about 1 GB, so single kernels of it can be profiled
+    "sphere_64lambda": Workload("sphere_64lambda", 1_572_864, wavelengths_to_kappa(2.0, 64), 7,
+                                leaf_ns=3, leaf_nc=6, nrhs=8, targets=1_024, seed=5, surface="sphere",
+                                precision="mixed",
+                                description="Fibonacci sphere N=1572864, 64 lambda, D=7, 8 RHS"),
 }
 
 

@@ -111,13 +111,15 @@ typedef struct {
                        the child cone values from L1, instead of one warp per parent cone
                        in runs of nodes that share a child cone (testing: the two kernels
                        sum in the same order);
-                       bit 10: the run kernel takes at most 8 runs per pass (testing:
-                       exercises its multi-pass path);
+                       bit 10: the run kernel's runs are taken by 8 lanes instead of 32
+                       (testing: every lane then takes several runs of a child step);
                        bit 11: FP32 upward steps whose geometry is computed on the fly use
                        the run kernel too (by default they use one node per lane, which
                        keeps the FP64 geometry work dense; testing and measurement). */
-    long long value_budget_bytes; /* device bytes for cone values; 0 = 60% of the free
-                       memory at plan time.  When the values of every level for
+    long long value_budget_bytes; /* device bytes for cone values; 0 = 85% of the free
+                       memory at plan time less the sorted density and field buffers and
+                       a reserve of min(24 GB, a tenth of the device) for the adjoint's
+                       transpose lists and workspace.  When the values of every level for
                        max_nrhs right-hand sides exceed it, the plan keeps two levels
                        (d and d-1) and applies right-hand sides in chunks that fit; the
                        per-level values returned by ifgf_plan_get_values are then those
@@ -383,10 +385,12 @@ ifgf_status ifgf_plan_set_graphs(ifgf_plan *plan, int on);
 
 /*
  * Totals since profiling was turned on: ms[s] milliseconds and launches[s] kernel
- * launches of stage s, calls = profiled calls; count >= 7.  Stages: 0 density
+ * launches of stage s, calls = profiled calls; count >= 8.  Stages: 0 density
  * permutation, 1 leaf analytic factors, 2 upward interpolation (all levels),
  * 3 target evaluation (near + cousin interpolation), 4 output permutation,
- * 5 adjoint cone levels, 6 adjoint source evaluation.
+ * 5 adjoint cone levels, 6 adjoint source evaluation (and the conjugated near field),
+ * 7 transpose lists that the adjoint of a two-buffer plan builds between its launches
+ * (launch count 0: their sorts are library kernels).
  */
 ifgf_status ifgf_plan_timings(const ifgf_plan *plan, double *ms, int64_t *launches, int64_t *calls,
                               int count);

@@ -41,7 +41,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_apply", "ifgf_apply_adjoint", "ifgf_apply_p
            "ifgf_plan_stats", "ifgf_plan_check", "ifgf_plan_set_profiling", "ifgf_plan_set_graphs", "ifgf_plan_autotune", "ifgf_plan_set_tiles", "ifgf_plan_timings",
            "ifgf_plan_tune_key", "ifgf_tune_cache_lookup", "ifgf_tune_cache_store", "ifgf_plan_autotune_cached",
            "ifgf_device_peak", "ifgf_last_error"]
-STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval"]
+STAGES = ["permute_in", "leaf", "upward", "eval", "permute_out", "adj_level", "adj_eval", "adj_lists"]
 LEAF_SHAPES = ["16x8", "32x4", "8x16"]
 
 

@@ -21,6 +21,9 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
 cudaError_t ifgf_run_batched(const PlanDev &pd, int nrhs, const void *in_user, void *out_user, void *in_sorted,
                              void *out_sorted, int mode, cudaStream_t st, StageTimer &tm);
 cudaError_t ifgf_batched_prepare();
+// shared-memory limits of the FP32 run kernels (one per translation unit that holds them)
+cudaError_t ifgf_prepare_runs_r1();
+cudaError_t ifgf_prepare_runs_r4();
 cudaError_t ifgf_batched_autotune(PlanDev &pd, int nrhs, const void *sig, void *us, cudaStream_t st, int reps,
                                   float *ms);
 
@@ -165,6 +168,12 @@ extern "C" ifgf_status ifgf_plan_create(const double *points, int64_t n, double 
     if (s == IFGF_OK && ifgf_is_batched(o.precision) && ifgf_batched_prepare() != cudaSuccess) {
         cudaGetLastError();
         p->last_error = "shared-memory limit of the tensor-core kernel";
+        s = IFGF_ECUDA;
+    }
+    if (s == IFGF_OK && o.precision != IFGF_FP64 &&
+        (ifgf_prepare_runs_r1() != cudaSuccess || ifgf_prepare_runs_r4() != cudaSuccess)) {
+        cudaGetLastError();
+        p->last_error = "shared-memory limit of the run kernel";
         s = IFGF_ECUDA;
     }
     if (s != IFGF_OK) {

@@ -9,6 +9,12 @@ cudaError_t ifgf_run_typed_f32(const PlanDev &pd, int nrhs, const void *in_user,
     return ifgf::run_typed<float>(pd, nrhs, in_user, out_user, in_sorted, out_sorted, mode, adjoint, st, tm);
 }
 
+cudaError_t ifgf_prepare_runs_r1()
+{
+    cudaError_t e = ifgf::set_run_smem_limit<1, 3, 5>();
+    return e == cudaSuccess ? ifgf::set_run_smem_limit<1, 4, 7>() : e;
+}
+
 cudaError_t ifgf_build_uptable_f32(const PlanDev &pd, int d, void *tab, cudaStream_t st)
 {
     return ifgf::build_uptable<float>(pd, d, tab, st);

@@ -31,6 +31,9 @@
 // launch of the FP32 kernels blocked for 4 right-hand sides (ifgf_apply_f32_r4.cu)
 cudaError_t ifgf_launch_f32_r4(const PlanDev &pd, int nrhs, const void *in, void *out, int mode, int adjoint,
                                cudaStream_t st, StageTimer &tm);
+// the FP32 upward step d -> d-1 for more than 4 right-hand sides: the run kernel on
+// blocks of 4 (ifgf_apply_f32_r4.cu)
+void ifgf_upward_runs_blocks(const PlanDev &pd, int d, int nrhs, cudaStream_t st);
 
 namespace ifgf {
 
@@ -192,7 +195,7 @@ __device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 
     const float a = __fdividef((float)kInv4Pi, r);
     if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
     float c, s;
-    sincosf(kf * r, &s, &c);
+    expi_f32(kf * r, c, s);
     return {a * c, a * s};
 }
 
@@ -214,7 +217,7 @@ __device__ __forceinline__ cpx<float> leaf_factor32(float Rf, float dx, float dy
     if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
     const float ph = __fdividef(kf * num, r1 + Rf);
     float c, s;
-    sincosf(ph, &s, &c);
+    expi_f32(ph, c, s);
     return {a * c, a * s};
 }
 
@@ -285,7 +288,7 @@ __device__ __forceinline__ cpx<T> recentre(double kappa, double Rj, const double
         const float yd = fmaf((float)dir[0], fx, fmaf((float)dir[1], fy, (float)dir[2] * fz));
         const float diff = __fdividef(fmaf(-2.0f * Rf, yd, dd), rkf + Rf);
         float c, s;
-        sincosf((float)kappa * diff, &s, &c);
+        expi_f32((float)kappa * diff, c, s);
         return {a * c, a * s};
     }
 }
@@ -680,7 +683,7 @@ __global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int
 //      into shared memory: local coordinates, factor, child cone slot;
 //   B. groups the nodes by child cone slot (ballots) and cuts each group into runs of at
 //      most kRunK nodes, in node order;
-//   C. copies the values of the first kRunStage cones into the warp's shared-memory stage
+//   C. copies the values of the first run_stage_cones(P) cones into the warp's shared-memory stage
 //      (coalesced 16-byte loads);
 //   D. gives each lane one run: it reads each value of its cone once and applies it to the
 //      run's kRunK evaluations (the weight products (ws wt) wp per node, so that only
@@ -688,65 +691,129 @@ __global__ void __launch_bounds__(32 * kUpWarps) k_upward_staged(PlanDev pd, int
 //      accumulator in shared memory.
 // Every node sums its children in the same order as k_upward; the contraction associates
 // its products differently (the same polynomial, equal to FP32 rounding).  Cones beyond
-// the first kRunStage of a child step (rare) are read from global memory; more than 32 runs
-// (rare) take a second pass.
+// the first run_stage_cones(P) of a child step are read from global memory.  A child step has at
+// most P runs (every group of g nodes gives ceil(g / kRunK)); lanes take them 32 apart, so
+// a step with more than 32 runs gives some lanes a second one (each node is in one run,
+// so no two lanes write the same accumulator).
 constexpr int kRunK = 3;
-constexpr int kRunStage = 4;
+// cones staged per child step: 4 at (3, 5); 2 at (4, 7), whose cones are 2.6 times larger
+// (a parent cone's nodes fall into 1 or 2 cones of a child nearly always)
+__host__ __device__ constexpr int run_stage_cones(int P) { return P > 100 ? 2 : 4; }
 constexpr int kRunWarps = 2;  // 2 x 14.3 KB of shared memory per CTA (4 right-hand sides), under the 48 KB default
 
-// the run's evaluations: values src[node][r] (r < nrhs) of one child cone, per evaluation e
+// Shape of the run kernel per register blocking R and cone size P: whether the contraction
+// unrolls its angular loops (compile-time weight indices and value offsets, more
+// registers), and the CTAs per SM its register budget is sized for.
+//   - one right-hand side: unrolled, 6 CTAs (the select chains of the rolled form cost
+//     more than its FMAs);
+//   - four at (3, 5): rolled, 8 CTAs (measured faster on the 256-wavelength sphere than
+//     unrolled at 6; shared memory admits 7 CTAs of 30 KB, which takes 128 registers too);
+//   - four at (4, 7): unrolled, 4 CTAs (shared memory admits 4 CTAs of 53 KB).
+template <int R, int P>
+struct RunShape {
+    static constexpr bool unroll_angular = R == 1 || P > 100;
+    static constexpr int min_ctas = R == 1 ? 6 : (P > 100 ? 4 : 8);
+};
+
+// the run's evaluations: values src[node * stride + r] (r < nb) of one child cone, per evaluation e
 // the weights w[e] = (ws (PS), wt (PA), wp (PA)); out[e][r] = sum over the nodes (a, b, c) of
-// (ws[a] wt[b]) wp[c] src[(a PA + b) PA + c][r].  Each value is read once and applied to the
-// run's kRunK evaluations; per evaluation only the accumulators and the weights are live.
-template <int R, int PS, int PA, typename Src>
-__device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)[PS + 2 * PA], cpx<float> (*out)[R])
+// (ws[a] wt[b]) wp[c] src[(a PA + b) PA + c][r], in node order.  Each value is read once and
+// applied to the run's kRunK evaluations; per evaluation only the accumulators and the
+// weights are live.  Rolled indices take their weights by selects, so that w stays in
+// registers.
+template <int R, int PS, int PA>
+__device__ __forceinline__ void run_values(const float2 *p, int stride, int nb, float *v)
 {
+    if (R == 4 && nb == 4 && stride == 4) {
+        const float4 v01 = reinterpret_cast<const float4 *>(p)[0];
+        const float4 v23 = reinterpret_cast<const float4 *>(p)[1];
+        v[0] = v01.x; v[1] = v01.y; v[2] = v01.z; v[3] = v01.w;
+        v[4] = v23.x; v[5] = v23.y; v[6] = v23.z; v[7] = v23.w;
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 x = make_float2(0.f, 0.f);
+            if (R == 1 || r < nb) x = p[r];
+            v[2 * r] = x.x;
+            v[2 * r + 1] = x.y;
+        }
+    }
+}
+
+template <int R, int PS, int PA>
+__device__ __forceinline__ void run_fma(const float (*w)[PS + 2 * PA], const float *wab, int c, const float *v,
+                                        cpx<float> (*out)[R])
+{
+#pragma unroll
+    for (int e = 0; e < kRunK; ++e) {
+        const float wn = wab[e] * w[e][PS + PA + c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            out[e][r].x += wn * v[2 * r];
+            out[e][r].y += wn * v[2 * r + 1];
+        }
+    }
+}
+
+template <int R, int PS, int PA, bool FULL>
+__device__ __forceinline__ void contract_run(const float2 *src, int stride_, int nb_, const float (*w)[PS + 2 * PA],
+                                             cpx<float> (*out)[R])
+{
+    // FULL: a packed block of R right-hand sides (the common case), with compile-time strides
+    const int stride = FULL ? R : stride_, nb = FULL ? R : nb_;
 #pragma unroll
     for (int e = 0; e < kRunK; ++e)
 #pragma unroll
         for (int r = 0; r < R; ++r) out[e][r] = {0.f, 0.f};
+    if constexpr (RunShape<R, PS * PA * PA>::unroll_angular) {
+        // a rolled; b and c unrolled
 #pragma unroll 1
-    for (int ab = 0; ab < PS * PA; ++ab) {
-        const int a = ab / PA, b = ab - a * PA;
-        float wab[kRunK];
-#pragma unroll
-        for (int e = 0; e < kRunK; ++e) {
-            // w[e][a] and w[e][PS + b] with the rolled index, by selects (w stays in registers)
-            float wa = w[e][0], wb = w[e][PS];
-#pragma unroll
-            for (int m = 1; m < PS; ++m)
-                if (a == m) wa = w[e][m];
-#pragma unroll
-            for (int m = 1; m < PA; ++m)
-                if (b == m) wb = w[e][PS + m];
-            wab[e] = wa * wb;
-        }
-#pragma unroll
-        for (int c = 0; c < PA; ++c) {
-            const int idx = ab * PA + c;
-            float v[2 * R];
-            if (R == 4 && nrhs == 4) {
-                const float4 v01 = reinterpret_cast<const float4 *>(src)[idx * 2];
-                const float4 v23 = reinterpret_cast<const float4 *>(src)[idx * 2 + 1];
-                v[0] = v01.x; v[1] = v01.y; v[2] = v01.z; v[3] = v01.w;
-                v[4] = v23.x; v[5] = v23.y; v[6] = v23.z; v[7] = v23.w;
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float2 x = make_float2(0.f, 0.f);
-                    if (R == 1 || r < nrhs) x = src[idx * nrhs + r];
-                    v[2 * r] = x.x;
-                    v[2 * r + 1] = x.y;
-                }
-            }
+        for (int a = 0; a < PS; ++a) {
+            float wa[kRunK];
 #pragma unroll
             for (int e = 0; e < kRunK; ++e) {
-                const float wn = wab[e] * w[e][PS + PA + c];
+                wa[e] = w[e][0];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    out[e][r].x += wn * v[2 * r];
-                    out[e][r].y += wn * v[2 * r + 1];
+                for (int m = 1; m < PS; ++m)
+                    if (a == m) wa[e] = w[e][m];
+            }
+            const float2 *sa = src + (size_t)a * PA * PA * stride;
+#pragma unroll
+            for (int b = 0; b < PA; ++b) {
+                float wab[kRunK];
+#pragma unroll
+                for (int e = 0; e < kRunK; ++e) wab[e] = wa[e] * w[e][PS + b];
+#pragma unroll
+                for (int c = 0; c < PA; ++c) {
+                    float v[2 * R];
+                    run_values<R, PS, PA>(sa + (size_t)(b * PA + c) * stride, stride, nb, v);
+                    run_fma<R, PS, PA>(w, wab, c, v, out);
                 }
+            }
+        }
+    } else {
+        // (a, b) rolled; c unrolled
+#pragma unroll 1
+        for (int ab = 0; ab < PS * PA; ++ab) {
+            const int a = ab / PA, b = ab - a * PA;
+            float wab[kRunK];
+#pragma unroll
+            for (int e = 0; e < kRunK; ++e) {
+                float wa = w[e][0], wb = w[e][PS];
+#pragma unroll
+                for (int m = 1; m < PS; ++m)
+                    if (a == m) wa = w[e][m];
+#pragma unroll
+                for (int m = 1; m < PA; ++m)
+                    if (b == m) wb = w[e][PS + m];
+                wab[e] = wa * wb;
+            }
+            const float2 *sab = src + (size_t)ab * PA * stride;
+#pragma unroll
+            for (int c = 0; c < PA; ++c) {
+                float v[2 * R];
+                run_values<R, PS, PA>(sab + (size_t)c * stride, stride, nb, v);
+                run_fma<R, PS, PA>(w, wab, c, v, out);
             }
         }
     }
@@ -754,19 +821,20 @@ __device__ __forceinline__ void contract_run(Src src, int nrhs, const float (*w)
 
 // Shared memory of one warp of k_upward_runs for P nodes and nrhs right-hand sides, in this
 // order (each array starts on a boundary of its element type; 8-byte arrays first):
-//   stage [kRunStage][P][nrhs] complex   (16-byte aligned: the 16-byte copies)
+//   stage [run_stage_cones(P)][P][nb] complex   (16-byte aligned: the 16-byte copies)
 //   acc   [P][R] complex, f [P] complex  (8 bytes)
-//   t     [P][3] float, slot [P], runs [32][kRunK], run group [32]  (4 bytes)
+//   t     [P][3] float, slot [P], runs [P][kRunK], run group [P]  (4 bytes)
 // The warp's block is a multiple of 16 bytes, so every warp's stage stays 16-byte aligned.
-__host__ __device__ constexpr size_t run_stage_floats(int P, int nrhs) { return (size_t)kRunStage * P * nrhs * 2; }
-__host__ __device__ constexpr size_t run_warp_bytes(int P, int R, int nrhs)
+__host__ __device__ constexpr size_t run_stage_floats(int P, int nb) { return (size_t)run_stage_cones(P) * P * nb * 2; }
+__host__ __device__ constexpr size_t run_warp_bytes(int P, int R, int nb)
 {
-    return ((run_stage_floats(P, nrhs) + (size_t)P * R * 2 + (size_t)P * 2 + (size_t)P * 3) * 4 + (size_t)P * 4 +
-            32 * kRunK * 4 + 32 * 4 + 15) / 16 * 16;
+    return ((run_stage_floats(P, nb) + (size_t)P * R * 2 + (size_t)P * 2 + (size_t)P * 3) * 4 + (size_t)P * 4 +
+            (size_t)P * kRunK * 4 + (size_t)P * 4 + 15) / 16 * 16;
 }
 
 template <int R, int PS, int PA, bool TAB>
-__global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, int d, int nrhs)
+__global__ void __launch_bounds__(32 * kRunWarps, RunShape<R, PS * PA * PA>::min_ctas)
+    k_upward_runs(PlanDev pd, int d, int nrhs, int r0, int nb)
 {
     constexpr int P = PS * PA * PA;
     constexpr int NW = PS + 2 * PA;
@@ -779,14 +847,14 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
     const int slot = blockIdx.x * kRunWarps + warp;
     if (slot >= Lp.nact) return;  // the whole warp
     // this warp's shared memory
-    float *base = (float *)((unsigned char *)s_runs_raw + (size_t)warp * run_warp_bytes(P, R, nrhs));
+    float *base = (float *)((unsigned char *)s_runs_raw + (size_t)warp * run_warp_bytes(P, R, nb));
     float2 *stage = (float2 *)base;
-    float2 *acc = (float2 *)(base + run_stage_floats(P, nrhs));  // [P][R]
+    float2 *acc = (float2 *)(base + run_stage_floats(P, nb));  // [P][R]
     float2 *gf = acc + (size_t)P * R;                           // [P]
     float *gt = (float *)(gf + P);                              // [P][3]
     int *gsl = (int *)(gt + (size_t)P * 3);                     // [P]
-    int *runs = gsl + P;                                        // [32][kRunK]
-    int *rgrp = runs + 32 * kRunK;                              // [32] group of each run
+    int *runs = gsl + P;                                        // [P][kRunK]
+    int *rgrp = runs + P * kRunK;                               // [P] group of each run
     const int j = Lp.act_box[slot];
     const int pcone = Lp.act_cone[slot];
     const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
@@ -800,7 +868,7 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
         tab = (const UpEntry32 *)L.utab + (size_t)row * 8 * P;
     }
     for (int q = lane; q < P * R; q += 32) acc[q] = make_float2(0.f, 0.f);
-    const int rmax = (pd.flags & 1024) ? 8 : 32;  // runs per pass (flags bit 10: 8, testing)
+    const int rstep = (pd.flags & 1024) ? 8 : 32;  // lanes taking runs (flags bit 10: 8, testing)
     for (int kk = 0; kk < nch; ++kk) {
         const int k = k0 + kk;
         const int oct = (int)(L.key[k] & 7u);
@@ -842,7 +910,7 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
 #pragma unroll
         for (int c = 0; c < NCH; ++c) pend[c] = __ballot_sync(kFull, sl_c[c] >= 0);
         int nruns = 0, ngroups = 0;
-        for (int q = lane; q < 32 * kRunK; q += 32) runs[q] = -1;
+        for (int q = lane; q < P * kRunK; q += 32) runs[q] = -1;
         __syncwarp();
         while (true) {
             int c0 = -1;
@@ -864,70 +932,40 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
                 const unsigned m = __ballot_sync(kFull, mem);
                 if (mem) {
                     const int rank = before + __popc(m & ((1u << lane) - 1u));
-                    const int run = nruns + rank / kRunK;
-                    if (run < rmax) runs[run * kRunK + rank % kRunK] = lane + 32 * c;
+                    runs[(nruns + rank / kRunK) * kRunK + rank % kRunK] = lane + 32 * c;
                 }
                 before += __popc(m);
                 pend[c] &= ~m;
             }
             const int nr = (before + kRunK - 1) / kRunK;
-            for (int q = nruns + lane; q < nruns + nr && q < rmax; q += 32) rgrp[q] = g;
+            for (int q = nruns + lane; q < nruns + nr; q += 32) rgrp[q] = g;
             // C. stage this group's cone values (asynchronous copies: the groups' loads
             // overlap, and all complete at the wait below)
-            if (g < kRunStage) {
-                const int vals = P * nrhs;
-                const float2 *from = (const float2 *)L.F + (size_t)g_sl * vals;
-                float2 *to = stage + (size_t)g * vals;
-                if ((vals & 1) == 0) {
-                    for (int q = lane; q < vals / 2; q += 32) cp_async16(to + 2 * q, from + 2 * q);
+            if (g < run_stage_cones(P)) {
+                // values [r0, r0 + nb) of each node, packed as [P][nb]
+                const float2 *from = (const float2 *)L.F + (size_t)g_sl * P * nrhs + r0;
+                float2 *to = stage + (size_t)g * P * nb;
+                if (nb == nrhs && (P * nb) % 2 == 0) {  // the whole cone, contiguous
+                    for (int q = lane; q < P * nb / 2; q += 32) cp_async16(to + 2 * q, from + 2 * q);
+                } else if (nb % 2 == 0 && nrhs % 2 == 0 && r0 % 2 == 0) {  // 16-byte pairs per node
+                    for (int q = lane; q < P * nb / 2; q += 32) {
+                        const int node = q / (nb / 2), h = q - node * (nb / 2);
+                        cp_async16(to + node * nb + 2 * h, from + (size_t)node * nrhs + 2 * h);
+                    }
                 } else {
-                    for (int q = lane; q < vals; q += 32) cp_async8(to + q, from + q);
+                    for (int q = lane; q < P * nb; q += 32) {
+                        const int node = q / nb, r = q - node * nb;
+                        cp_async8(to + q, from + (size_t)node * nrhs + r);
+                    }
                 }
             }
             nruns += nr;
         }
         cp_async_wait_all();
         __syncwarp();
-        // D. the runs (more passes when a child step has more than rmax)
-        for (int pass = 0; pass * rmax < nruns; ++pass) {
-            if (pass > 0) {  // rebuild the runs beyond the first 32 from the groups
-                __syncwarp();
-                for (int q = lane; q < 32 * kRunK; q += 32) runs[q] = -1;
-                __syncwarp();
-                int cnt = 0, g = 0;
-                if (lane == 0) {
-                    // nodes in group order, node order within a group: run index r counts on
-                    for (int gg = 0; gg < ngroups; ++gg) {
-                        int sl0 = -1;
-                        for (int node = 0; node < P; ++node) {
-                            if (gsl[node] < 0) continue;
-                            // the group of a node: the order of first appearance of its slot
-                            bool first = true;
-                            for (int m = 0; m < node; ++m)
-                                if (gsl[m] == gsl[node]) { first = false; break; }
-                            if (first) {
-                                if (g == gg) sl0 = gsl[node];
-                                ++g;
-                            }
-                        }
-                        g = 0;
-                        int rank = 0;
-                        for (int node = 0; node < P; ++node) {
-                            if (gsl[node] != sl0) continue;
-                            const int run = cnt + rank / kRunK - rmax * pass;
-                            if (run >= 0 && run < rmax) {
-                                runs[run * kRunK + rank % kRunK] = node;
-                                rgrp[run] = gg;
-                            }
-                            ++rank;
-                        }
-                        cnt += (rank + kRunK - 1) / kRunK;
-                    }
-                }
-                __syncwarp();
-            }
-            const int r = lane;
-            if (r < rmax && pass * rmax + r < nruns) {
+        // D. the runs, lane l taking runs l, l + rstep, ...
+        if (lane < rstep) {
+            for (int r = lane; r < nruns; r += rstep) {
                 int nodes[kRunK];
                 float w[kRunK][NW];
 #pragma unroll
@@ -940,11 +978,13 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
                 }
                 const int g = rgrp[r];
                 cpx<float> val[kRunK][R];
-                if (g < kRunStage) {
-                    contract_run<R, PS, PA>((const float2 *)(stage + (size_t)g * P * nrhs), nrhs, w, val);
+                if (g < run_stage_cones(P)) {
+                    const float2 *sg = stage + (size_t)g * P * nb;
+                    if (nb == R) contract_run<R, PS, PA, true>(sg, R, R, w, val);
+                    else contract_run<R, PS, PA, false>(sg, nb, nb, w, val);
                 } else {
                     const int sl = gsl[nodes[0]];
-                    contract_run<R, PS, PA>((const float2 *)L.F + (size_t)sl * P * nrhs, nrhs, w, val);
+                    contract_run<R, PS, PA, false>((const float2 *)L.F + (size_t)sl * P * nrhs + r0, nrhs, nb, w, val);
                 }
 #pragma unroll
                 for (int e = 0; e < kRunK; ++e) {
@@ -966,36 +1006,71 @@ __global__ void __launch_bounds__(32 * kRunWarps, 8) k_upward_runs(PlanDev pd, i
     for (int q = lane; q < P; q += 32)
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (R == 1 || r < nrhs) {
+            if (R == 1 || r < nb) {
                 const float2 a = acc[q * R + r];
-                st<float>(Lp.F, ((size_t)slot * P + q) * nrhs + r, cpx<float>{a.x, a.y});
+                st<float>(Lp.F, ((size_t)slot * P + q) * nrhs + r0 + r, cpx<float>{a.x, a.y});
             }
 }
 
-// Launch of the upward step d -> d-1: the run kernel for FP32 values with up to 4
-// right-hand sides per pass (flags bit 9 selects k_upward, for comparison tests), else
-// k_upward.
+// Dynamic shared memory of the run kernel, at most: (4, 7) with 4 right-hand sides per block
+// takes 53 KB per CTA, above the 48 KB default, so every instantiation is given this
+// limit once at plan creation (ifgf_prepare_runs).
+constexpr int kRunSmemMax = 64 * 1024;
+
+template <int R, int PS, int PA>
+inline cudaError_t set_run_smem_limit()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_upward_runs<R, PS, PA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kRunSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_upward_runs<R, PS, PA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kRunSmemMax);
+    return e;
+}
+
+// One launch of the run kernel for right-hand sides [r0, r0 + nb) of nrhs (nb <= R).
+template <int R, int PS, int PA>
+inline void launch_runs(const PlanDev &pd, int d, int nrhs, int r0, int nb, cudaStream_t st)
+{
+    constexpr int P = PS * PA * PA;
+    const size_t smem = (size_t)kRunWarps * run_warp_bytes(P, R, nb);
+    const int nslot = pd.lev[d - 1].nact;
+    const int grid = (nslot + kRunWarps - 1) / kRunWarps;
+    if (pd.lev[d].utab) k_upward_runs<R, PS, PA, true><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs, r0, nb);
+    else k_upward_runs<R, PS, PA, false><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs, r0, nb);
+}
+
+// Launch of the upward step d -> d-1 for FP32 values: the run kernel where the geometry is
+// stored (table or cache; flags bit 11: also where it is computed on the fly), with up to 4
+// right-hand sides per launch (blocks of 4 for more); the staged kernel where the geometry
+// is computed on the fly (up to 4 right-hand sides); k_upward otherwise, and for FP64
+// values (flags bit 9 selects k_upward for FP32 too, for comparison tests).
 template <typename T, int R, int PS, int PA>
 inline void launch_upward(const PlanDev &pd, int d, int nrhs, int64_t np, cudaStream_t st)
 {
-    if constexpr (sizeof(T) == 4 && R <= 4) {
+    if constexpr (sizeof(T) == 4) {
         constexpr int P = PS * PA * PA;
-        const size_t smem = (size_t)kRunWarps * run_warp_bytes(P, R, nrhs);
-        // within the default 48 KB of dynamic shared memory (all of (3, 5); (4, 7) up to 2
-        // right-hand sides); larger configurations run k_upward
-        if (nrhs <= R && !(pd.flags & 512) && smem <= 48 * 1024) {
-            const int nslot = pd.lev[d - 1].nact;
-            const int grid = (nslot + kRunWarps - 1) / kRunWarps;
-            if (pd.lev[d].utab) {
-                k_upward_runs<R, PS, PA, true><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
-            } else if (pd.lev[d].ucache || (pd.flags & 2048)) {
-                k_upward_runs<R, PS, PA, false><<<grid, 32 * kRunWarps, smem, st>>>(pd, d, nrhs);
-            } else {
-                // geometry on the fly: the staged kernel (one node per lane)
-                const size_t ssmem = (size_t)kUpWarps * kUpStage * P * nrhs * sizeof(float2);
-                k_upward_staged<R, PS, PA, false><<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, ssmem, st>>>(pd, d, nrhs);
+        const bool stored = pd.lev[d].utab || pd.lev[d].ucache || (pd.flags & 2048);
+        if (!(pd.flags & 512)) {
+            if constexpr (R <= 4) {
+                if (nrhs <= R) {
+                    if (stored) {
+                        launch_runs<R, PS, PA>(pd, d, nrhs, 0, nrhs, st);
+                        return;
+                    }
+                    const size_t ssmem = (size_t)kUpWarps * kUpStage * P * nrhs * sizeof(float2);
+                    if (ssmem <= 48 * 1024) {
+                        k_upward_staged<R, PS, PA, false>
+                            <<<grid_for(np, 32 * kUpWarps), 32 * kUpWarps, ssmem, st>>>(pd, d, nrhs);
+                        return;
+                    }
+                }
+            } else if (stored) {
+                // more than 4 right-hand sides: blocks of 4 (the kernels of the 4-wide
+                // translation unit)
+                ifgf_upward_runs_blocks(pd, d, nrhs, st);
+                return;
             }
-            return;
         }
     }
     if (pd.lev[d].utab) k_upward<T, R, PS, PA, true><<<grid_for(np, 128), 128, 0, st>>>(pd, d, nrhs);
@@ -1711,43 +1786,55 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                                int64_t max_entries)
 {
     const PlanDev &pd = p->dev;
+    StageTimer &tm = p->timer;
     JitLists tl, ul;
     ifgf_status s = IFGF_OK;
     // the conjugated near field first (it stores), then per level the adjoint values and,
     // in adaptive trees, the sources whose leaf box lies on that level (they add)
-    if (mode & 1) k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
+    if (mode & 1) {
+        k_near_staged<T, R><<<pd.n_near_tile, kNearThreads, 0, st>>>(pd, nrhs, vs, ws, 1);
+        tm.mark(STAGE_ADJ_EVAL, 1, st);
+    }
     if (mode & 2) {
         for (int d = 3; d <= pd.D && s == IFGF_OK; ++d) {
             const int nact = pd.lev[d].nact;
             if (nact == 0) {
-                if (pd.adaptive || d == pd.D)
+                if (pd.adaptive || d == pd.D) {
                     k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1, d);
+                    tm.mark(STAGE_ADJ_EVAL, 1, st);
+                }
                 continue;
             }
             NvtxRange range("adjoint level (lists built here)", d);
             s = ifgf_jit_targets(p, d, &tl, st);
             if (s != IFGF_OK) break;
+            tm.mark(STAGE_ADJ_LISTS, 0, st);
             {
                 const AdjLists al = {tl.start, tl.list, 0, nullptr, nullptr, 0, 0, nact, 1, 0, nullptr};
                 launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                 if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; break; }
+                tm.mark(STAGE_ADJ_LEVEL, 1, st);
             }
             if (d > 3) {
                 std::vector<int> bounds;
                 s = ifgf_jit_chunks(p, d, max_entries, &bounds);
                 for (size_t c = 0; c + 1 < bounds.size() && s == IFGF_OK; ++c) {
                     s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, st);
+                    tm.mark(STAGE_ADJ_LISTS, 0, st);
                     if (s != IFGF_OK || ul.s1 == ul.s0) continue;
                     const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1, nullptr};
                     launch_adj_level<T, R, PS, PA>(pd, d, nrhs, vs, mode, al, st);
                     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint level launch"; s = IFGF_ECUDA; }
+                    tm.mark(STAGE_ADJ_LEVEL, 1, st);
                     // the lists are freed (and rebuilt) only after the launch has read them
                     if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
                 }
             }
             // the sources of this level's leaves, before level d + 2 reuses the buffer
-            if (pd.adaptive || d == pd.D)
+            if (pd.adaptive || d == pd.D) {
                 k_adj_eval<T, R, PS, PA><<<grid_for(pd.n, 128), 128, 0, st>>>(pd, nrhs, vs, ws, 2, mode & 1, d);
+                tm.mark(STAGE_ADJ_EVAL, 1, st);
+            }
             if (cudaStreamSynchronize(st) != cudaSuccess) { p->last_error = "adjoint level"; s = IFGF_ECUDA; }
         }
     }
@@ -1765,7 +1852,9 @@ ifgf_status run_adjoint_jit(ifgf_plan *p, int nrhs, const void *in_user, void *o
     const PlanDev &pd = p->dev;
     const int64_t tot = (int64_t)pd.n * nrhs;
     const int64_t max_entries = (p->flags & 64) ? 4096 : ((int64_t)1 << 28);
+    p->timer.mark(-1, 0, st);
     k_permute_in<T><<<grid_for(tot, 256), 256, 0, st>>>(in_user, p->sig_sorted, pd.perm, pd.n, nrhs);
+    p->timer.mark(STAGE_PERMUTE_IN, 1, st);
     constexpr int RB = sizeof(T) == 8 ? 4 : 8;
     ifgf_status s;
     if (pd.Ps == 3 && pd.Pang == 5) {
@@ -1783,6 +1872,7 @@ ifgf_status run_adjoint_jit(ifgf_plan *p, int nrhs, const void *in_user, void *o
         return IFGF_EINVAL;
     if (s != IFGF_OK) return s;
     k_permute_out<T><<<grid_for(tot, 256), 256, 0, st>>>(p->u_sorted, out_user, pd.perm, pd.n, nrhs);
+    p->timer.mark(STAGE_PERMUTE_OUT, 1, st);
     if (cudaGetLastError() != cudaSuccess) { p->last_error = "permute launch"; return IFGF_ECUDA; }
     return IFGF_OK;
 }

@@ -147,11 +147,11 @@ struct PlanDev {
 // Per-stage CUDA-event timing of one call (enabled by ifgf_plan_set_profiling).
 enum IfgfStage {
     STAGE_PERMUTE_IN = 0, STAGE_LEAF, STAGE_UPWARD, STAGE_EVAL, STAGE_PERMUTE_OUT,
-    STAGE_ADJ_LEVEL, STAGE_ADJ_EVAL, STAGE_COUNT
+    STAGE_ADJ_LEVEL, STAGE_ADJ_EVAL, STAGE_ADJ_LISTS, STAGE_COUNT
 };
 
 struct StageTimer {
-    static constexpr int kMax = 512;
+    static constexpr int kMax = 2048;  // marks per evaluation (an adjoint built just in time marks per list range)
     bool on = false;
     int n = 0;
     cudaEvent_t ev[kMax] = {};
@@ -204,7 +204,7 @@ struct ifgf_plan {
     int leaf_max = 0;          // adaptive tree: boxes of level >= 3 with at most leaf_max points are leaves
     int device = 0;            // the CUDA device current at ifgf_plan_create (owns every buffer)
     double timeout_s = 0;      // host-side wait limit of an evaluation (0: none)
-    size_t value_budget = 0;   // bytes for cone values (0: 60% of free memory at plan time)
+    size_t value_budget = 0;   // bytes for cone values (0: 85% of the free memory less buffers and reserve)
     bool pingpong = false;     // two alternating level buffers instead of one per level
     size_t cache_bytes = 0;    // evaluation caches (0: none)
     int rhs_chunk = 1;         // right-hand sides per internal pass

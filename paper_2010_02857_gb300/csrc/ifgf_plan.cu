@@ -1246,8 +1246,10 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
 
     // Upward tables: the geometry of the step d -> d-1 depends only on (parent cone id,
     // child octant, node).  Tabulate it where the table has at most half as many
-    // entries as the level has upward evaluations per apply and takes at most half of
-    // the memory left after the value buffers (finest levels first).
+    // entries as the level has upward evaluations per apply and fits the memory left
+    // after the value buffers (finest levels first): all of it but the reserve in
+    // two-buffer plans, whose adjoint builds its transpose lists level by level inside
+    // the reserve, and half of it otherwise.
     const size_t entry_bytes = ifgf_uptable_entry_bytes(p->precision, Ps, Pang);
     for (int d = D; d >= 4; --d) {
         LevelDev &L = pd.lev[d];
@@ -1276,7 +1278,7 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         // keep room for the adjoint's cone values, allocated on the first adjoint call
         // (as large as the forward values of a plan that keeps every level)
         const size_t reserve = std::min(kReserveBytes, totalb / 10) + (p->pingpong ? 0 : value_bytes);
-        const size_t room = freeb > reserve ? (freeb - reserve) / 2 : 0;
+        const size_t room = freeb > reserve ? (p->pingpong ? freeb - reserve : (freeb - reserve) / 2) : 0;
         if ((p->flags & 2) || rows == 0 || 2 * entries > p->lh[d].upward_evals || bytes > room) continue;
         DALLOC(uids, int, rows);
         Scratch dummy;

@@ -302,6 +302,18 @@ def test_adjoint_with_just_in_time_lists(pkg, torch_cuda, precision, tol):
     u = g.apply(torch.from_numpy(s).cuda()).cpu().numpy()
     lhs, rhs = np.vdot(v, u), np.vdot(w, s)
     assert abs(lhs - rhs) / abs(lhs) < (1e-12 if precision == "fp64" else 1e-5)
+    # profiled: the list building and the adjoint launches of every range are timed, and
+    # the result does not change
+    g.set_profiling(True)
+    w2 = g.apply_adjoint(torch.from_numpy(v).cuda()).cpu().numpy()
+    tm = g.timings()
+    g.set_profiling(False)
+    assert np.array_equal(w2, w)
+    st = tm["stages"]
+    assert tm["calls"] == 1
+    assert st["adj_level"]["launches"] > 4 and st["adj_level"]["ms"] > 0  # many ranges (bit 6)
+    assert st["adj_lists"]["ms"] > 0 and st["adj_eval"]["launches"] >= 2  # two chunks' near fields
+    assert st["permute_in"]["launches"] == 2 and st["permute_out"]["launches"] == 2
     assert g.check() == 0
 
 
@@ -701,7 +713,8 @@ def test_batched_every_rhs_elementwise_vs_oracle(pkg, torch_cuda, nrhs, precisio
 
 
 @pytest.mark.parametrize("nrhs,flags", [(1, 0), (2, 0), (3, 0), (4, 0), (4, 2), (4, 8 | 32), (4, 1024),
-                                        (1, 2 | 1024), (4, 2 | 2048), (3, 8 | 32 | 2048)])
+                                        (1, 2 | 1024), (4, 2 | 2048), (3, 8 | 32 | 2048), (6, 0), (8, 0),
+                                        (7, 2 | 1024)])
 def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
     # the FP32 upward step in runs of nodes that share a child cone (default) and the
     # kernel with one thread per parent node reading the values from L1 (flags bit 9) sum
@@ -709,7 +722,8 @@ def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
     # associates each 75-term contraction differently (weight products), so the cone
     # values agree to FP32 rounding carried over the levels (1e-5, a tenth of the mixed
     # path's element-wise bound); tabled (default) and on-the-fly geometry (bit 1);
-    # two-level buffers without caches (bits 3 and 5); at most 8 runs per pass (bit 10)
+    # two-level buffers without caches (bits 3 and 5); runs taken by 8 lanes (bit 10);
+    # more than 4 right-hand sides: the run kernel on blocks of 4 (6 = 4 + 2, 7 = 4 + 3)
     torch = torch_cuda
     wl, pts, _ = _make((6000, 6, 6, 1, 2))
     sig = wi.complex_normal(200 + nrhs, (nrhs, wl.n))
@@ -725,6 +739,29 @@ def test_run_fp32_upward_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
             assert maxrel(va, vb) < 1e-5, (d, maxrel(va, vb))
     o = oracle.Plan(pts, wl.kappa, 6, 3, 5, 1, 2)
     uo = o.apply(sig)
+    for r in range(nrhs):
+        assert maxrel(ua[r], uo[r]) < ELEM_MIXED, (r, maxrel(ua[r], uo[r]))
+    assert a.check() == 0 and b.check() == 0
+
+
+@pytest.mark.parametrize("nrhs,flags", [(1, 0), (1, 2), (1, 1024), (1, 2 | 2048), (2, 0), (4, 0), (6, 1024)])
+def test_run_fp32_upward_order_4_7_matches_l1_kernel(pkg, torch_cuda, nrhs, flags):
+    # (P_s, P_ang) = (4, 7): a child step of 196 nodes has more than 32 runs, so lanes take
+    # several runs each; 2 and 4 right-hand sides take 53 KB of shared memory per CTA (above
+    # the default limit); 6 run as blocks of 4 + 2; same comparison as at (3, 5)
+    torch = torch_cuda
+    wl, pts, _ = _make((4000, 4, 5, 1, 2))
+    sig = wi.complex_normal(210 + nrhs, (nrhs, wl.n))
+    kw = dict(max_nrhs=nrhs, precision="mixed")
+    a = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 4, 7, 1, 2, flags=flags, **kw)
+    b = pkg.Plan(torch.from_numpy(pts).cuda(), wl.kappa, 5, 4, 7, 1, 2, flags=flags | 512, **kw)
+    s = torch.from_numpy(sig).cuda().to(torch.complex64)
+    ua, ub = a.apply(s).cpu().numpy(), b.apply(s).cpu().numpy()
+    assert maxrel(ua, ub) < 1e-5, maxrel(ua, ub)
+    for d in range(3, 6):
+        va, vb = a.values(d, nrhs), b.values(d, nrhs)
+        assert maxrel(va, vb) < 1e-5, (d, maxrel(va, vb))
+    uo = oracle.Plan(pts, wl.kappa, 5, 4, 7, 1, 2).apply(sig)
     for r in range(nrhs):
         assert maxrel(ua[r], uo[r]) < ELEM_MIXED, (r, maxrel(ua[r], uo[r]))
     assert a.check() == 0 and b.check() == 0
