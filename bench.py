@@ -69,12 +69,17 @@ def adjoint_flops_per_eval(ps: int, pa: int) -> int:
 
 NUM_SMS = 152
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of
-# the kernel, keyed by (workload, precision).  Each entry records the SHA-256 of the
-# kernel source it was captured on; when the source has changed since, the bench
-# reports null instead of a stale figure.
+# DRAM bytes (read + write) per launch of the dominant kernels, from an ncu capture of
+# them, keyed by (workload, precision): the mean over the launches whose time the
+# roofline's "achieved" averages (for FP32 plans the upward stage: k_upward_runs on the
+# tabled levels and k_upward_staged on the level computed on the fly, one chunk of
+# right-hand sides).  Each entry records the SHA-256 of the kernel source it was captured
+# on; when the source has changed since, the bench reports null instead of a stale figure.
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_02857_gb300", "csrc", "ifgf_apply_impl.cuh")
-TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_BYTES_PER_LAUNCH = {
+    # 6 upward launches of one 4-RHS chunk: 963.9 GB read + 377.3 GB written
+    ("sphere_256lambda", "mixed"): {"bytes": 223.5e9, "sha": "a9e61ba4ea9117e9"},
+}
 
 
 def _source_sha(path: str) -> str:
@@ -462,7 +467,7 @@ def main():
                            "l2": "flushed between steps (256 MB write)", "launch": "CUDA graph replay",
                            "parallelism": f"rhs-sharded x{world}", "batch_nrhs": batch},
                 "t_plan_ms": t_plan * 1e3, "tiles": tiles,
-                "stage_ms": {k: v["ms"] / calls for k, v in st.items() if v["launches"]},
+                "stage_ms": {k: v["ms"] / calls for k, v in st.items() if v["launches"] or v["ms"]},
                 "e2e": {"value": world * n * n * nrhs / e2e_s, "unit": UNIT,
                         "h2d_bytes_per_step": n * nrhs * eb, "d2h_bytes_per_step": n * nrhs * eb,
                         "ms_per_step": e2e_s * 1e3},

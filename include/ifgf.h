@@ -115,7 +115,10 @@ typedef struct {
                        (testing: every lane then takes several runs of a child step);
                        bit 11: FP32 upward steps whose geometry is computed on the fly use
                        the run kernel too (by default they use one node per lane, which
-                       keeps the FP64 geometry work dense; testing and measurement). */
+                       keeps the FP64 geometry work dense; testing and measurement);
+                       bit 12: plan creation marks the cones of relevance rule (ii) node by
+                       node for every parent slot, instead of once per distinct parent cone
+                       id and child octant (testing: both mark the same cones). */
     long long value_budget_bytes; /* device bytes for cone values; 0 = 85% of the free
                        memory at plan time less the sorted density and field buffers and
                        a reserve of min(24 GB, a tenth of the device) for the adjoint's

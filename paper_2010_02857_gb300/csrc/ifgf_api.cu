@@ -594,10 +594,11 @@ extern "C" ifgf_status ifgf_plan_stats(const ifgf_plan *plan, char *buf, size_t 
         const LevelDev &L = plan->dev.lev[d];
         snprintf(tmp, sizeof tmp,
                  "%s{\"d\": %d, \"nbox\": %d, \"ncous\": %lld, \"nact\": %d, \"ns\": %d, \"nc\": %d, "
-                 "\"cousin_evals\": %lld, \"upward_evals\": %lld, \"table_rows\": %lld, \"union_rows\": %lld}",
+                 "\"cousin_evals\": %lld, \"upward_evals\": %lld, \"table_rows\": %lld, \"union_rows\": %lld, "
+                 "\"act_sets\": %d}",
                  d > 1 ? ", " : "", d, L.nbox, (long long)h.ncous, d >= 3 ? L.nact : 0, d >= 3 ? L.ns : 0,
                  d >= 3 ? L.nc : 0, (long long)h.cousin_evals, (long long)h.upward_evals, (long long)h.table_rows,
-                 (long long)h.union_rows);
+                 (long long)h.union_rows, h.act_sets);
         s += tmp;
     }
     s += "]}";

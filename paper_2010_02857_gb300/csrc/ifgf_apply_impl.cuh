@@ -191,11 +191,13 @@ __device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 
     const float dx = (p.hx - oh.x) + (p.lx - ol.x);
     const float dy = (p.hy - oh.y) + (p.ly - ol.y);
     const float dz = (p.hz - oh.z) + (p.lz - ol.z);
-    const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float a = __fdividef((float)kInv4Pi, r);
+    // r^2 > 0 (the self term is skipped by index); 1/r from the SFU's reciprocal square root
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float y = rsqrtf(r2);
+    const float a = (float)kInv4Pi * y;
     if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
     float c, s;
-    expi_f32(kf * r, c, s);
+    expi_f32(kf * (r2 * y), c, s);
     return {a * c, a * s};
 }
 
@@ -212,10 +214,13 @@ __device__ __forceinline__ cpx<float> green_near32(const Rel32 &p, const float4 
 __device__ __forceinline__ cpx<float> leaf_factor32(float Rf, float dx, float dy, float dz, float kf, const float4 &o)
 {
     const float num = fmaf(-2.0f * Rf, fmaf(dx, o.x, fmaf(dy, o.y, dz * o.z)), o.w);
-    const float r1 = sqrtf(fmaxf(fmaf(Rf, Rf, num), 0.f));
-    const float a = __fdividef(Rf, r1);
+    // |q - x_j|^2 and its reciprocal square root (the SFU's, 2 ulp): the amplitude R / r1
+    // and r1 itself from one special-function operation
+    const float r2 = fmaxf(fmaf(Rf, Rf, num), 0.f);
+    const float y = rsqrtf(r2);
+    const float a = Rf * y;
     if (kf == 0.f) return {a, 0.f};  // Laplace kernel: no phase
-    const float ph = __fdividef(kf * num, r1 + Rf);
+    const float ph = __fdividef(kf * num, fmaf(r2, y, Rf));
     float c, s;
     expi_f32(ph, c, s);
     return {a * c, a * s};
@@ -234,8 +239,9 @@ __device__ __forceinline__ cpx<T> leaf_factor(const PlanDev &pd, double R, const
         expi(pd.kappa * (r2 * y - R), c, s);
         return {a * c, a * s};
     } else {
-        // the quotients need FP32 relative accuracy only (r1 + R and r1 lie far inside
-        // the range where the fast division is accurate to 2 ulp)
+        // the quotient and the reciprocal square root need FP32 relative accuracy only
+        // (their arguments lie far inside the range where the fast forms are accurate to
+        // 2 ulp)
         return leaf_factor32((float)R, (float)dir[0], (float)dir[1], (float)dir[2], (float)pd.kappa, pd.leaf_off[j]);
     }
 }
@@ -331,12 +337,17 @@ __global__ void __launch_bounds__(128) k_leaf(PlanDev pd, int d, int nrhs, const
     double q[3], dir[3];
     double R0 = node_pos(L, PS, PA, L.act_cone[slot], node, c[0], c[1], c[2], q, dir);
     const int j0 = L.start[b], j1 = L.end[b];
+    // FP32 factors: the node's radius, direction and kappa converted once, not per source
+    const float Rf = (float)R0, dxf = (float)dir[0], dyf = (float)dir[1], dzf = (float)dir[2];
+    const float kf = (float)pd.kappa;
     for (int r0 = 0; r0 < nrhs; r0 += R) {
         cpx<T> acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = {T(0), T(0)};
         for (int j = j0; j < j1; ++j) {
-            cpx<T> g = leaf_factor<T>(pd, R0, q, dir, j);
+            cpx<T> g;
+            if constexpr (sizeof(T) == 8) g = leaf_factor<T>(pd, R0, q, dir, j);
+            else g = leaf_factor32(Rf, dxf, dyf, dzf, kf, pd.leaf_off[j]);
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 if (R == 1 || r0 + r < nrhs) {
@@ -1788,6 +1799,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
     const PlanDev &pd = p->dev;
     StageTimer &tm = p->timer;
     JitLists tl, ul;
+    JitWork work;  // reused by every list build of this call
     ifgf_status s = IFGF_OK;
     // the conjugated near field first (it stores), then per level the adjoint values and,
     // in adaptive trees, the sources whose leaf box lies on that level (they add)
@@ -1806,7 +1818,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                 continue;
             }
             NvtxRange range("adjoint level (lists built here)", d);
-            s = ifgf_jit_targets(p, d, &tl, st);
+            s = ifgf_jit_targets(p, d, &tl, &work, st);
             if (s != IFGF_OK) break;
             tm.mark(STAGE_ADJ_LISTS, 0, st);
             {
@@ -1819,7 +1831,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
                 std::vector<int> bounds;
                 s = ifgf_jit_chunks(p, d, max_entries, &bounds);
                 for (size_t c = 0; c + 1 < bounds.size() && s == IFGF_OK; ++c) {
-                    s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, st);
+                    s = ifgf_jit_upward(p, d, bounds[c], bounds[c + 1], &ul, &work, st);
                     tm.mark(STAGE_ADJ_LISTS, 0, st);
                     if (s != IFGF_OK || ul.s1 == ul.s0) continue;
                     const AdjLists al = {nullptr, nullptr, 0, ul.start, ul.list, ul.s0, ul.s0, ul.s1, 2, 1, nullptr};
@@ -1840,6 +1852,7 @@ ifgf_status launch_adjoint_jit(ifgf_plan *p, int nrhs, const void *vs, void *ws,
     }
     ifgf_jit_release(&tl);
     ifgf_jit_release(&ul);
+    work.release();
     if (s != IFGF_OK) return s;
     if (cudaGetLastError() != cudaSuccess) { p->last_error = "adjoint launch"; return IFGF_ECUDA; }
     return IFGF_OK;

@@ -191,6 +191,7 @@ struct LevelHost {
     int64_t cousin_evals = 0, upward_evals = 0;
     int64_t words = 0;
     int64_t table_rows = 0;   // rows of the upward table of step d -> d-1 (0: none)
+    int act_sets = 0;         // rule (ii) of level d marked per distinct parent cone id (1) or per node (0)
     int64_t union_rows = 0;   // distinct relevant cone ids of level d-1 (the rows a table would have)
 };
 
@@ -296,19 +297,55 @@ struct TEntry32 {
 // lists do not stay resident (two-buffer plans): CSR over the level-d slots [s0, s1)
 // (start[s - s0] .. start[s - s0 + 1] index list).  Target lists hold point indices;
 // upward lists hold parent slot * P + node, read as unsigned.
+// A device buffer that only grows: the list builds of one adjoint call reuse it, so that
+// hundreds of ranges do not each allocate and free gigabytes.
+struct GrowBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        if (ptr && bytes <= cap) return true;
+        release();
+        if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+            return false;
+        }
+        cap = bytes;
+        return true;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+};
+
 struct JitLists {
     int s0 = 0, s1 = 0;
     int *start = nullptr;
     int *list = nullptr;
-    void *mem = nullptr;   // owns start and list
+    GrowBuf mem;   // holds start and list
+};
+
+// scratch of the list builds of one adjoint call (counts, offsets, unsorted and sorted
+// keys, values, sort and scan temporaries)
+struct JitWork {
+    GrowBuf cnt, off, keys, vals, sorted, sort_tmp, scan_tmp;
+    void release()
+    {
+        cnt.release(); off.release(); keys.release(); vals.release();
+        sorted.release(); sort_tmp.release(); scan_tmp.release();
+    }
 };
 
 // plan.cu
 ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st);
 // cousin-target transpose lists of level d (all slots)
-ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, cudaStream_t st);
+ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, JitWork *w, cudaStream_t st);
 // upward transpose lists of level d for the parent boxes [b0, b1) of level d-1
-ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, cudaStream_t st);
+ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, JitWork *w, cudaStream_t st);
 void ifgf_jit_release(JitLists *l);
 // apply_f64.cu / apply_f32.cu: the adjoint with just-in-time lists (one RHS chunk)
 ifgf_status ifgf_run_adjoint_jit_f64(ifgf_plan *p, int nrhs, const void *in, void *out, int mode, cudaStream_t st);

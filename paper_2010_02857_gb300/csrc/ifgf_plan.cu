@@ -464,6 +464,99 @@ __global__ void k_activate_parent(PlanDev pd, int d, uint64_t *bits)
     }
 }
 
+// Rule (ii) by parent cone id.  The cell of a parent interpolation point seen from a child
+// centre depends only on (parent cone id, child octant, node): the point relative to the
+// child centre is R dir - delta (node_rel).  So the set of child cones that one parent cone
+// id marks in the child of one octant is the same for every box; it is computed once per
+// distinct parent cone id of the level (the union of the boxes' relevant cones) and octant,
+// and every (parent slot, child) pair then sets those bits.  The sets are the ones the
+// per-node kernel marks, bit for bit.  At most kConeSet cells are kept per (id, octant); a
+// larger set is stored as count -1 and its pairs take the per-node path.
+constexpr int kConeSet = 4;
+
+// one warp per (union row, octant): count, then the distinct cells in order of first node
+__global__ void k_cone_sets(PlanDev pd, int d, const int *uids, int rows, int *sets)
+{
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)rows * 8) return;  // the whole warp
+    const int row = (int)(wid >> 3), oct = (int)(wid & 7);
+    const double hh = L.H * 0.5;
+    int found[kConeSet];
+#pragma unroll
+    for (int i = 0; i < kConeSet; ++i) found[i] = -1;
+    int n = 0;  // distinct cells so far (the same in every lane)
+    bool over = false;
+    for (int n0 = 0; n0 < pd.P; n0 += 32) {
+        const int node = n0 + lane;
+        int cone = -1;
+        if (node < pd.P) {
+            double v[3];
+            node_rel(Lp, pd.Ps, pd.Pang, uids[row], node, hh, oct, v, nullptr);
+            cone = cone_of_mixed(L, v[0], v[1], v[2]).cone;
+        }
+        unsigned pending = __ballot_sync(0xffffffffu, cone >= 0);
+        while (pending) {
+            const int c = __shfl_sync(0xffffffffu, cone, __ffs(pending) - 1);
+            pending &= ~__ballot_sync(0xffffffffu, cone == c);
+            bool known = false;
+#pragma unroll
+            for (int i = 0; i < kConeSet; ++i) known = known || (i < n && found[i] == c);
+            if (!known) {
+                if (n < kConeSet) {
+#pragma unroll
+                    for (int i = 0; i < kConeSet; ++i)
+                        if (i == n) found[i] = c;
+                    ++n;
+                } else {
+                    over = true;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        int *out = sets + (size_t)wid * (kConeSet + 1);
+        out[0] = over ? -1 : n;
+#pragma unroll
+        for (int i = 0; i < kConeSet; ++i) out[1 + i] = found[i];
+    }
+}
+
+// one thread per (parent slot, child position): the child's bits of the slot's cone id
+__global__ void k_activate_parent_sets(PlanDev pd, int d, const uint64_t *ubits, const int *urank, const int *sets,
+                                       uint64_t *bits)
+{
+    const LevelDev &L = pd.lev[d];
+    const LevelDev &Lp = pd.lev[d - 1];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)Lp.nact * 8) return;
+    const int slot = (int)(t >> 3), kk = (int)(t & 7);
+    const int j = Lp.act_box[slot];
+    const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
+    if (kk >= nch) return;
+    const int k = k0 + kk, oct = (int)(L.key[k] & 7u);
+    const int pcone = Lp.act_cone[slot];
+    const int row = table_row(ubits, urank, pcone);
+    if (row < 0) {  // every relevant cone id is in the union
+        atomicAdd(pd.err, 1);
+        return;
+    }
+    const int *set = sets + ((size_t)row * 8 + oct) * (kConeSet + 1);
+    const int cnt = set[0];
+    if (cnt >= 0) {
+        for (int i = 0; i < cnt; ++i) set_bit(bits, L.words, k, set[1 + i]);
+        return;
+    }
+    const double hh = L.H * 0.5;
+    for (int node = 0; node < pd.P; ++node) {
+        double v[3];
+        node_rel(Lp, pd.Ps, pd.Pang, pcone, node, hh, oct, v, nullptr);
+        set_bit(bits, L.words, k, cone_of_mixed(L, v[0], v[1], v[2]).cone);
+    }
+}
+
 // union over boxes of a level's relevant-cone bitmaps
 __global__ void k_union_bits(const uint64_t *bits, int nbox, int words, uint64_t *ubits)
 {
@@ -1112,9 +1205,43 @@ ifgf_status ifgf_build_plan(ifgf_plan *p, const double *points, cudaStream_t st)
         k_activate_cousins<<<nblocks(n), kThreads, 0, st>>>(pd, d, bits);
         CK(cudaGetLastError());
         if (d >= 4) {
-            int64_t nt = (int64_t)pd.lev[d - 1].nact * P;
-            k_activate_parent<<<nblocks(nt), kThreads, 0, st>>>(pd, d, bits);
+            // rule (ii): per distinct parent cone id where they are few against the parent
+            // slots (each slot has up to 8 children of P nodes), else per node (flags bit
+            // 12 forces the per-node kernel; the marked bits are the same)
+            const LevelDev &Lp = pd.lev[d - 1];
+            const int64_t pw = Lp.words;
+            Scratch ub, ucnt, ur;
+            if (!ub.alloc((size_t)pw * 8) || !ucnt.alloc((size_t)(pw + 1) * 4) || !ur.alloc((size_t)(pw + 1) * 4))
+                return IFGF_ENOMEM;
+            CK(cudaMemsetAsync(ub.ptr, 0, (size_t)pw * 8, st));
+            CK(cudaMemsetAsync(ucnt.ptr, 0, (size_t)(pw + 1) * 4, st));
+            const int64_t tot = (int64_t)Lp.nbox * Lp.words;
+            k_union_bits<<<nblocks(tot), kThreads, 0, st>>>(Lp.bits, Lp.nbox, Lp.words, (uint64_t *)ub.ptr);
+            k_popc<<<nblocks(pw), kThreads, 0, st>>>((const uint64_t *)ub.ptr, pw, (int *)ucnt.ptr);
             CK(cudaGetLastError());
+            ifgf_status su = cub_exclusive_sum(p, (int *)ucnt.ptr, (int *)ur.ptr, pw + 1, st);
+            if (su != IFGF_OK) return su;
+            int rows = 0;
+            CK(cudaMemcpy(&rows, (int *)ur.ptr + pw, sizeof(int), cudaMemcpyDeviceToHost));
+            if (!(p->flags & 4096) && rows > 0 && 2 * (int64_t)rows <= Lp.nact) {
+                Scratch uid, dummy, sets;
+                if (!uid.alloc((size_t)rows * 4) || !dummy.alloc((size_t)rows * 4) ||
+                    !sets.alloc((size_t)rows * 8 * (kConeSet + 1) * 4))
+                    return IFGF_ENOMEM;
+                k_expand<<<nblocks(pw), kThreads, 0, st>>>((const uint64_t *)ub.ptr, (const int *)ur.ptr, pw, (int)pw,
+                                                          (int *)uid.ptr, (int *)dummy.ptr);
+                k_cone_sets<<<nblocks((int64_t)rows * 8 * 32), kThreads, 0, st>>>(pd, d, (const int *)uid.ptr, rows,
+                                                                                   (int *)sets.ptr);
+                k_activate_parent_sets<<<nblocks((int64_t)Lp.nact * 8), kThreads, 0, st>>>(
+                    pd, d, (const uint64_t *)ub.ptr, (const int *)ur.ptr, (const int *)sets.ptr, bits);
+                CK(cudaGetLastError());
+                CK(cudaStreamSynchronize(st));
+                p->lh[d].act_sets = 1;
+            } else {
+                int64_t nt = (int64_t)Lp.nact * P;
+                k_activate_parent<<<nblocks(nt), kThreads, 0, st>>>(pd, d, bits);
+                CK(cudaGetLastError());
+            }
         }
         Scratch cnt;
         if (!cnt.alloc((size_t)(nw + 1) * 4)) return IFGF_ENOMEM;
@@ -1509,34 +1636,43 @@ namespace {
 
 // stable sort of (key, value) pairs by key into list, and CSR starts over nslot keys
 ifgf_status sort_into_csr(ifgf_plan *p, int *keys, int *vals, int64_t m, int nslot, int *start, int *list,
-                          cudaStream_t st)
+                          JitWork *w, cudaStream_t st)
 {
-    Scratch kb;
-    if (!kb.alloc((size_t)m * 4)) { p->last_error = "adjoint list sort"; return IFGF_ENOMEM; }
+    if (!w->sorted.ensure((size_t)m * 4)) { p->last_error = "adjoint list sort"; return IFGF_ENOMEM; }
     int end_bit = 1;
     while (end_bit < 31 && (1 << end_bit) <= nslot) ++end_bit;
     size_t bytes = 0;
-    CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
-    Scratch tmp;
-    if (!tmp.alloc(bytes)) { p->last_error = "adjoint list sort temp"; return IFGF_ENOMEM; }
-    CK(cub::DeviceRadixSort::SortPairs(tmp.ptr, bytes, keys, (int *)kb.ptr, vals, list, m, 0, end_bit, st));
-    k_csr_from_sorted<<<nblocks(nslot + 1), kThreads, 0, st>>>((int *)kb.ptr, m, nslot, start);
+    CK(cub::DeviceRadixSort::SortPairs(nullptr, bytes, keys, (int *)w->sorted.ptr, vals, list, m, 0, end_bit, st));
+    if (!w->sort_tmp.ensure(bytes)) { p->last_error = "adjoint list sort temp"; return IFGF_ENOMEM; }
+    CK(cub::DeviceRadixSort::SortPairs(w->sort_tmp.ptr, bytes, keys, (int *)w->sorted.ptr, vals, list, m, 0, end_bit,
+                                       st));
+    k_csr_from_sorted<<<nblocks(nslot + 1), kThreads, 0, st>>>((int *)w->sorted.ptr, m, nslot, start);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     return IFGF_OK;
 }
 
-// one allocation for start [nslot + 1] and list [m]
+// exclusive prefix sum with the scan temporary of the workspace
+ifgf_status jit_exclusive_sum(ifgf_plan *p, const int *in, int *out, int64_t n, JitWork *w, cudaStream_t st)
+{
+    size_t bytes = 0;
+    CK(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, st));
+    if (!w->scan_tmp.ensure(bytes)) { p->last_error = "scan scratch"; return IFGF_ENOMEM; }
+    CK(cub::DeviceScan::ExclusiveSum(w->scan_tmp.ptr, bytes, in, out, n, st));
+    CK(cudaStreamSynchronize(st));
+    return IFGF_OK;
+}
+
+// start [nslot + 1] and list [m] in the list's own (grow-only) buffer
 ifgf_status jit_alloc(ifgf_plan *p, JitLists *out, int nslot, int64_t m)
 {
     const size_t sb = ((size_t)(nslot + 1) * 4 + 255) / 256 * 256;
-    if (cudaMalloc(&out->mem, sb + (size_t)m * 4 + 16) != cudaSuccess) {
-        out->mem = nullptr;
+    if (!out->mem.ensure(sb + (size_t)m * 4 + 16)) {
         p->last_error = "just-in-time adjoint lists";
         return IFGF_ENOMEM;
     }
-    out->start = (int *)out->mem;
-    out->list = (int *)((char *)out->mem + sb);
+    out->start = (int *)out->mem.ptr;
+    out->list = (int *)((char *)out->mem.ptr + sb);
     return IFGF_OK;
 }
 
@@ -1544,34 +1680,32 @@ ifgf_status jit_alloc(ifgf_plan *p, JitLists *out, int nslot, int64_t m)
 
 void ifgf_jit_release(JitLists *l)
 {
-    if (l->mem) cudaFree(l->mem);
+    l->mem.release();
     *l = JitLists();
 }
 
-ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, cudaStream_t st)
+ifgf_status ifgf_jit_targets(ifgf_plan *p, int d, JitLists *out, JitWork *w, cudaStream_t st)
 {
-    ifgf_jit_release(out);
     PlanDev &pd = p->dev;
     const LevelDev &L = pd.lev[d];
     const int n = (int)p->n;
-    Scratch cnt, off;
-    if (!cnt.alloc((size_t)(n + 1) * 4) || !off.alloc((size_t)(n + 1) * 4)) return IFGF_ENOMEM;
-    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(n + 1) * 4, st));
-    k_point_cousin_count<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)cnt.ptr);
+    if (!w->cnt.ensure((size_t)(n + 1) * 4) || !w->off.ensure((size_t)(n + 1) * 4)) return IFGF_ENOMEM;
+    int *cnt = (int *)w->cnt.ptr, *off = (int *)w->off.ptr;
+    CK(cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * 4, st));
+    k_point_cousin_count<<<nblocks(n), kThreads, 0, st>>>(pd, d, cnt);
     CK(cudaGetLastError());
-    ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, n + 1, st);
+    ifgf_status s = jit_exclusive_sum(p, cnt, off, n + 1, w, st);
     if (s != IFGF_OK) return s;
     int m = 0;
-    CK(cudaMemcpy(&m, (int *)off.ptr + n, sizeof(int), cudaMemcpyDeviceToHost));
-    Scratch keys, vals;
-    if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
-    k_emit_tlist<<<nblocks(n), kThreads, 0, st>>>(pd, d, (int *)off.ptr, (int *)keys.ptr, (int *)vals.ptr);
+    CK(cudaMemcpy(&m, off + n, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!w->keys.ensure((size_t)m * 4) || !w->vals.ensure((size_t)m * 4)) return IFGF_ENOMEM;
+    k_emit_tlist<<<nblocks(n), kThreads, 0, st>>>(pd, d, off, (int *)w->keys.ptr, (int *)w->vals.ptr);
     CK(cudaGetLastError());
     s = jit_alloc(p, out, L.nact, m);
     if (s != IFGF_OK) return s;
     out->s0 = 0;
     out->s1 = L.nact;
-    return sort_into_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, L.nact, out->start, out->list, st);
+    return sort_into_csr(p, (int *)w->keys.ptr, (int *)w->vals.ptr, m, L.nact, out->start, out->list, w, st);
 }
 
 ifgf_status ifgf_jit_chunks(ifgf_plan *p, int d, int64_t max_entries, std::vector<int> *bounds)
@@ -1596,9 +1730,8 @@ ifgf_status ifgf_jit_chunks(ifgf_plan *p, int d, int64_t max_entries, std::vecto
     return IFGF_OK;
 }
 
-ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, cudaStream_t st)
+ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, JitWork *w, cudaStream_t st)
 {
-    ifgf_jit_release(out);
     PlanDev &pd = p->dev;
     const LevelDev &L = pd.lev[d];
     const LevelDev &Lp = pd.lev[d - 1];
@@ -1610,21 +1743,20 @@ ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, 
     CK(cudaMemcpy(&sl[0], L.act_start + cb[0], 4, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&sl[1], L.act_start + cb[1], 4, cudaMemcpyDeviceToHost));
     const int nq = q[1] - q[0], ns = sl[1] - sl[0];
-    Scratch cnt, off;
-    if (!cnt.alloc((size_t)(nq + 1) * 4) || !off.alloc((size_t)(nq + 1) * 4)) return IFGF_ENOMEM;
-    CK(cudaMemsetAsync(cnt.ptr, 0, (size_t)(nq + 1) * 4, st));
-    if (nq > 0) k_parent_slot_count_range<<<nblocks(nq), kThreads, 0, st>>>(pd, d, q[0], q[1], (int *)cnt.ptr);
+    if (!w->cnt.ensure((size_t)(nq + 1) * 4) || !w->off.ensure((size_t)(nq + 1) * 4)) return IFGF_ENOMEM;
+    int *cnt = (int *)w->cnt.ptr, *off = (int *)w->off.ptr;
+    CK(cudaMemsetAsync(cnt, 0, (size_t)(nq + 1) * 4, st));
+    if (nq > 0) k_parent_slot_count_range<<<nblocks(nq), kThreads, 0, st>>>(pd, d, q[0], q[1], cnt);
     CK(cudaGetLastError());
-    ifgf_status s = cub_exclusive_sum(p, (int *)cnt.ptr, (int *)off.ptr, nq + 1, st);
+    ifgf_status s = jit_exclusive_sum(p, cnt, off, nq + 1, w, st);
     if (s != IFGF_OK) return s;
     int m = 0;
-    CK(cudaMemcpy(&m, (int *)off.ptr + nq, sizeof(int), cudaMemcpyDeviceToHost));
-    Scratch keys, vals;
-    if (!keys.alloc((size_t)m * 4) || !vals.alloc((size_t)m * 4)) return IFGF_ENOMEM;
+    CK(cudaMemcpy(&m, off + nq, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!w->keys.ensure((size_t)m * 4) || !w->vals.ensure((size_t)m * 4)) return IFGF_ENOMEM;
     const int64_t nt = (int64_t)nq * pd.P;
     if (nt > 0)
-        k_emit_ulist_range<<<nblocks(nt), kThreads, 0, st>>>(pd, d, q[0], q[1], sl[0], (int *)off.ptr,
-                                                             (int *)keys.ptr, (int *)vals.ptr);
+        k_emit_ulist_range<<<nblocks(nt), kThreads, 0, st>>>(pd, d, q[0], q[1], sl[0], off, (int *)w->keys.ptr,
+                                                             (int *)w->vals.ptr);
     CK(cudaGetLastError());
     s = jit_alloc(p, out, ns, m);
     if (s != IFGF_OK) return s;
@@ -1635,5 +1767,5 @@ ifgf_status ifgf_jit_upward(ifgf_plan *p, int d, int b0, int b1, JitLists *out, 
         CK(cudaStreamSynchronize(st));
         return IFGF_OK;
     }
-    return sort_into_csr(p, (int *)keys.ptr, (int *)vals.ptr, m, ns, out->start, out->list, st);
+    return sort_into_csr(p, (int *)w->keys.ptr, (int *)w->vals.ptr, m, ns, out->start, out->list, w, st);
 }

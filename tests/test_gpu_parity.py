@@ -83,6 +83,28 @@ def test_tree_and_cones_bit_exact(pkg, torch_cuda, case):
     assert g.check() == 0
 
 
+@pytest.mark.parametrize("case,precision", [((12000, 8, 6, 1, 2), "fp64"), ((12000, 8, 6, 1, 2), "mixed"),
+                                            ((16000, 4, 5, 3, 6), "mixed")])
+def test_rule_ii_by_cone_id_marks_the_same_cones(pkg, torch_cuda, case, precision):
+    # relevance rule (ii) marked once per distinct parent cone id and octant (default,
+    # where the ids are few against the parent slots) and node by node (flags bit 12):
+    # the same relevant cones on every level, and both equal to the oracle's
+    wl, pts, _ = _make(case)
+    n, nl, D, ns, nc = case
+    a = pkg.Plan(pts, wl.kappa, D, 3, 5, ns, nc, precision=precision)
+    b = pkg.Plan(pts, wl.kappa, D, 3, 5, ns, nc, precision=precision, flags=4096)
+    o = oracle.Plan(pts, wl.kappa, D, 3, 5, ns, nc)
+    sa, sb = a.stats()["level"], b.stats()["level"]
+    assert any(lv["act_sets"] for lv in sa) and not any(lv["act_sets"] for lv in sb)
+    for d in range(3, D + 1):
+        ga, gc = a.active(d)
+        ha, hc = b.active(d)
+        oa, oc = o.active(d)
+        assert np.array_equal(ga, ha) and np.array_equal(gc, hc), d
+        assert np.array_equal(ga, oa) and np.array_equal(gc, oc), d
+    assert a.check() == 0 and b.check() == 0
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_fp64_apply_matches_oracle_and_direct(pkg, torch_cuda, case):
     torch = torch_cuda
