@@ -524,36 +524,61 @@ __global__ void k_cone_sets(PlanDev pd, int d, const int *uids, int rows, int *s
     }
 }
 
-// one thread per (parent slot, child position): the child's bits of the slot's cone id
+// One thread per (child position, parent slot), slots innermost: the lanes of a warp hold
+// consecutive slots, mostly of one parent box, so they mark cones of the same child box.
+// Lanes that set bits in the same bitmap word combine them first (match, then an OR
+// reduction over the group) and one of them issues the atomic: the slots of a box all
+// write into a few words of each child, and one atomic each would serialise in L2.
 __global__ void k_activate_parent_sets(PlanDev pd, int d, const uint64_t *ubits, const int *urank, const int *sets,
                                        uint64_t *bits)
 {
     const LevelDev &L = pd.lev[d];
     const LevelDev &Lp = pd.lev[d - 1];
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)Lp.nact * 8) return;
-    const int slot = (int)(t >> 3), kk = (int)(t & 7);
-    const int j = Lp.act_box[slot];
-    const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
-    if (kk >= nch) return;
-    const int k = k0 + kk, oct = (int)(L.key[k] & 7u);
-    const int pcone = Lp.act_cone[slot];
-    const int row = table_row(ubits, urank, pcone);
-    if (row < 0) {  // every relevant cone id is in the union
-        atomicAdd(pd.err, 1);
-        return;
+    const int64_t total = (int64_t)Lp.nact * 8;
+    if (__all_sync(0xffffffffu, t >= total)) return;  // whole warps past the end
+    bool valid = t < total;
+    const int kk = valid ? (int)(t / Lp.nact) : 0, slot = valid ? (int)(t % Lp.nact) : 0;
+    int k = 0, oct = 0, pcone = 0, cnt = 0;
+    const int *set = nullptr;
+    if (valid) {
+        const int j = Lp.act_box[slot];
+        const int k0 = Lp.child_start[j], nch = Lp.child_start[j + 1] - k0;
+        valid = kk < nch;
+        if (valid) {
+            k = k0 + kk;
+            oct = (int)(L.key[k] & 7u);
+            pcone = Lp.act_cone[slot];
+            const int row = table_row(ubits, urank, pcone);
+            if (row < 0) {  // every relevant cone id is in the union
+                atomicAdd(pd.err, 1);
+                valid = false;
+            } else {
+                set = sets + ((size_t)row * 8 + oct) * (kConeSet + 1);
+                cnt = set[0];
+            }
+        }
     }
-    const int *set = sets + ((size_t)row * 8 + oct) * (kConeSet + 1);
-    const int cnt = set[0];
-    if (cnt >= 0) {
-        for (int i = 0; i < cnt; ++i) set_bit(bits, L.words, k, set[1 + i]);
-        return;
+#pragma unroll
+    for (int i = 0; i < kConeSet; ++i) {
+        unsigned long long key = ~0ull, bit = 0;
+        if (valid && i < cnt) {
+            const int cone = set[1 + i];
+            key = (unsigned long long)k * L.words + (unsigned)(cone >> 6);
+            bit = 1ull << (cone & 63);
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const unsigned lo = __reduce_or_sync(grp, (unsigned)bit), hi = __reduce_or_sync(grp, (unsigned)(bit >> 32));
+        if (key != ~0ull && (threadIdx.x & 31) == __ffs(grp) - 1)
+            atomicOr((unsigned long long *)&bits[key], ((unsigned long long)hi << 32) | lo);
     }
-    const double hh = L.H * 0.5;
-    for (int node = 0; node < pd.P; ++node) {
-        double v[3];
-        node_rel(Lp, pd.Ps, pd.Pang, pcone, node, hh, oct, v, nullptr);
-        set_bit(bits, L.words, k, cone_of_mixed(L, v[0], v[1], v[2]).cone);
+    if (valid && cnt < 0) {  // more than kConeSet cells: node by node
+        const double hh = L.H * 0.5;
+        for (int node = 0; node < pd.P; ++node) {
+            double v[3];
+            node_rel(Lp, pd.Ps, pd.Pang, pcone, node, hh, oct, v, nullptr);
+            set_bit(bits, L.words, k, cone_of_mixed(L, v[0], v[1], v[2]).cone);
+        }
     }
 }
 
